@@ -1,0 +1,427 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from analytic_refs import SodSolution, bjorken_conformal
+from workload.eos import A_SB, build_table
+from workload.gubser import GubserSolution
+from workload.problem import (HBARC, Problem, bjorken_problem, conformal_eos, cylinder_problem,
+                              gubser_problem, sod_diagonal_problem, sod_problem)
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_setups.json")))
+
+
+# ------------------------------------------------------------------------- minmod (Sec. 3.1)
+def test_minmod_is_smallest_magnitude_or_zero():
+    rng = np.random.default_rng(0)
+    vals = np.concatenate([rng.normal(size=3000), np.zeros(300)])
+    rng.shuffle(vals)
+    for x, y, z in vals.reshape(-1, 3):
+        m = oracle.minmod3(x, y, z)
+        if (x > 0 and y > 0 and z > 0) or (x < 0 and y < 0 and z < 0):
+            assert m == min((x, y, z), key=abs)
+        else:
+            assert m == 0.0
+    assert oracle.minmod3(1.0, 2.0, 3.0) == 1.0 and oracle.minmod3(-3.0, -2.0, -1.5) == -1.5
+    assert oracle.minmod3(0.0, 1.0, 1.0) == 0.0  # sgn(0) = 0
+
+
+def _line_problem(nx=16, coords="cartesian"):
+    p = Problem(name="line", nx=nx, ny=1, neta=1, dx=0.1, dy=0.1, deta=0.1, dtau=0.01, tau0=1.0, nsteps=1,
+                coords=coords, eos=conformal_eos(), regulate=False)
+    return p
+
+
+def test_constant_state_has_zero_rhs():
+    p = _line_problem()
+    p.e = np.full(p.ncells, 3.0)
+    p.u = np.stack([np.full(p.ncells, 0.4), np.full(p.ncells, -0.2), np.full(p.ncells, 0.1)])
+    C = oracle.Oracle(p).rhs()
+    assert np.max(np.abs(C)) < 1e-13
+
+
+def test_linear_pressure_gradient_source():
+    """Fluid at rest with e linear in x: fluxes vanish (v = 0) and S_c^x = -d_x P exactly."""
+    p = _line_problem()
+    X, _, _ = p.coords_xyz()
+    p.e = (5.0 + 2.0 * X).ravel()
+    C = oracle.Oracle(p).rhs()
+    interior = slice(2, -2)
+    np.testing.assert_allclose(C[1][interior], -2.0 / 3.0, rtol=1e-12)
+    assert np.max(np.abs(C[0][interior])) < 1e-12 and np.max(np.abs(C[2:4])) < 1e-12
+
+
+def test_linear_advection_flux_divergence():
+    """Uniform velocity, e linear in x, theta = 1: slopes are exact, faces are continuous and
+    C[T^tt] = -v d_x (T^tt + P) exactly in the interior."""
+    p = _line_problem()
+    X, _, _ = p.coords_xyz()
+    v = 0.3
+    ux = v / math.sqrt(1 - v * v)
+    p.e = (5.0 + 2.0 * X).ravel()
+    p.u = np.stack([np.full(p.ncells, ux), np.zeros(p.ncells), np.zeros(p.ncells)])
+    o = oracle.Oracle(p)
+    C = o.rhs()
+    g2 = 1.0 / (1 - v * v)
+    dTtt = (4.0 / 3.0 * g2 - 1.0 / 3.0) * 2.0
+    dP = 2.0 / 3.0
+    np.testing.assert_allclose(C[0][3:-3], -v * (dTtt + dP), rtol=1e-12)
+
+
+def test_direction_permutation_symmetry_is_exact():
+    """The same 1D problem along x, y and eta (Cartesian) gives bit-identical results."""
+    res = []
+    for axis in range(3):
+        p = sod_problem(nx=60, dx=0.1, t_end=1.0, axis=axis)
+        o = oracle.Oracle(p)
+        o.step(p.nsteps)
+        s = o.get_state()
+        res.append((s["e"].copy(), s["u"][1 + axis].copy()))
+    for axis in (1, 2):
+        assert np.array_equal(res[0][0], res[axis][0])
+        assert np.array_equal(res[0][1], res[axis][1])
+
+
+# --------------------------------------------------------------------------- EOS (Sec. 2.3)
+def test_stefan_boltzmann_constant():
+    nc, nf = GOLD["sb_eos"]["Nc"], GOLD["sb_eos"]["Nf"]
+    assert abs(A_SB - 3 * (2 * (nc * nc - 1) + 3.5 * nc * nf) * math.pi ** 2 / 90) < 1e-14
+    assert abs(A_SB - 15.6269) < 1e-4
+
+
+@pytest.fixture(scope="module")
+def eos_pair():
+    tab, dense = build_table(n=4096)
+    p = bjorken_problem(eos="table").replace(eos=tab)
+    return oracle.Oracle(p), tab, dense
+
+
+def test_eos_table_interpolation_matches_thermodynamics(eos_pair):
+    o, tab, dense = eos_pair
+    rng = np.random.default_rng(1)
+    for T in np.exp(rng.uniform(math.log(0.01 / HBARC), math.log(1.5 / HBARC), 200)):
+        e = dense["e"](T)
+        P, cs2, Tt = o.eos(e)
+        assert abs(P / dense["P"](T) - 1) < 1e-8
+        assert abs(Tt / T - 1) < 1e-8
+        assert abs(cs2 - dense["cs2"](T)) < 2e-6
+    for i in (0, 17, 2048, 4094):  # nodes are reproduced exactly
+        P, cs2, Tt = o.eos(tab.e[i])
+        assert abs(P - tab.p[i]) <= 1e-15 * abs(tab.p[i]) and abs(cs2 - tab.cs2[i]) < 1e-15
+
+
+# --------------------------------------------------------------------- inversion (Sec. 2.4)
+def _forward(e, P0, Pi, u, pi, tau):
+    """Eqs. (Ttt), (Tti): T^{tau tau} = (e+P) ut^2 - P + pi^tt, T^{tau i} = (e+P) ut u^i + pi^{ti}."""
+    P = P0 + Pi
+    q = np.zeros(15)
+    q[0] = (e + P) * u[0] ** 2 - P + pi[0]
+    for i in range(1, 4):
+        q[i] = (e + P) * u[0] * u[i] + pi[i]
+    q[4:14] = pi
+    q[14] = Pi
+    return q
+
+
+@pytest.mark.parametrize("kind", ["conformal", "table"])
+def test_inversion_round_trip(kind, baseline_eos):
+    eos = conformal_eos() if kind == "conformal" else baseline_eos
+    p = bjorken_problem(eos="conformal" if kind == "conformal" else "table").replace(
+        eos=eos, zeta_over_s=("gauss", 0.1, 0.17 / HBARC, 0.03 / HBARC) if kind == "table" else ("const", 0, 0, 1))
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for k in range(400):
+        tau = rng.uniform(0.3, 3.0)
+        e = math.exp(rng.uniform(math.log(1e-3), math.log(2e3)))
+        speed = 0.999 if k % 10 == 0 else rng.uniform(0, 0.99)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        g = 1 / math.sqrt(1 - speed ** 2)
+        u = np.array([g, g * speed * d[0], g * speed * d[1], g * speed * d[2] / tau])
+        P0 = o.eos(e)[0]
+        Pi = 0.0 if kind == "conformal" else rng.uniform(-0.2, 0.2) * P0
+        pi = np.zeros(10)  # pi enters E and M only through T - pi, so zero keeps the test exact
+        q = _forward(e, P0, Pi, u, pi, tau)
+        st, out = o.invert(tau, q)
+        assert st == 0
+        err = abs(out[0] / e - 1)
+        worst = max(worst, err)
+        tol = 1e-13 * (1 + g * g)  # cancellation in e = E - M^2/(E+P) grows like gamma^2
+        assert err < tol, (k, speed, err)
+        np.testing.assert_allclose(out[2:6], u, rtol=1e-12 * (1 + g * g), atol=1e-12)
+
+
+def test_conformal_closed_form():
+    p = gubser_problem(nx=2, ny=2, neta=2)
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        E = rng.uniform(0.1, 100)
+        M = E * rng.uniform(0, 0.99)
+        q = np.zeros(15)
+        q[0], q[1] = E, M
+        st, out = o.invert(1.0, q)
+        ref = math.sqrt(4 * E * E - 3 * M * M) - E
+        assert st == 0 and abs(out[0] - ref) < 1e-13 * E
+
+
+def test_inversion_reports_unphysical_state():
+    p = gubser_problem(nx=2, ny=2, neta=2)
+    o = oracle.Oracle(p)
+    q = np.zeros(15)
+    q[0], q[1] = 1.0, 1.5  # M > E
+    st, _ = o.invert(1.0, q)
+    assert st != 0
+
+
+# --------------------------------------------------------------------- regulator (Sec. 3.2)
+def test_regulator_factor_cases():
+    p = gubser_problem(nx=2, ny=2, neta=2)
+    o = oracle.Oracle(p)
+    u = np.array([1.0, 0, 0, 0])
+    assert o.regulator_factor(1.0, 3.0, 1.0, u, np.zeros(16), 0.0) == 1.0
+    # fluid at rest, pi = diag(0, a, -a, 0): Pi^{mu nu}Pi_{mu nu} = 2 a^2, rho = sqrt(2) a / sqrt(e^2+3P^2)
+    for a in (0.01, 0.3, 5.0):
+        pi = np.zeros((4, 4))
+        pi[1, 1], pi[2, 2] = a, -a
+        e, P = 3.0, 1.0
+        rho = math.sqrt(2) * a / math.sqrt(e * e + 3 * P * P)
+        f = o.regulator_factor(1.0, e, P, u, pi, 0.0)
+        assert abs(f - math.tanh(rho) / rho) < 1e-15
+    # a trace violation drives rho through the second ratio
+    pi = np.zeros((4, 4))
+    pi[1, 1] = pi[2, 2] = 0.1
+    f = o.regulator_factor(1.0, 3.0, 1.0, u, pi, 0.0)
+    rho = abs(-0.2) / (0.1 * math.sqrt(0.02))
+    assert abs(f - math.tanh(rho) / rho) < 1e-14
+
+
+# ------------------------------------------------------------------- Bjorken (Secs. 5.4-5.5)
+def test_bjorken_conformal_second_order():
+    gold = GOLD["bjorken"]
+    errs = []
+    for dt in (0.01, 0.005, 0.0025):
+        ns = int(round(0.5 / dt))
+        p = bjorken_problem(T0_gev=gold["T0_gev"], tau0=gold["tau0_fm"], eta_over_s=gold["eta_over_s"],
+                            dtau=dt, nsteps=ns)
+        o = oracle.Oracle(p)
+        o.step(ns)
+        s = o.get_state()
+        assert np.ptp(s["e"]) == 0.0  # stays homogeneous
+        ref = bjorken_conformal(p.tau0, p.e[0], -p.tau0 ** 2 * p.pi[9][0], [s["tau"]], gold["eta_over_s"], A_SB)
+        pi = -s["tau"] ** 2 * s["pi"][9][0]
+        errs.append((abs(s["e"][0] / ref[0][-1] - 1), abs(pi / ref[1][-1] - 1)))
+    for k in range(2):
+        assert errs[0][k] / errs[1][k] > 3.5 and errs[1][k] / errs[2][k] > 3.5
+    assert errs[2][0] < 3e-5 and errs[2][1] < 5e-4
+
+
+def test_bjorken_bulk_second_order(baseline_eos):
+    """Nonconformal Bjorken with Pi (Eqs. evolutionEd-evolutionpi) near T_c, where zeta/s is large."""
+    from scipy.integrate import solve_ivp
+    es, taumin = 0.2, 0.005
+    errs = []
+    for dt in (0.004, 0.002, 0.001):
+        ns = int(round(0.4 / dt))
+        p = bjorken_problem(T0_gev=0.22, tau0=0.6, dtau=dt, nsteps=ns, eos="table", zeta=True,
+                            eta_over_s=es).replace(tau_relax_min=taumin)
+        o = oracle.Oracle(p)
+
+        def rhs(t, y):
+            e, pi, Pi = y
+            P, cs2, T = o.eos(e)
+            d = math.exp(math.log(0.2) - ((T * HBARC - 0.17) / 0.05) ** 2)
+            zs = 0.1 * math.exp(-((T * HBARC - 0.17) / 0.03) ** 2)
+            rateP = min(15 * d * d * T / zs, 1 / taumin)
+            rate_pi = min(T / (5 * es), 1 / taumin)
+            # Eqs. (evolutionEd), (evolutionPi), (evolutionpi) with the coefficients of Sec. 2.2
+            return [-(e + P + Pi - pi) / t,
+                    4 / 3 * ((e + P) / 5) / t - (4 / 3 + (10 / 7) / 3) * pi / t + 2 / 3 * 1.2 * Pi / t - rate_pi * pi,
+                    -15 * d * d * (e + P) / t - rateP * Pi - 2 / 3 * Pi / t + 1.6 * d * pi / t]
+        y0 = [p.e[0], -p.tau0 ** 2 * p.pi[9][0], 0.0]
+        r = solve_ivp(rhs, (p.tau0, p.tau0 + ns * dt), y0, method="Radau", rtol=1e-12, atol=1e-14)
+        o.step(ns)
+        s = o.get_state()
+        pi = -s["tau"] ** 2 * s["pi"][9][0]
+        errs.append((abs(s["e"][0] / r.y[0][-1] - 1), abs(pi / r.y[1][-1] - 1)))
+        assert abs(s["Pi"][0]) > 1e-4 * s["e"][0]  # bulk is active
+        # Pi agrees to the resolution of the tabulated ln(1/3 - cs2) (linear between nodes,
+        # ~1e-5 relative in (1/3 - cs2) at 4096 nodes), independently of dtau
+        assert abs(s["Pi"][0] / r.y[2][-1] - 1) < 1e-5
+    for k in range(2):
+        assert errs[0][k] / errs[1][k] > 3.5 and errs[1][k] / errs[2][k] > 3.5
+
+
+# ---------------------------------------------------------------------- Gubser (Secs. 5.6-5.7)
+def _gubser_err(nx, dx, dt, nsteps, eta_over_s):
+    p = gubser_problem(nx=nx, ny=nx, dx=dx, dtau=dt, nsteps=nsteps, eta_over_s=eta_over_s)
+    o = oracle.Oracle(p)
+    assert o.step(nsteps) == 0
+    s = o.get_state()
+    X, Y, _ = p.coords_xyz()
+    X, Y = X.ravel(), Y.ravel()
+    ref = p.gubser.state(s["tau"], X, Y, A_SB)
+    ymin = np.min(np.abs(Y))
+    m = (np.abs(Y - ymin) < 1e-9) & (np.abs(X) <= 1.2) & (np.arange(len(X)) < p.nx * p.ny)
+    return (np.max(np.abs(s["e"][m] / ref["e"][m] - 1)), np.max(np.abs(s["u"][1][m] - ref["ux"][m])))
+
+
+def test_gubser_ideal_converges():
+    e1, u1 = _gubser_err(32, 0.1, 0.01, 20, 0.0)
+    e2, u2 = _gubser_err(64, 0.05, 0.005, 40, 0.0)
+    assert e1 < 0.025 and u1 < 0.025
+    assert e1 / e2 > 2.0 and u1 / u2 > 2.0
+
+
+def test_gubser_viscous_c0():
+    """Semi-analytic viscous Gubser (tau_pipi = 0, theta = 1.8, eta/s = 0.2) on the 32x32x8 grid,
+    and a grid-convergence check at half the spacing.  Tolerances are calibrated by that study:
+    3e-2 in e and u^x at dx = 0.1 (the error about halves with dx)."""
+    g = GOLD["gubser_viscous"]
+    assert g["theta"] == 1.8 and g["eta_over_s"] == 0.2
+    e1, u1 = _gubser_err(32, 0.1, 0.01, 20, 0.2)
+    e2, u2 = _gubser_err(64, 0.05, 0.005, 40, 0.2)
+    assert e1 < 0.03 and u1 < 0.03
+    assert e1 / e2 > 1.8 and u1 / u2 > 1.8
+
+
+# --------------------------------------------------------------- shock tubes (Secs. 5.1-5.3)
+def test_sod_converges_to_riemann_solution():
+    g = GOLD["sod"]
+    eL, eR = g["e_left_gev_fm3"] / HBARC, g["e_right_gev_fm3"] / HBARC
+    sol = SodSolution(eL, eR)
+    assert abs(sol.rh_residual) < 1e-12 * eL
+    L1 = []
+    for dx in g["dx_fm"]:
+        p = sod_problem(nx=int(round(20 / dx)), dx=dx, t_end=2.0, e_left_gev=g["e_left_gev_fm3"],
+                        e_right_gev=g["e_right_gev_fm3"])
+        o = oracle.Oracle(p)
+        assert o.step(p.nsteps) == 0
+        s = o.get_state()
+        X, _, _ = p.coords_xyz()
+        x = X.ravel()
+        eref, _ = sol(x, p.nsteps * p.dtau)
+        m = np.abs(x) <= 4
+        L1.append(np.sum(np.abs(s["e"][m] - eref[m])) * dx / (eL * 8))
+    assert L1[0] > L1[1] > L1[2]
+    assert L1[0] / L1[2] > 3.0
+    assert L1[2] < 3e-3
+
+
+def test_sod_diagonal_matches_1d():
+    """Membrane along y = x (Sec. 5.2): e on the anti-diagonal equals the 1D solution at
+    x' = (x - y)/sqrt(2) to the resolution of the 1D scheme."""
+    g = GOLD["sod"]
+    eL = g["e_left_gev_fm3"] / HBARC
+    sol = SodSolution(eL, g["e_right_gev_fm3"] / HBARC)
+    p = sod_diagonal_problem(n=80, dx=0.1, t_end=1.0)
+    o = oracle.Oracle(p)
+    o.step(p.nsteps)
+    s = o.get_state()
+    E = s["e"].reshape(p.ny, p.nx)
+    X, Y, _ = p.coords_xyz()
+    X, Y = X.reshape(p.ny, p.nx), Y.reshape(p.ny, p.nx)
+    i = np.arange(p.nx)
+    xs = (X[p.ny - 1 - i, i] - Y[p.ny - 1 - i, i]) / math.sqrt(2)
+    eref, _ = sol(xs, p.nsteps * p.dtau)
+    m = np.abs(xs) < 2.5
+    L1 = np.mean(np.abs(E[p.ny - 1 - i, i][m] - eref[m])) / eL
+    assert L1 < 0.03
+    # mirror symmetry about y = x after swapping the sides: e(x, y) + e(y, x) structure
+    assert np.max(np.abs(E - E.T[::-1, ::-1])) < 1e-12 * eL
+
+
+def test_cylindrical_explosion_keeps_xy_symmetry():
+    g = GOLD["cylinder"]
+    p = cylinder_problem(n=40, dx=0.25, t_end=1.0, R=g["R_fm"], e_in_gev=g["e_in_gev_fm3"],
+                         e_out_gev=g["e_out_gev_fm3"])
+    o = oracle.Oracle(p)
+    o.step(p.nsteps)
+    s = o.get_state()
+    E = s["e"].reshape(p.ny, p.nx)
+    assert np.max(np.abs(E - E.T)) <= 1e-13 * E.max()
+    assert np.max(np.abs(E - E[::-1, :])) <= 1e-13 * E.max()
+    ux = s["u"][1].reshape(p.ny, p.nx)
+    uy = s["u"][2].reshape(p.ny, p.nx)
+    assert np.max(np.abs(ux - uy.T)) <= 1e-13
+
+
+# ---------------------------------------------------------------- conservation (periodic)
+def test_energy_momentum_conserved_on_periodic_cartesian_grid(baseline_eos):
+    n = 8
+    p = Problem(name="per", nx=n, ny=n, neta=n, dx=0.2, dy=0.2, deta=0.2, dtau=0.02, tau0=1.0, nsteps=40,
+                coords="cartesian", bc="periodic", theta=1.5, eos=baseline_eos,
+                eta_over_s=("const", 0.2, 0, 1), zeta_over_s=("gauss", 0.1, 0.17 / HBARC, 0.03 / HBARC),
+                tau_relax_min=0.02)
+    X, Y, Z = p.coords_xyz()
+    k = 2 * np.pi / (n * 0.2)
+    p.e = (1.0 / HBARC) * (1 + 0.5 * np.sin(k * X) * np.cos(k * Y) + 0.3 * np.sin(k * Z)).ravel()
+    p.u = np.stack([0.2 * np.sin(k * Y).ravel(), 0.1 * np.cos(k * X).ravel(), 0.15 * np.sin(k * (X + Z)).ravel()])
+    o = oracle.Oracle(p)
+    q0 = o.get_state()["q"][:4].sum(axis=1)
+    assert o.step(p.nsteps) == 0
+    s = o.get_state()
+    q1 = s["q"][:4].sum(axis=1)
+    assert np.max(np.abs(s["pi"])) > 1e-3 and np.max(np.abs(s["Pi"])) > 1e-3
+    assert np.max(np.abs(q1 - q0)) < 1e-13 * q0[0]
+
+
+# ------------------------------------------------- constraint preservation (Sec. 2.4)
+def _projected_pi(u, tau, rng, scale):
+    g = np.array([1.0, -1.0, -1.0, -tau ** 2])
+    gi = 1.0 / g
+    ul = g * u
+    D = np.diag(gi) - np.outer(u, u)          # Delta^{mu nu}
+    Dm = np.eye(4) - np.outer(u, ul)          # Delta^mu_alpha
+    X = rng.normal(size=(4, 4))
+    X = X + X.T
+    Y = Dm @ X @ Dm.T
+    tr = np.einsum("ab,a,b->", Y, g, np.ones(4)) if False else np.sum(g * np.diag(Y))
+    Y = Y - D * tr / 3.0 * (1 / 1.0) * (1.0 if True else 0)
+    # remove the trace with Delta (g_{mu nu} Delta^{mu nu} = 3)
+    return scale * Y
+
+
+def test_uniform_flow_preserves_pi_constraints():
+    """A homogeneous state with u^eta != 0 evolves by ODEs; pi^{mu nu} u_nu = 0 and
+    g_{mu nu} pi^{mu nu} = 0 are preserved up to the first-order error of the backward
+    difference for d_tau u (they shrink linearly with dtau).  A wrong Christoffel term in G_pi
+    or I1 breaks this."""
+    rng = np.random.default_rng(3)
+    viol = []
+    for dt in (0.004, 0.002):
+        tau0 = 1.0
+        ux, uy, un = 0.3, -0.2, 0.4
+        ut = math.sqrt(1 + ux * ux + uy * uy + tau0 ** 2 * un * un)
+        u = np.array([ut, ux, uy, un])
+        pi4 = _projected_pi(u, tau0, np.random.default_rng(3), 0.3)
+        idx = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
+        p = Problem(name="uni", nx=2, ny=2, neta=2, dx=0.1, dy=0.1, deta=0.1, dtau=dt, tau0=tau0,
+                    nsteps=int(round(0.2 / dt)), coords="milne", eos=conformal_eos(),
+                    eta_over_s=("const", 0.2, 0, 1), regulate=False)
+        N = p.ncells
+        p.e = np.full(N, 10.0)
+        p.u = np.tile(np.array([[ux], [uy], [un]]), (1, N))
+        p.pi = np.tile(np.array([[pi4[a, b]] for a, b in idx]), (1, N))
+        o = oracle.Oracle(p)
+        assert o.step(p.nsteps) == 0
+        s = o.get_state()
+        tau = s["tau"]
+        g = np.array([1.0, -1.0, -1.0, -tau ** 2])
+        P = np.zeros((4, 4))
+        for k, (a, b) in enumerate(idx):
+            P[a, b] = P[b, a] = s["pi"][k][0]
+        uu = s["u"][:, 0]
+        orth = P @ (g * uu)
+        orth[3] *= tau
+        trace = np.sum(g * np.diag(P))
+        norm = math.sqrt(abs(np.einsum("ab,ab,a,b->", P, P, g, g)))
+        viol.append(max(np.max(np.abs(orth)), abs(trace)) / norm)
+    assert viol[0] < 2e-3
+    assert 1.6 < viol[0] / viol[1] < 2.4  # first order in dtau
