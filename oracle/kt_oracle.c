@@ -207,7 +207,8 @@ static int invert_core(const ko_ctx* c, double tau, const double* q, double e0, 
       st = KO_ST_INVERSION;
       e = (flo > 0.0) ? lo : hi;
     } else {
-      e = (e0 > lo && e0 < hi) ? e0 : 0.5 * (lo + hi);
+      /* start: the cell's previous e if it lies in the bracket, else E */
+      e = (e0 >= lo && e0 <= hi) ? e0 : hi;
       int it;
       for (it = 0; it < 200; ++it) {
         eos_eval(c, e, &P0, &cs2, &T, &lnd);
@@ -217,10 +218,11 @@ static int invert_core(const ko_ctx* c, double tau, const double* q, double e0, 
         if (f < 0.0) lo = e; else hi = e;
         double fp = 1.0 - M2 * cs2 / (A * A);
         double en = e - f / fp;
-        if (!(en > lo && en < hi)) en = 0.5 * (lo + hi);
+        if (!(en >= lo && en <= hi)) en = 0.5 * (lo + hi); /* bisect when Newton leaves the bracket */
         double de = fabs(en - e);
         e = en;
-        if (de <= ldexp(e, -50)) break;
+        /* f is known to about one ulp of E, so the root is resolved to that level */
+        if (de <= ldexp(E, -50)) break;
       }
       if (it >= 200) st = KO_ST_INVERSION;
     }
