@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Benchmark: cell updates/s per RK2 (Heun) step of the KT viscous-hydro step at 128^3.
+
+Workload: the 128^3 Milne grid with the nonconformal EOS (c_s^2(T) = 1/3 - 0.2 exp(-((T-0.17)/0.05)^2)),
+eta/s = 0.08, zeta/s = 0.1 exp(-((T-0.17)/0.03)^2), 50 Gaussian hotspots (seed 1), tau0 = 0.5 fm,
+dtau = 0.005 fm.  The state (~1.1-1.7 GB) is far larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode mixed|fp64]
+
+Under torchrun (N > 1) every rank advances its own event (different seed): replicas, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell updates/s per RK2 step at 128^3, plain FP64 vs FP32+learned; % HBM peak"
+UNIT = "cell updates/s"
+# algorithmic bytes per cell per RK2 step of the two fused stages (both stages read and write
+# every field once): 107 words; u, e, p are 4-byte words in mixed mode
+BYTES_PER_CELL = {"fp64": 107 * 8, "mixed": 59 * 8 + 48 * 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_rate(prob_full, nz_sample, nsteps, threads=None):
+    """Time the CPU oracle on a slab of the workload (same grid spacing, nz_sample eta cells)."""
+    import oracle
+    from workload.problem import hotspot_problem
+    p = hotspot_problem(nx=prob_full.nx, ny=prob_full.ny, neta=nz_sample)
+    o = oracle.Oracle(p, threads=threads)
+    cores = oracle.set_threads(threads or 0)
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    dt = time.perf_counter() - t0
+    return p.ncells * nsteps / dt, cores, f"{p.nx}x{p.ny}x{p.neta} slab of the 128^3 workload, {nsteps} steps"
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle (the only other implementation of the method here)."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    from workload.problem import hotspot_problem
+    cores = os.cpu_count()
+    prob = hotspot_problem(nx=args.n, ny=args.n, neta=args.n, nsteps=1)
+    nz = 4
+    p = hotspot_problem(nx=args.n, ny=args.n, neta=nz)
+    o = oracle.Oracle(p, threads=cores)
+    cores = oracle.set_threads(cores)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = p.ncells * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"hotspots {prob.nx}x{prob.ny}x{prob.neta} (sampled as a "
+                                   f"{p.nx}x{p.ny}x{p.neta} slab per step)", "dx_fm": 0.1, "deta": 0.1,
+                       "dtau_fm": 0.005, "eos": "tabulated c_s^2(T)", "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{p.nx}x{p.ny}x{p.neta} slab, {args.steps} steps after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def time_mode(prob, mode, steps, warmup, stream):
+    import torch
+    from paper_1608_06577_gb300 import KT
+    prec = 1 if mode == "mixed" else 0
+    with torch.cuda.stream(stream):
+        kt = KT(prob, precision=prec)
+    kt.set_problem_state()
+    kt.step(warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    kt.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    return kt, ms
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from workload.problem import hotspot_problem
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    n = args.n
+    prob = hotspot_problem(nx=n, ny=n, neta=n, seed=1 + rank)
+    cells = prob.ncells
+    hbm_peak, peak_kind = measured_peaks()
+    results = {}
+    modes = [args.mode] + [m for m in ("fp64", "mixed") if m != args.mode]
+    clocks = None
+    for mode in modes:
+        steps = args.steps if mode == args.mode else max(3, min(args.steps, 6))
+        barrier(world)
+        torch.cuda.synchronize()
+        if mode == args.mode:
+            with ClockSampler(local) as cs:
+                kt, ms = time_mode(prob, mode, steps, args.warmup, stream)
+            clocks = cs.summary()
+        else:
+            kt, ms = time_mode(prob, mode, steps, args.warmup, stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = max_over_ranks(ms, world)
+        st = kt.stats()
+        results[mode] = {"ms_per_step": ms / steps, "value": cells * world * steps / (ms * 1e-3), "steps": steps,
+                         "stats": st}
+        del kt
+        torch.cuda.empty_cache()
+
+    main = results[args.mode]
+    ms_step = main["ms_per_step"]
+    # dominant kernel: the fused stage kernel, two launches per step (the tau-advance kernel is ~0.1%)
+    stage_ms = ms_step / 2.0
+    bpc = BYTES_PER_CELL[args.mode]
+    achieved = cells * bpc / 2.0 / (stage_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "note": "algorithmic bytes per stage launch / average launch time; the kernel is FP64-pipe "
+                        "bound on GB300 (see profiles/)"}
+
+    e2e = None
+    if not args.no_e2e:
+        from paper_1608_06577_gb300 import KT
+        import numpy as np
+        with torch.cuda.stream(stream):
+            kt = KT(prob, precision=1 if args.mode == "mixed" else 0)
+        out = {"e": np.empty(cells), "u": np.empty((4, cells))}
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        kt.set_problem_state()
+        kt.step(args.steps)
+        kt.get_state(fields=("e", "u"))
+        t1 = time.perf_counter()
+        barrier(world)
+        dt = max_over_ranks(t1 - t0, world)
+        h2d = (1 + 3 + 10 + 1) * cells * 8
+        d2h = 5 * cells * 8
+        e2e = {"value": cells * world * args.steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": f"kt_set_state from host, {args.steps} steps, kt_get_state(e, u) to host"}
+        del kt
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, cores, sample = oracle_rate(prob, 32, 2, threads=os.cpu_count())
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        except Exception as ex:  # the baseline never blocks the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": main["steps"],
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": f"hotspots {n}x{n}x{n} Milne, nonconformal EOS, eta/s 0.08, "
+                                       f"zeta/s gaussian, {args.mode}", "global_batch": world, "seq_len": None,
+                           "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)",
+                           "precision_mode": args.mode},
+                "modes": {m: {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
+                              "newton_iters_per_cell_stage": r["stats"]["newton_iters"] / (cells * 2 * r["steps"])}
+                          for m, r in results.items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": 3 * main["steps"]}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * kt.h -- C ABI of libkt: the Kurganov-Tadmor (KT) semi-discrete step with Heun (RK2) time
+ * integration for 3+1d relativistic viscous hydrodynamics in Milne coordinates (tau, x, y, eta_s)
+ * with shear stress pi^{mu nu} and bulk pressure Pi, as stated in
+ * D. Bazow, U. Heinz, M. Strickland, "Massively parallel simulations of relativistic fluid
+ * dynamics on graphics processing units with CUDA", arXiv:1608.06577.
+ *
+ * Every step of the time integration runs in hand-written CUDA kernels for sm_103a (GB300).
+ * There is no CPU fallback: without a CUDA device kt_init fails with KT_ERR_CUDA.
+ *
+ * Units: hbar = c = 1, lengths in fm.  Energy density, pressures, pi^{mu nu} and Pi in fm^-4,
+ * temperature in fm^-1, tau and x, y in fm, eta_s dimensionless.
+ *
+ * Layouts of the state arguments: physical cells only, x fastest, then y, then eta
+ * (index i + nx*(j + ny*k)), component-major (all cells of component 0, then component 1 ...).
+ * Internally the state lives in padded structure-of-arrays fields with two ghost layers on
+ * each side (Sec. 4.1, Eqs. ghostCells_1/2; Sec. 4.2).
+ *
+ * Conventions.  Every call returns KT_OK (0) or a negative KT_ERR_* code; on error nothing
+ * is written to the caller's outputs and kt_last_error() describes the failure.  No call
+ * throws.  A context belongs to one host thread; its work is enqueued on the context's
+ * stream.  Pointers passed to a call are only read or written during that call (buffers are
+ * copied); the caller keeps ownership of everything it passes.
+ */
+#ifndef KT_H
+#define KT_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+enum {
+  KT_OK = 0,
+  KT_ERR_ARG = -1,        /* invalid argument (null pointer, bad size, bad option) */
+  KT_ERR_CUDA = -2,       /* a CUDA runtime call failed (message in kt_last_error) */
+  KT_ERR_OOM = -3,        /* device allocation failed or the caller's arena is too small */
+  KT_ERR_EOS = -4,        /* EOS table not strictly increasing in e, or too short */
+  KT_ERR_STATE = -5,      /* non-finite input state or T^{tau tau} <= |T^{tau i}| after set_state */
+  KT_ERR_INVERSION = -6,  /* a cell's root-find (Eq. eInferred) failed during a step */
+  KT_ERR_NONFINITE = -7   /* a non-finite value appeared during a step */
+};
+
+enum { KT_MILNE = 0, KT_CARTESIAN = 1 };              /* coordinates (Cartesian: Sec. 5.1) */
+enum { KT_BC_COPY = 0, KT_BC_PERIODIC = 1 };          /* ghost cells: Eqs. ghostCells_1/2 or periodic */
+enum { KT_FP64 = 0, KT_MIXED = 1 };                   /* precision mode */
+enum { KT_INV_PLAIN = 0, KT_INV_LEARNED = 1 };        /* inversion start: previous e, or MLP */
+enum { KT_EOS_CONFORMAL = 0, KT_EOS_TABLE = 1 };
+enum { KT_COEF_CONST = 0, KT_COEF_GAUSS = 1 };
+
+typedef struct {
+  int nx, ny, neta; /* physical cells per axis, each >= 1 */
+} kt_grid;
+
+/* Equation of state (Sec. 2.3).
+ * KT_EOS_CONFORMAL: e = a T^4, P0 = e/3, c_s^2 = 1/3.
+ * KT_EOS_TABLE: n >= 4 nodes, e strictly increasing (fm^-4); P0 (fm^-4), c_s^2 = dP0/de,
+ *   T (fm^-1), lndelta = ln(1/3 - c_s^2) per node.  Interpolation: piecewise cubic Hermite in
+ *   e with slopes dP0/de = c_s^2 and dT/de = c_s^2 T/(e+P0); c_s^2 between nodes is the
+ *   derivative of the P0 interpolant; lndelta is linear in e.  Copied at kt_init. */
+typedef struct {
+  int kind;
+  double a;
+  int n;
+  const double *e, *p, *cs2, *T, *lndelta;
+} kt_eos;
+
+/* Specific viscosity eta/s or zeta/s as a function of T (fm^-1):
+ * KT_COEF_CONST: c0;  KT_COEF_GAUSS: c0 exp(-((T - c1)/c2)^2).
+ * KT_COEF_CONST with c0 = 0 switches the channel off (pi == 0 or Pi == 0). */
+typedef struct {
+  int kind;
+  double c0, c1, c2;
+} kt_coef;
+
+typedef struct {
+  double theta_limiter;  /* generalised minmod parameter in [1, 2] (Sec. 3.1); default 1 */
+  int coords;            /* KT_MILNE (default) or KT_CARTESIAN */
+  int bc;                /* KT_BC_COPY (default) or KT_BC_PERIODIC */
+  int precision;         /* KT_FP64 (default) or KT_MIXED: FP32 stencil/sources, FP64 Heun + inversion */
+  int inversion;         /* KT_INV_PLAIN (default) or KT_INV_LEARNED */
+  int tau_pipi_on;       /* 1 (default): tau_pipi/tau_pi = 10/7; 0: tau_pipi = 0 */
+  int regulate;          /* 1 (default): Eq. (regPimunu) after every inversion */
+  double rho_max, xi0;   /* regulator parameters of Eq. (rho); defaults 1 and 0.1 */
+  double e_min;          /* the inversion clamps e >= e_min (fm^-4); default 0 */
+  double tau_relax_min;  /* floor on tau_pi and tau_Pi (fm); default 0 (no floor) */
+  void* stream;          /* cudaStream_t for all work; NULL = a stream owned by the context */
+  void* arena;           /* optional caller-owned device memory for the state; NULL = cudaMalloc */
+  size_t arena_bytes;    /* its size, at least kt_state_bytes() */
+  const float* mlp_weights; /* KT_INV_LEARNED: host pointer to KT_MLP_NPARAM floats (see below) */
+  int use_graph;         /* 1 (default): kt_step replays a captured CUDA graph of the step loop */
+} kt_options;
+
+/* Learned inversion start: an MLP 6 -> 32 -> 32 -> 1 with ReLU; weights row-major
+ * W1[32][6], b1[32], W2[32][32], b2[32], W3[32], b3[1]. */
+#define KT_MLP_NPARAM (32 * 6 + 32 + 32 * 32 + 32 + 32 + 1)
+
+typedef struct {
+  double tau;            /* current proper time */
+  long long steps;       /* steps taken since kt_set_state */
+  float max_speed;       /* max local propagation speed a (Eq. ax) seen in the last step, times the
+                            direction's metric factor (tau for eta): a CFL diagnostic */
+  unsigned int status;   /* OR of per-cell status bits of the last kt_step: 1 inversion, 2 non-finite */
+  long long newton_iters;/* total Newton iterations in the last kt_step (all cells, both stages) */
+  long long fallbacks;   /* learned mode: cells that fell back to the plain root-find */
+  long long regulated;   /* cells whose pi was scaled by a factor < 0.999 in the last kt_step */
+} kt_stats;
+
+typedef struct kt_ctx kt_ctx;
+
+/* Fill *opt with the defaults listed above.  Returns KT_OK or KT_ERR_ARG. */
+int kt_options_default(kt_options* opt);
+
+/* Device bytes the state of one grid needs with these options (for kt_options.arena). */
+int kt_state_bytes(const kt_grid* grid, const kt_options* opt, size_t* bytes);
+
+/* Create a context (Sec. 4.3 step 2, memory allocation).  dx is used for x and y.
+ * eos, eta_over_s, zeta_over_s: problem definition of Secs. 2.2-2.3 (copied).  opt may be NULL. */
+int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dtau, const kt_eos* eos,
+            const kt_coef* eta_over_s, const kt_coef* zeta_over_s, const kt_options* opt);
+
+/* Set the state at proper time tau from primaries (Sec. 4.3 steps 3-5): the conserved
+ * variables are formed with Eqs. (Ttt), (Tti), ghost cells are filled.
+ *   e:      [cells] energy density (required)
+ *   u:      [3][cells] u^x, u^y, u^eta (NULL = fluid at rest); u^tau from u.u = 1
+ *   pi:     [10][cells] pi^{tt,tx,ty,tn,xx,xy,xn,yy,yn,nn} (NULL = 0)
+ *   Pi:     [cells] bulk pressure (NULL = 0)
+ *   u_prev: [3][cells] u at tau - dtau for the first backward time difference (NULL = u,
+ *           i.e. u^{-1} = u^0 as in Sec. 4.3)
+ * on_device: 0 = host pointers, 1 = device pointers.  Returns KT_ERR_STATE for non-finite
+ * inputs. */
+int kt_set_state(kt_ctx* ctx, double tau, const double* e, const double* u, const double* pi,
+                 const double* Pi, const double* u_prev, int on_device);
+
+/* Advance n_steps full Heun steps (Eqs. step1-finalStep; Sec. 4.3 steps 1-9), each two fused
+ * stage launches.  Asynchronous on the context's stream; it synchronises once at the end to
+ * read the status word.  Returns KT_ERR_INVERSION / KT_ERR_NONFINITE if any cell failed. */
+int kt_step(kt_ctx* ctx, int n_steps);
+
+/* Copy the state out (physical cells).  Any output may be NULL.
+ *   e [cells], u [4][cells] (u^tau, u^x, u^y, u^eta), pi [10][cells], Pi [cells],
+ *   q [15][cells] conserved variables of Eq. (qComponents). */
+int kt_get_state(kt_ctx* ctx, double* tau, double* e, double* u, double* pi, double* Pi, double* q,
+                 int on_device);
+
+int kt_get_stats(kt_ctx* ctx, kt_stats* stats);
+const char* kt_last_error(const kt_ctx* ctx);
+void kt_free(kt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

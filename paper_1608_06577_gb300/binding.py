@@ -1,0 +1,222 @@
+"""ctypes binding of libkt (include/kt.h): argument marshalling only.
+
+Device memory comes from torch (the state arena is one torch uint8 tensor) and work is
+enqueued on torch's current CUDA stream.  Loading fails loudly when libkt.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+KT_OK = 0
+ERRORS = {-1: "KT_ERR_ARG", -2: "KT_ERR_CUDA", -3: "KT_ERR_OOM", -4: "KT_ERR_EOS", -5: "KT_ERR_STATE",
+          -6: "KT_ERR_INVERSION", -7: "KT_ERR_NONFINITE"}
+KT_FP64, KT_MIXED = 0, 1
+KT_INV_PLAIN, KT_INV_LEARNED = 0, 1
+MLP_NPARAM = 32 * 6 + 32 + 32 * 32 + 32 + 32 + 1
+
+
+class KTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("neta", C.c_int)]
+
+
+class Eos(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.c_double), ("n", C.c_int),
+                ("e", C.POINTER(C.c_double)), ("p", C.POINTER(C.c_double)), ("cs2", C.POINTER(C.c_double)),
+                ("T", C.POINTER(C.c_double)), ("lndelta", C.POINTER(C.c_double))]
+
+
+class Coef(C.Structure):
+    _fields_ = [("kind", C.c_int), ("c0", C.c_double), ("c1", C.c_double), ("c2", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("theta_limiter", C.c_double), ("coords", C.c_int), ("bc", C.c_int), ("precision", C.c_int),
+                ("inversion", C.c_int), ("tau_pipi_on", C.c_int), ("regulate", C.c_int), ("rho_max", C.c_double),
+                ("xi0", C.c_double), ("e_min", C.c_double), ("tau_relax_min", C.c_double),
+                ("stream", C.c_void_p), ("arena", C.c_void_p), ("arena_bytes", C.c_size_t),
+                ("mlp_weights", C.POINTER(C.c_float)), ("use_graph", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("tau", C.c_double), ("steps", C.c_longlong), ("max_speed", C.c_float), ("status", C.c_uint),
+                ("newton_iters", C.c_longlong), ("fallbacks", C.c_longlong), ("regulated", C.c_longlong)]
+
+
+def lib_path() -> str:
+    return os.path.join(HERE, "libkt.so")
+
+
+def load_library():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run paper_1608_06577_gb300.build.build() "
+                           "(libkt has no CPU fallback)")
+    L = C.CDLL(path)
+    dp, vp = C.POINTER(C.c_double), C.c_void_p
+    L.kt_options_default.argtypes = [C.POINTER(Options)]
+    L.kt_state_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Options), C.POINTER(C.c_size_t)]
+    L.kt_init.argtypes = [C.POINTER(vp), C.POINTER(Grid), C.c_double, C.c_double, C.c_double, C.POINTER(Eos),
+                          C.POINTER(Coef), C.POINTER(Coef), C.POINTER(Options)]
+    L.kt_set_state.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, C.c_int]
+    L.kt_step.argtypes = [vp, C.c_int]
+    L.kt_get_state.argtypes = [vp, dp, vp, vp, vp, vp, vp, C.c_int]
+    L.kt_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.kt_last_error.restype = C.c_char_p
+    L.kt_last_error.argtypes = [vp]
+    L.kt_free.argtypes = [vp]
+    L.kt_free.restype = None
+    _LIB = L
+    return L
+
+
+def _dptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _coef(t):
+    kind = {"const": 0, "gauss": 1}[t[0]]
+    return Coef(kind, float(t[1]), float(t[2]), float(t[3]))
+
+
+class KT:
+    """One libkt context for a problem description (a workload.Problem or a compatible object)."""
+
+    def __init__(self, prob, precision: int = KT_FP64, inversion: int = KT_INV_PLAIN, mlp_weights=None,
+                 use_graph: bool = True, device_arena: bool = True):
+        import torch
+        self.torch = torch
+        L = load_library()
+        self.prob = prob
+        self.ncells = prob.nx * prob.ny * prob.neta
+        g = Grid(prob.nx, prob.ny, prob.neta)
+        o = Options()
+        L.kt_options_default(C.byref(o))
+        o.theta_limiter = prob.theta
+        o.coords = 0 if prob.coords == "milne" else 1
+        o.bc = 0 if prob.bc == "copy" else 1
+        o.precision = precision
+        o.inversion = inversion
+        o.tau_pipi_on = int(bool(prob.tau_pipi_on))
+        o.regulate = int(bool(prob.regulate))
+        o.rho_max, o.xi0 = prob.rho_max, prob.xi0
+        o.e_min, o.tau_relax_min = prob.e_min, prob.tau_relax_min
+        o.use_graph = int(bool(use_graph))
+        self.stream = torch.cuda.current_stream()
+        o.stream = C.c_void_p(self.stream.cuda_stream)
+        self._keep = []
+        if mlp_weights is not None:
+            w = np.ascontiguousarray(mlp_weights, dtype=np.float32)
+            assert w.size == MLP_NPARAM
+            self._keep.append(w)
+            o.mlp_weights = w.ctypes.data_as(C.POINTER(C.c_float))
+        if device_arena:
+            nb = C.c_size_t()
+            rc = L.kt_state_bytes(C.byref(g), C.byref(o), C.byref(nb))
+            if rc != KT_OK:
+                raise KTError(rc, "kt_state_bytes")
+            self.arena = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+            o.arena, o.arena_bytes = C.c_void_p(self.arena.data_ptr()), nb.value
+        if isinstance(prob.eos, tuple):
+            eos = Eos(0, float(prob.eos[1]), 0, None, None, None, None, None)
+        else:
+            t = prob.eos
+            cols = [np.ascontiguousarray(a, dtype=np.float64) for a in (t.e, t.p, t.cs2, t.T, t.lndelta)]
+            self._keep += cols
+            P = C.POINTER(C.c_double)
+            eos = Eos(1, 0.0, t.n, *[a.ctypes.data_as(P) for a in cols])
+        ce, cz = _coef(prob.eta_over_s), _coef(prob.zeta_over_s)
+        ctx = C.c_void_p()
+        rc = L.kt_init(C.byref(ctx), C.byref(g), prob.dx, prob.deta, prob.dtau, C.byref(eos), C.byref(ce),
+                       C.byref(cz), C.byref(o))
+        if rc != KT_OK:
+            raise KTError(rc, "kt_init failed")
+        self.ctx = ctx
+        self.L = L
+
+    def _check(self, rc, what):
+        if rc != KT_OK:
+            raise KTError(rc, f"{what}: {self.L.kt_last_error(self.ctx).decode()}")
+        return rc
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None):
+                self.L.kt_free(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------------------- state
+    def set_state(self, tau, e, u=None, pi=None, Pi=None, u_prev=None):
+        """Host numpy arrays (physical cells, x fastest) or CUDA torch tensors."""
+        torch = self.torch
+        arrs = [e, u, pi, Pi, u_prev]
+        on_dev = any(isinstance(a, torch.Tensor) and a.is_cuda for a in arrs if a is not None)
+        if on_dev:
+            torch.cuda.synchronize()  # inputs produced on torch's streams must be complete
+        ptrs = []
+        keep = []
+        for a in arrs:
+            if a is None:
+                ptrs.append(None)
+            elif on_dev:
+                t = a.to(dtype=torch.float64).contiguous()
+                keep.append(t)
+                ptrs.append(C.c_void_p(t.data_ptr()))
+            else:
+                h = np.ascontiguousarray(a, dtype=np.float64)
+                keep.append(h)
+                ptrs.append(_dptr(h))
+        rc = self.L.kt_set_state(self.ctx, float(tau), *ptrs, int(on_dev))
+        return self._check(rc, "kt_set_state")
+
+    def set_problem_state(self):
+        p = self.prob
+        return self.set_state(p.tau0, p.e, p.u, p.pi, p.Pi, p.u_prev)
+
+    def step(self, n=1, check=True):
+        rc = self.L.kt_step(self.ctx, int(n))
+        if check:
+            self._check(rc, "kt_step")
+        return rc
+
+    def get_state(self, fields=("e", "u", "pi", "Pi", "q")):
+        N = self.ncells
+        out = {}
+        shapes = {"e": (N,), "u": (4, N), "pi": (10, N), "Pi": (N,), "q": (15, N)}
+        for f in ("e", "u", "pi", "Pi", "q"):
+            out[f] = np.empty(shapes[f]) if f in fields else None
+        tau = C.c_double()
+        rc = self.L.kt_get_state(self.ctx, C.byref(tau), *[_dptr(out[f]) for f in ("e", "u", "pi", "Pi", "q")], 0)
+        self._check(rc, "kt_get_state")
+        out["tau"] = tau.value
+        return out
+
+    def get_state_device(self, e=None, u=None, pi=None, Pi=None, q=None):
+        """Copy into preallocated CUDA float64 tensors (any may be None)."""
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())  # noqa: E731
+        self.torch.cuda.synchronize()
+        tau = C.c_double()
+        rc = self.L.kt_get_state(self.ctx, C.byref(tau), ptr(e), ptr(u), ptr(pi), ptr(Pi), ptr(q), 1)
+        self._check(rc, "kt_get_state")
+        return tau.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.L.kt_get_stats(self.ctx, C.byref(s)), "kt_get_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}

@@ -1,0 +1,575 @@
+// kt_abi.cu -- host side of libkt: the C ABI declared in include/kt.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/kt.h"
+#include "kt_stage.cuh"
+
+using namespace kt;
+
+namespace {
+
+constexpr int KSTAT_WORDS = 8;  // device stats block: status, max speed bits, pad, 3 counters
+
+struct Ctx {
+  kt_options opt;
+  Params P;
+  int mixed;             // 1: float u, e, p and float stencil
+  size_t esz;            // bytes per u/e/p element
+  cudaStream_t stream;
+  bool own_stream = false;
+  // device memory
+  void* base = nullptr;  // owned allocation (null if caller arena)
+  size_t bytes = 0;
+  double* q = nullptr;   // 15 fields
+  double* qs = nullptr;  // 15 fields
+  void* U[3] = {};       // 3 x 4 fields
+  void* E[2] = {};
+  void* Pb[2] = {};
+  double* stage = nullptr;  // staging: 18 packed fields
+  EosSeg<double>* seg_d = nullptr;
+  EosSeg<float>* seg_f = nullptr;
+  double* d_tau = nullptr;
+  unsigned* d_stat = nullptr;  // [0] status [1] max speed bits [2..] counters (u64 aligned at +4 words)
+  float* d_mlp = nullptr;
+  int cur = 0, prev = 1, spare = 2;
+  double tau = 0.0;
+  long long steps = 0;
+  bool have_state = false;
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // 3-step graph per rotation phase
+  kt_stats last{};
+  char err[512] = {0};
+};
+
+int fail(Ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(c, KT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+Lattice make_lattice(const kt_grid* g) {
+  Lattice L;
+  L.nx = g->nx; L.ny = g->ny; L.nz = g->neta;
+  L.pitch = (int)align_up((size_t)g->nx + 4, 4);
+  L.NY = g->ny + 4;
+  L.NZ = g->neta + 4;
+  L.plane = (long long)L.pitch * L.NY;
+  L.fstride = (long long)align_up((size_t)(L.plane * L.NZ), 32);
+  return L;
+}
+
+size_t state_bytes(const Lattice& L, int mixed, int eos_n) {
+  size_t fs = (size_t)L.fstride;
+  size_t es = mixed ? 4 : 8;
+  size_t b = 0;
+  b += align_up(30 * fs * 8, 256);             // q, qs
+  b += align_up(12 * fs * es, 256);            // U[3]
+  b += align_up(4 * fs * es, 256);             // E[2], P[2]
+  size_t ncell = (size_t)L.nx * L.ny * L.nz;
+  b += align_up(18 * ncell * 8, 256);          // staging
+  b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(EosSeg<double>), 256);
+  b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(EosSeg<float>), 256);
+  b += 256;                                    // tau
+  b += 256;                                    // stats
+  b += align_up(KT_MLP_NPARAM * 4, 256);       // MLP weights
+  return b;
+}
+
+void coef_from(Coef& d, const kt_coef* s) {
+  d.kind = s ? s->kind : KT_COEF_CONST;
+  d.c0 = s ? s->c0 : 0.0;
+  d.c1 = s ? s->c1 : 0.0;
+  d.c2 = s ? s->c2 : 1.0;
+  d.ln_c0 = (d.c0 > 0.0) ? std::log(d.c0) : -INFINITY;
+}
+
+// Per-interval cubic coefficients of the table EOS (see kt_eos in kt.h).
+template <typename R>
+void build_segments(const kt_eos* eos, std::vector<EosSeg<R>>& out) {
+  int n = eos->n;
+  out.resize(n);
+  for (int i = 0; i + 1 < n; ++i) {
+    double e0 = eos->e[i], e1 = eos->e[i + 1];
+    double de = e1 - e0;
+    double P0 = eos->p[i], P1 = eos->p[i + 1];
+    double m0 = eos->cs2[i] * de, m1 = eos->cs2[i + 1] * de;
+    double T0 = eos->T[i], T1 = eos->T[i + 1];
+    double s0 = eos->cs2[i] * T0 / (e0 + P0) * de, s1 = eos->cs2[i + 1] * T1 / (e1 + P1) * de;
+    EosSeg<R> s;
+    s.e0 = (R)e0; s.inv_de = (R)(1.0 / de);
+    s.P0 = (R)P0; s.mP = (R)m0; s.cP2 = (R)(3.0 * (P1 - P0) - 2.0 * m0 - m1); s.cP3 = (R)(2.0 * (P0 - P1) + m0 + m1);
+    s.T0 = (R)T0; s.mT = (R)s0; s.cT2 = (R)(3.0 * (T1 - T0) - 2.0 * s0 - s1); s.cT3 = (R)(2.0 * (T0 - T1) + s0 + s1);
+    s.l0 = (R)eos->lndelta[i]; s.dl = (R)(eos->lndelta[i + 1] - eos->lndelta[i]);
+    out[i] = s;
+  }
+  out[n - 1] = out[n - 2];
+  out[n - 1].e0 = (R)eos->e[n - 1];  // sentinel: only its e0 is read by the interval search
+}
+
+// ------------------------------------------------------------------ small kernels
+__device__ __forceinline__ double gnn_at(const Params& P, double tau) { return P.milne ? tau * tau : 1.0; }
+
+template <typename R>
+__global__ void set_state_kernel(const Params P, const double* __restrict__ in, int has_u, int has_pi, int has_Pi,
+                                 int has_up, double tau, double* q, R* U, R* Up, R* E, R* Pb, unsigned* status) {
+  const Lattice& L = P.L;
+  long long ncp = (long long)L.nx * L.ny * L.nz;
+  long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= ncp) return;
+  int i = (int)(o % L.nx), j = (int)((o / L.nx) % L.ny), k = (int)(o / ((long long)L.nx * L.ny));
+  const double* pe = in;
+  const double* pu = in + ncp;
+  const double* ppi = in + 4 * ncp;
+  const double* pPi = in + 14 * ncp;
+  const double* pup = in + 15 * ncp;
+  double e = pe[o];
+  double ux = has_u ? pu[o] : 0.0, uy = has_u ? pu[ncp + o] : 0.0, un = has_u ? pu[2 * ncp + o] : 0.0;
+  double g = gnn_at(P, tau);
+  double ut = sqrt(1.0 + ux * ux + uy * uy + g * un * un);
+  double pi[10];
+  for (int m = 0; m < 10; ++m) pi[m] = has_pi ? ppi[m * ncp + o] : 0.0;
+  double Pi = has_Pi ? pPi[o] : 0.0;
+  double P0 = eos_P<double>(P, e);
+  double Pt = P0 + Pi;
+  double qn[NQ];
+  // Eqs. (Ttt), (Tti)
+  qn[0] = (e + Pt) * ut * ut - Pt + pi[0];
+  qn[1] = (e + Pt) * ut * ux + pi[1];
+  qn[2] = (e + Pt) * ut * uy + pi[2];
+  qn[3] = (e + Pt) * ut * un + pi[3];
+  for (int m = 0; m < 10; ++m) qn[4 + m] = pi[m];
+  qn[14] = Pi;
+  double u4[4] = {ut, ux, uy, un}, up4[4];
+  if (has_up) {
+    double px = pup[o], py = pup[ncp + o], pn = pup[2 * ncp + o];
+    double gp = gnn_at(P, tau - P.dtau);
+    up4[0] = sqrt(1.0 + px * px + py * py + gp * pn * pn); up4[1] = px; up4[2] = py; up4[3] = pn;
+  } else {
+    for (int m = 0; m < 4; ++m) up4[m] = u4[m];
+  }
+  bool bad = !isfinite(e) || !(e >= 0.0) || !isfinite(ut) || !isfinite(Pi) || !isfinite(up4[0]);
+  for (int m = 0; m < 10; ++m) bad |= !isfinite(pi[m]);
+  if (bad) atomicOr(status, ST_NONFINITE);
+  // store own cell and the ghosts it owns
+  const long long fs = L.fstride;
+  const int pc[3] = {i + 2, j + 2, k + 2};
+  const int nn[3] = {L.nx, L.ny, L.nz};
+  for (int t = -1; t < 12; ++t) {
+    int ii = pc[0], jj = pc[1], kk = pc[2];
+    if (t >= 0) {
+      int ax = t / 4, gi = t % 4, n = nn[ax];
+      int gpos = (gi < 2) ? gi : n + gi;
+      if (ghost_source(gpos, n, P.periodic) != pc[ax]) continue;
+      if (ax == 0) ii = gpos; else if (ax == 1) jj = gpos; else kk = gpos;
+    }
+    long long c = L.idx(ii, jj, kk);
+    for (int n = 0; n < NQ; ++n) q[n * fs + c] = qn[n];
+    for (int m = 0; m < 4; ++m) { U[m * fs + c] = (R)u4[m]; Up[m * fs + c] = (R)up4[m]; }
+    E[c] = (R)e;
+    Pb[c] = (R)P0;
+  }
+}
+
+// gather one padded field (double or float) into a packed physical array
+template <typename S>
+__global__ void gather_kernel(const Params P, const S* __restrict__ f, double* out) {
+  const Lattice& L = P.L;
+  long long ncp = (long long)L.nx * L.ny * L.nz;
+  long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= ncp) return;
+  int i = (int)(o % L.nx), j = (int)((o / L.nx) % L.ny), k = (int)(o / ((long long)L.nx * L.ny));
+  out[o] = (double)f[L.idx(i + 2, j + 2, k + 2)];
+}
+
+__global__ void advance_tau_kernel(double* tau, double dtau) { tau[0] += dtau; }
+
+// ------------------------------------------------------------------ launches
+template <typename R>
+StageIO<R> make_io(Ctx* c, int stage) {
+  StageIO<R> io;
+  const long long fs = c->P.L.fstride;
+  (void)fs;
+  R* U0 = (R*)c->U[c->cur];
+  R* Uprev = (R*)c->U[c->prev];
+  R* Usp = (R*)c->U[c->spare];
+  if (stage == 1) {
+    io.q_in = c->q; io.q_base = nullptr; io.q_out = c->qs;
+    io.u_in = U0; io.u_prev = Uprev; io.u_out = Uprev;        // u^* over u^{n-1}
+    io.e_in = (R*)c->E[0]; io.p_in = (R*)c->Pb[0];
+    io.e_out = (R*)c->E[1]; io.p_out = (R*)c->Pb[1];
+  } else {
+    io.q_in = c->qs; io.q_base = c->q; io.q_out = c->q;       // q^{n+1} over q^n
+    io.u_in = Uprev; io.u_prev = U0; io.u_out = Usp;          // u^{n+1} into the spare buffer
+    io.e_in = (R*)c->E[1]; io.p_in = (R*)c->Pb[1];
+    io.e_out = (R*)c->E[0]; io.p_out = (R*)c->Pb[0];
+  }
+  io.d_tau = c->d_tau;
+  io.status = c->d_stat;
+  io.max_speed_bits = c->d_stat + 1;
+  io.counters = (unsigned long long*)(c->d_stat + 4);
+  io.mlp = nullptr;
+  return io;
+}
+
+dim3 stage_block() { return dim3(32, 4, 2); }
+dim3 stage_grid(const Lattice& L) {
+  dim3 b = stage_block();
+  return dim3((L.nx + b.x - 1) / b.x, (L.ny + b.y - 1) / b.y, (L.nz + b.z - 1) / b.z);
+}
+
+// enqueue one full step (two stages + tau advance) for the current rotation phase, then rotate
+int enqueue_step(Ctx* c) {
+  dim3 g = stage_grid(c->P.L), b = stage_block();
+  if (c->mixed) {
+    stage_kernel<float, 1><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 1));
+    stage_kernel<float, 2><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 2));
+  } else {
+    stage_kernel<double, 1><<<g, b, 0, c->stream>>>(c->P, make_io<double>(c, 1));
+    stage_kernel<double, 2><<<g, b, 0, c->stream>>>(c->P, make_io<double>(c, 2));
+  }
+  advance_tau_kernel<<<1, 1, 0, c->stream>>>(c->d_tau, c->P.dtau);
+  // u^{n-1} <- u^n, u^n <- u^{n+1}; the old u^{n-1} buffer (holding u^*) becomes the spare
+  int ncur = c->spare, nprev = c->cur, nspare = c->prev;
+  c->cur = ncur; c->prev = nprev; c->spare = nspare;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, KT_ERR_CUDA, "stage launch: %s", cudaGetErrorString(e));
+  return KT_OK;
+}
+
+int phase_of(const Ctx* c) {
+  // three rotation phases, identified by which buffer is current
+  return c->cur;
+}
+
+int build_graph(Ctx* c, int phase) {
+  int save[3] = {c->cur, c->prev, c->spare};
+  cudaGraph_t gr;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = KT_OK;
+  for (int s = 0; s < 3 && rc == KT_OK; ++s) rc = enqueue_step(c);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
+  c->cur = save[0]; c->prev = save[1]; c->spare = save[2];
+  if (rc != KT_OK) return rc;
+  if (e != cudaSuccess) return fail(c, KT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph[phase], gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(c, KT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return KT_OK;
+}
+
+}  // namespace
+
+struct kt_ctx : Ctx {};
+
+// ==================================================================== C ABI
+extern "C" {
+
+int kt_options_default(kt_options* o) {
+  if (!o) return KT_ERR_ARG;
+  memset(o, 0, sizeof(*o));
+  o->theta_limiter = 1.0;
+  o->coords = KT_MILNE;
+  o->bc = KT_BC_COPY;
+  o->precision = KT_FP64;
+  o->inversion = KT_INV_PLAIN;
+  o->tau_pipi_on = 1;
+  o->regulate = 1;
+  o->rho_max = 1.0;
+  o->xi0 = 0.1;
+  o->e_min = 0.0;
+  o->tau_relax_min = 0.0;
+  o->use_graph = 1;
+  return KT_OK;
+}
+
+int kt_state_bytes(const kt_grid* grid, const kt_options* opt, size_t* bytes) {
+  if (!grid || !bytes || grid->nx < 1 || grid->ny < 1 || grid->neta < 1) return KT_ERR_ARG;
+  kt_options d;
+  kt_options_default(&d);
+  const kt_options* o = opt ? opt : &d;
+  *bytes = state_bytes(make_lattice(grid), o->precision == KT_MIXED, 4097);
+  return KT_OK;
+}
+
+int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dtau, const kt_eos* eos,
+            const kt_coef* eta_over_s, const kt_coef* zeta_over_s, const kt_options* opt) {
+  if (!out) return KT_ERR_ARG;
+  *out = nullptr;
+  kt_ctx* c = new (std::nothrow) kt_ctx();
+  if (!c) return KT_ERR_OOM;
+  auto bail = [&](int code) { kt_free(c); return code; };
+  if (!grid || grid->nx < 1 || grid->ny < 1 || grid->neta < 1 || !(dx > 0) || !(deta > 0) || !(dtau > 0) || !eos) {
+    fprintf(stderr, "kt_init: invalid grid, spacing or eos\n");
+    return bail(KT_ERR_ARG);
+  }
+  if (opt) c->opt = *opt; else kt_options_default(&c->opt);
+  const kt_options& o = c->opt;
+  if (o.precision != KT_FP64 && o.precision != KT_MIXED) return bail(KT_ERR_ARG);
+  if (!(o.theta_limiter >= 1.0 && o.theta_limiter <= 2.0)) return bail(KT_ERR_ARG);
+  if (o.coords != KT_MILNE && o.coords != KT_CARTESIAN) return bail(KT_ERR_ARG);
+  if (o.bc != KT_BC_COPY && o.bc != KT_BC_PERIODIC) return bail(KT_ERR_ARG);
+  if (o.inversion == KT_INV_LEARNED && !o.mlp_weights) return bail(KT_ERR_ARG);
+  c->mixed = (o.precision == KT_MIXED);
+  c->esz = c->mixed ? 4 : 8;
+
+  Params& P = c->P;
+  memset(&P, 0, sizeof(P));
+  P.L = make_lattice(grid);
+  P.dx = dx; P.dy = dx; P.deta = deta; P.dtau = dtau;
+  P.theta = o.theta_limiter;
+  P.milne = (o.coords == KT_MILNE);
+  P.periodic = (o.bc == KT_BC_PERIODIC);
+  coef_from(P.eta, eta_over_s);
+  coef_from(P.zeta, zeta_over_s);
+  P.eos_table = (eos->kind == KT_EOS_TABLE);
+  P.eos_a = eos->a;
+  if (eos->kind == KT_EOS_TABLE) {
+    if (eos->n < 4 || !eos->e || !eos->p || !eos->cs2 || !eos->T || !eos->lndelta) return bail(KT_ERR_EOS);
+    for (int i = 0; i + 1 < eos->n; ++i)
+      if (!(eos->e[i + 1] > eos->e[i]) || !(eos->e[i] > 0)) return bail(KT_ERR_EOS);
+    P.eos_n = eos->n;
+    P.lne0 = (float)std::log(eos->e[0]);
+    P.inv_h = (float)((eos->n - 1) / (std::log(eos->e[eos->n - 1]) - std::log(eos->e[0])));
+  } else if (eos->kind == KT_EOS_CONFORMAL) {
+    if (!(eos->a > 0)) return bail(KT_ERR_EOS);
+    P.eos_n = 0;
+  } else {
+    return bail(KT_ERR_EOS);
+  }
+  P.shear_on = !(P.eta.kind == KT_COEF_CONST && P.eta.c0 == 0.0);
+  P.bulk_on = !(P.zeta.kind == KT_COEF_CONST && P.zeta.c0 == 0.0) && P.eos_table;
+  P.tpp = o.tau_pipi_on ? 10.0 / 7.0 : 0.0;
+  P.regulate = o.regulate;
+  P.rho_max = o.rho_max;
+  P.xi0 = o.xi0;
+  P.e_min = o.e_min;
+  P.rate_max = (o.tau_relax_min > 0) ? 1.0 / o.tau_relax_min : INFINITY;
+  P.ln_rate_max = std::log(P.rate_max);
+
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+    fail(c, KT_ERR_CUDA, "no CUDA device");
+    fprintf(stderr, "kt_init: no CUDA device (libkt has no CPU fallback)\n");
+    return bail(KT_ERR_CUDA);
+  }
+
+  // every call synchronises its stream before returning, so a context-owned stream is safe when
+  // the caller passes none (the legacy default stream cannot be captured into a graph)
+  c->stream = (cudaStream_t)o.stream;
+  if (!c->stream) {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      fail(c, KT_ERR_CUDA, "stream creation failed");
+      return bail(KT_ERR_CUDA);
+    }
+    c->own_stream = true;
+  }
+
+  // ---- device memory, carved from one block
+  size_t need = state_bytes(P.L, c->mixed, P.eos_n);
+  char* base;
+  if (o.arena) {
+    if (o.arena_bytes < need) return bail(KT_ERR_OOM);
+    base = (char*)o.arena;
+  } else {
+    if (cudaMalloc(&c->base, need) != cudaSuccess) { cudaGetLastError(); return bail(KT_ERR_OOM); }
+    base = (char*)c->base;
+  }
+  c->bytes = need;
+  size_t off = 0;
+  auto carve = [&](size_t b) { void* p = base + off; off += align_up(b, 256); return p; };
+  const size_t fs = (size_t)P.L.fstride;
+  char* qq = (char*)carve(30 * fs * 8);
+  c->q = (double*)qq;
+  c->qs = (double*)(qq + 15 * fs * 8);
+  char* uu = (char*)carve(12 * fs * c->esz);
+  for (int b = 0; b < 3; ++b) c->U[b] = uu + (size_t)b * 4 * fs * c->esz;
+  char* ep = (char*)carve(4 * fs * c->esz);
+  c->E[0] = ep; c->E[1] = ep + fs * c->esz; c->Pb[0] = ep + 2 * fs * c->esz; c->Pb[1] = ep + 3 * fs * c->esz;
+  size_t ncell = (size_t)P.L.nx * P.L.ny * P.L.nz;
+  c->stage = (double*)carve(18 * ncell * 8);
+  int nseg = P.eos_n > 0 ? P.eos_n : 1;
+  c->seg_d = (EosSeg<double>*)carve(nseg * sizeof(EosSeg<double>));
+  c->seg_f = (EosSeg<float>*)carve(nseg * sizeof(EosSeg<float>));
+  c->d_tau = (double*)carve(256);
+  c->d_stat = (unsigned*)carve(256);
+  c->d_mlp = (float*)carve(KT_MLP_NPARAM * 4);
+  P.seg_d = c->seg_d;
+  P.seg_f = c->seg_f;
+
+  CK(cudaMemsetAsync(qq, 0, 30 * fs * 8, c->stream));
+  CK(cudaMemsetAsync(ep, 0, 4 * fs * c->esz, c->stream));
+  // unused corner ghosts hold a fluid at rest (u^tau = 1); they are never read
+  {
+    std::vector<unsigned char> one(4 * fs * c->esz, 0);
+    for (size_t i = 0; i < fs; ++i) {
+      if (c->mixed) { float v = 1.f; memcpy(&one[i * 4], &v, 4); }
+      else { double v = 1.0; memcpy(&one[i * 8], &v, 8); }
+    }
+    for (int b = 0; b < 3; ++b) CK(cudaMemcpyAsync(c->U[b], one.data(), one.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync((char*)c->U[0] + fs * c->esz, 0, 3 * fs * c->esz, c->stream));
+    CK(cudaMemsetAsync((char*)c->U[1] + fs * c->esz, 0, 3 * fs * c->esz, c->stream));
+    CK(cudaMemsetAsync((char*)c->U[2] + fs * c->esz, 0, 3 * fs * c->esz, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (P.eos_table) {
+    std::vector<EosSeg<double>> sd;
+    std::vector<EosSeg<float>> sf;
+    build_segments<double>(eos, sd);
+    build_segments<float>(eos, sf);
+    CK(cudaMemcpyAsync(c->seg_d, sd.data(), sd.size() * sizeof(sd[0]), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->seg_f, sf.data(), sf.size() * sizeof(sf[0]), cudaMemcpyHostToDevice, c->stream));
+  }
+  if (o.mlp_weights) {
+    CK(cudaMemcpyAsync(c->d_mlp, o.mlp_weights, KT_MLP_NPARAM * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = c;
+  return KT_OK;
+}
+
+int kt_set_state(kt_ctx* c, double tau, const double* e, const double* u, const double* pi, const double* Pi,
+                 const double* u_prev, int on_device) {
+  if (!c || !e || !(tau > 0 || !c->P.milne)) return c ? fail(c, KT_ERR_ARG, "kt_set_state: bad argument") : KT_ERR_ARG;
+  const Lattice& L = c->P.L;
+  size_t ncp = (size_t)L.nx * L.ny * L.nz;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  double* s = c->stage;
+  CK(cudaMemcpyAsync(s, e, ncp * 8, kind, c->stream));
+  if (u) CK(cudaMemcpyAsync(s + ncp, u, 3 * ncp * 8, kind, c->stream));
+  if (pi) CK(cudaMemcpyAsync(s + 4 * ncp, pi, 10 * ncp * 8, kind, c->stream));
+  if (Pi) CK(cudaMemcpyAsync(s + 14 * ncp, Pi, ncp * 8, kind, c->stream));
+  if (u_prev) CK(cudaMemcpyAsync(s + 15 * ncp, u_prev, 3 * ncp * 8, kind, c->stream));
+  CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
+  double tau_h = tau;
+  CK(cudaMemcpyAsync(c->d_tau, &tau_h, 8, cudaMemcpyHostToDevice, c->stream));
+  c->cur = 0; c->prev = 1; c->spare = 2;
+  int nb = (int)((ncp + 255) / 256);
+  if (c->mixed)
+    set_state_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, s, u != nullptr, pi != nullptr, Pi != nullptr,
+                                                       u_prev != nullptr, tau, c->q, (float*)c->U[0], (float*)c->U[1],
+                                                       (float*)c->E[0], (float*)c->Pb[0], c->d_stat);
+  else
+    set_state_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, s, u != nullptr, pi != nullptr, Pi != nullptr,
+                                                        u_prev != nullptr, tau, c->q, (double*)c->U[0], (double*)c->U[1],
+                                                        (double*)c->E[0], (double*)c->Pb[0], c->d_stat);
+  CK(cudaGetLastError());
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, c->d_stat, 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->tau = tau;
+  c->steps = 0;
+  c->have_state = true;
+  if (st) return fail(c, KT_ERR_STATE, "kt_set_state: non-finite or negative input");
+  return KT_OK;
+}
+
+int kt_step(kt_ctx* c, int n_steps) {
+  if (!c || n_steps < 0) return KT_ERR_ARG;
+  if (!c->have_state) return fail(c, KT_ERR_ARG, "kt_step: no state set");
+  CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
+  int done = 0;
+  if (c->opt.use_graph) {
+    while (n_steps - done >= 3) {
+      int ph = phase_of(c);
+      if (!c->graph[ph]) {
+        int rc = build_graph(c, ph);
+        if (rc != KT_OK) return rc;
+      }
+      CK(cudaGraphLaunch(c->graph[ph], c->stream));
+      // three steps return the rotation to the same phase
+      done += 3;
+    }
+  }
+  for (; done < n_steps; ++done) {
+    int rc = enqueue_step(c);
+    if (rc != KT_OK) return rc;
+  }
+  unsigned hst[KSTAT_WORDS];
+  CK(cudaMemcpyAsync(hst, c->d_stat, sizeof(hst), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int s = 0; s < n_steps; ++s) c->tau += c->P.dtau;
+  c->steps += n_steps;
+  unsigned long long cnt[2];
+  memcpy(cnt, &hst[4], sizeof(cnt));
+  c->last.status = hst[0];
+  float ms;
+  memcpy(&ms, &hst[1], 4);
+  c->last.max_speed = ms;
+  c->last.newton_iters = (long long)cnt[0];
+  c->last.regulated = (long long)cnt[1];
+  if (hst[0] & ST_NONFINITE) return fail(c, KT_ERR_NONFINITE, "kt_step: non-finite value");
+  if (hst[0] & ST_INVERSION) return fail(c, KT_ERR_INVERSION, "kt_step: inversion failed in some cell");
+  return KT_OK;
+}
+
+int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, double* Pi, double* q, int on_device) {
+  if (!c) return KT_ERR_ARG;
+  const Lattice& L = c->P.L;
+  size_t ncp = (size_t)L.nx * L.ny * L.nz;
+  const long long fs = L.fstride;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  int nb = (int)((ncp + 255) / 256);
+  // (source field, destination) pairs, gathered through the staging area in groups
+  struct Job { const void* f; int is_r; double* dst; };
+  std::vector<Job> jobs;
+  const char* Ucur = (const char*)c->U[c->cur];
+  if (e) jobs.push_back({c->E[0], 1, e});
+  if (u) for (int m = 0; m < 4; ++m) jobs.push_back({Ucur + (size_t)m * fs * c->esz, 1, u + m * ncp});
+  if (pi) for (int m = 0; m < 10; ++m) jobs.push_back({c->q + (size_t)(4 + m) * fs, 0, pi + m * ncp});
+  if (Pi) jobs.push_back({c->q + (size_t)14 * fs, 0, Pi});
+  if (q) for (int n = 0; n < NQ; ++n) jobs.push_back({c->q + (size_t)n * fs, 0, q + n * ncp});
+  for (size_t b = 0; b < jobs.size(); b += 18) {
+    size_t nj = std::min<size_t>(18, jobs.size() - b);
+    for (size_t t = 0; t < nj; ++t) {
+      const Job& jb = jobs[b + t];
+      double* dst = c->stage + t * ncp;
+      if (jb.is_r && c->mixed) gather_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, (const float*)jb.f, dst);
+      else gather_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, (const double*)jb.f, dst);
+    }
+    CK(cudaGetLastError());
+    for (size_t t = 0; t < nj; ++t) CK(cudaMemcpyAsync(jobs[b + t].dst, c->stage + t * ncp, ncp * 8, kind, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (tau) *tau = c->tau;
+  return KT_OK;
+}
+
+int kt_get_stats(kt_ctx* c, kt_stats* s) {
+  if (!c || !s) return KT_ERR_ARG;
+  *s = c->last;
+  s->tau = c->tau;
+  s->steps = c->steps;
+  return KT_OK;
+}
+
+const char* kt_last_error(const kt_ctx* c) { return c ? c->err : "null context"; }
+
+void kt_free(kt_ctx* c) {
+  if (!c) return;
+  for (int p = 0; p < 3; ++p)
+    if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+  if (c->base) cudaFree(c->base);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,451 @@
+// kt_stage.cuh -- the fused KT + Heun stage kernel (one launch per Runge-Kutta stage).
+//
+// One thread owns one physical cell and performs, in order (Sec. 4.3 steps 1-4 / 5-8):
+//   a) for x, y, eta: generalised-minmod slopes of the 15 conserved components and of u^tau,
+//      u^d on the 5-point stencil; half-cell extrapolations; local speeds a = max(|v+|,|v-|);
+//      central-upwind fluxes at both faces; -(H_{i+1/2} - H_{i-1/2})/dx       (Eqs. Hflux, ax)
+//   b) the source vector J = S + G of App. B: central differences of v P - v pi^{tau nu} +
+//      pi^{d nu}, the geometric terms, and the relaxation sources built from theta, D u,
+//      sigma, omega (App. A) with the coefficients of Eqs. (betaPi)-(lambdapiPi)
+//   c) the Heun update in FP64: q* = q + dtau C[q]   or   q^{n+1} = (q^n + q* + dtau C[q*])/2
+//   d) the FP64 inversion T^{tau mu} -> (e, u^mu) of Eq. (eInferred) at tau^{n+1}
+//   e) the regulator of Eq. (regPimunu)
+//   f) stores, including the ghost copies owned by boundary cells (Eqs. ghostCells_1/2)
+// R is the arithmetic type of a) and b): double (KT_FP64) or float (KT_MIXED).
+#pragma once
+#include "kt_device.cuh"
+
+namespace kt {
+
+template <typename R>
+struct StageIO {
+  const double* q_in;    // 15 fields, stencil input (q^n or q^*)
+  const double* q_base;  // stage 2: q^n, read at the own cell only (aliases q_out)
+  double* q_out;
+  const R* u_in;         // 4 fields, stencil input (u^n or u^*)
+  const R* u_prev;       // 4 fields, own cell only: u^{n-1} (stage 1) or u^n (stage 2)
+  R* u_out;              // may alias u_prev (own cell only)
+  const R* e_in;
+  const R* p_in;
+  R* e_out;
+  R* p_out;
+  const double* d_tau;   // tau^n
+  unsigned* status;
+  unsigned* max_speed_bits;
+  unsigned long long* counters;  // [0] Newton iterations, [1] regulated cells, [2] fallbacks
+  const float* mlp;      // learned start (null: plain)
+};
+
+// ------------------------------------------------------------------ one direction of a)
+template <typename R, int D>
+__device__ __forceinline__ void direction_pass(const Params& P, const StageIO<R>& io, long long c, R gnn,
+                                               R tau, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax) {
+  const Lattice& L = P.L;
+  const long long fs = L.fstride;
+  const long long s = (D == 0) ? 1LL : ((D == 1) ? (long long)L.pitch : L.plane);
+  const R invD = (D == 0) ? R(1.0 / P.dx) : ((D == 1) ? R(1.0 / P.dy) : R(1.0 / P.deta));
+  const R hinv = R(0.5) * invD;
+  const R th = R(P.theta);
+  const R* u = io.u_in;
+
+  // u^mu on the stencil
+  R um1[4], up1[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    um1[m] = ld<R>(u + m * fs, c - s);
+    up1[m] = ld<R>(u + m * fs, c + s);
+  }
+  R u0t = ld<R>(u, c), u0d = ld<R>(u + (D + 1) * fs, c);
+  R um2t = ld<R>(u, c - 2 * s), um2d = ld<R>(u + (D + 1) * fs, c - 2 * s);
+  R up2t = ld<R>(u, c + 2 * s), up2d = ld<R>(u + (D + 1) * fs, c + 2 * s);
+  // face states of u^tau and u^d; faces L = i-1/2, R = i+1/2; m = left state, p = right state
+  R st_m = limited_slope(um2t, um1[0], u0t, th), st_0 = limited_slope(um1[0], u0t, up1[0], th),
+    st_p = limited_slope(u0t, up1[0], up2t, th);
+  R sd_m = limited_slope(um2d, um1[D + 1], u0d, th), sd_0 = limited_slope(um1[D + 1], u0d, up1[D + 1], th),
+    sd_p = limited_slope(u0d, up1[D + 1], up2d, th);
+  const R h = R(0.5);
+  R vLm = (um1[D + 1] + h * sd_m) / (um1[0] + h * st_m);
+  R vLp = (u0d - h * sd_0) / (u0t - h * st_0);
+  R vRm = (u0d + h * sd_0) / (u0t + h * st_0);
+  R vRp = (up1[D + 1] - h * sd_p) / (up1[0] - h * st_p);
+  R aL = fmax(fabs(vLp), fabs(vLm));
+  R aR = fmax(fabs(vRp), fabs(vRm));
+  amax = fmaxf(amax, (float)((D == 2) ? aR * sqrt(gnn) : aR));
+
+  // d_d u^mu and d_i v^i by central differences (Sec. 3.1)
+#pragma unroll
+  for (int m = 0; m < 4; ++m) du[D + 1][m] = (up1[m] - um1[m]) * hinv;
+  R vpl = up1[D + 1] / up1[0], vmi = um1[D + 1] / um1[0];
+  dv += (vpl - vmi) * hinv;
+
+  // S_c: -d_d (v^d P delta^nu_tau - g^{d nu} P - v^d pi^{tau nu} + pi^{d nu}), P = P0 + Pi
+  const double* q = io.q_in;
+  R Ppl = ld<R>(io.p_in, c + s) + ld<R>(q + 14 * fs, c + s);
+  R Pmi = ld<R>(io.p_in, c - s) + ld<R>(q + 14 * fs, c - s);
+  dq[0] -= (Ppl * vpl - Pmi * vmi) * hinv;
+  dq[D + 1] -= ((D == 2) ? (Ppl - Pmi) / gnn : (Ppl - Pmi)) * hinv;
+
+#pragma unroll
+  for (int n = 0; n < NQ; ++n) {
+    const double* qn = q + n * fs;
+    R a2 = ld<R>(qn, c - 2 * s), a1 = ld<R>(qn, c - s), a0 = ld<R>(qn, c), b1 = ld<R>(qn, c + s),
+      b2 = ld<R>(qn, c + 2 * s);
+    R sm = limited_slope(a2, a1, a0, th), s0 = limited_slope(a1, a0, b1, th), sp = limited_slope(a0, b1, b2, th);
+    R qLm = a1 + h * sm, qLp = a0 - h * s0, qRm = a0 + h * s0, qRp = b1 - h * sp;
+    // H = (F(q+) + F(q-))/2 - a (q+ - q-)/2 with F = v q (Eq. Hflux)
+    R HL = h * (vLp * qLp + vLm * qLm) - h * aL * (qLp - qLm);
+    R HR = h * (vRp * qRp + vRm * qRm) - h * aR * (qRp - qRm);
+    dq[n] -= (HR - HL) * invD;
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+      if (n == pix(0, nu)) dq[nu] += (vpl * b1 - vmi * a1) * hinv;
+      if (n == pix(D + 1, nu)) dq[nu] -= (b1 - a1) * hinv;
+    }
+  }
+  (void)tau;
+}
+
+// ------------------------------------------------------------ d) inversion, FP64 (Sec. 2.4)
+// f(e) = e - E + M^2/(E + P0(e) + Pi) = 0 by Newton-Raphson inside the bracket [lo, E],
+// with bisection whenever a step leaves it; stop at |de| <= 2^-50 E (at most 100 steps).
+__device__ __forceinline__ unsigned invert_fp64(const Params& P, double tau, const double (&qn)[NQ], double guess,
+                                                double& e, double& P0, double (&uo)[4], unsigned& iters) {
+  double E = qn[0] - qn[4];
+  double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
+  double Pi = qn[14];
+  double gnn = P.milne ? tau * tau : 1.0;
+  double M2 = fma(Mx, Mx, fma(My, My, gnn * Mn * Mn));
+  unsigned st = 0;
+  if (!(E > 0.0) || !isfinite(E) || !isfinite(M2) || !(M2 < E * E)) {
+    st = ST_INVERSION;
+    e = (P.e_min > 0.0) ? P.e_min : 1e-30;
+  } else if (!P.eos_table && (!P.bulk_on || Pi == 0.0)) {
+    double M = sqrt(M2);  // conformal closed form e = sqrt(4E^2 - 3M^2) - E, cancellation-free
+    e = 3.0 * (E - M) * (E + M) / (sqrt(fma(4.0 * E, E, -3.0 * M2)) + E);
+  } else {
+    double lo = (P.e_min > 0.0) ? P.e_min : 1e-300, hi = E;
+    e = (guess >= lo && guess <= hi) ? guess : hi;  // the cell's previous e, else E
+    int it;
+    for (it = 0; it < 100; ++it) {
+      double p0, c2;
+      eos_P_cs2<double>(P, e, p0, c2);
+      double A = E + p0 + Pi;
+      double rA = 1.0 / A;
+      double f = e - E + M2 * rA;
+      if (f == 0.0) break;
+      if (f < 0.0) lo = e; else hi = e;
+      double fp = 1.0 - M2 * c2 * rA * rA;
+      double en = e - f / fp;
+      if (!(en >= lo && en <= hi)) en = 0.5 * (lo + hi);
+      double de = fabs(en - e);
+      e = en;
+      if (de <= ldexp(E, -50)) { ++it; break; }  // f is known to about one ulp of E
+    }
+    iters += (unsigned)it;
+    if (it >= 100) st |= ST_INVERSION;
+  }
+  if (e < P.e_min) e = P.e_min;
+  P0 = eos_P<double>(P, e);
+  if (st) {
+    uo[0] = 1.0; uo[1] = uo[2] = uo[3] = 0.0;
+  } else {
+    double Pt = P0 + Pi;
+    double ut = sqrt((E + Pt) / (e + Pt));
+    double w = 1.0 / ((e + Pt) * ut);
+    uo[0] = ut; uo[1] = Mx * w; uo[2] = My * w; uo[3] = Mn * w;
+  }
+  if (!isfinite(e) || !isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3]))
+    st |= ST_NONFINITE;
+  return st;
+}
+
+// ------------------------------------------------------------ e) regulator (Sec. 3.2)
+template <typename R>
+__device__ __forceinline__ R regulator_factor(const Params& P, R gnn, R e, R P0, const R (&u)[4], const R (&pi)[4][4],
+                                              R Pi) {
+  const R glo[4] = {R(1), R(-1), R(-1), -gnn};
+  const R gup[4] = {R(1), R(-1), R(-1), R(-1) / gnn};
+  R PP = R(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      R X = Pi * (((a == b) ? gup[a] : R(0)) - u[a] * u[b]) + pi[a][b];
+      PP += X * X * glo[a] * glo[b];
+    }
+  if (!(PP > R(0))) return R(1);
+  R nPP = sqrt(PP);
+  R rho = nPP / (R(P.rho_max) * sqrt(e * e + R(3) * P0 * P0));
+  R den = R(1) / (R(P.xi0 * P.rho_max) * nPP);
+  R tr = pi[0][0] - pi[1][1] - pi[2][2] - gnn * pi[3][3];
+  rho = fmax(rho, fabs(tr) * den);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    R o = pi[l][0] * u[0] - pi[l][1] * u[1] - pi[l][2] * u[2] - gnn * pi[l][3] * u[3];
+    if (l == 3 && P.milne) o *= sqrt(gnn);
+    rho = fmax(rho, fabs(o) * den);
+  }
+  if (rho < R(1e-4)) return R(1) - rho * rho / R(3);
+  return tanh(rho) / rho;
+}
+
+// ---------------------------------------------------------------- f) stores with ghosts
+template <typename R>
+__device__ __forceinline__ void store_cell(const StageIO<R>& io, long long fs, long long t, const double (&qn)[NQ],
+                                           const double (&uo)[4], double e, double P0) {
+#pragma unroll
+  for (int n = 0; n < NQ; ++n) io.q_out[n * fs + t] = qn[n];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) io.u_out[m * fs + t] = (R)uo[m];
+  io.e_out[t] = (R)e;
+  io.p_out[t] = (R)P0;
+}
+
+// padded ghost coordinate g in {0, 1, n+2, n+3} that copies the physical padded coordinate p
+__device__ __forceinline__ int ghost_source(int g, int n, int periodic) {
+  if (periodic) return 2 + (((g - 2) % n) + n) % n;
+  return (g < 2) ? 2 : n + 1;
+}
+
+template <typename R>
+__device__ __forceinline__ void store_with_ghosts(const Params& P, const StageIO<R>& io, int i, int j, int k,
+                                                  const double (&qn)[NQ], const double (&uo)[4], double e, double P0) {
+  const Lattice& L = P.L;
+  const long long fs = L.fstride;
+  store_cell<R>(io, fs, L.idx(i, j, k), qn, uo, e, P0);
+  const int nn[3] = {L.nx, L.ny, L.nz};
+  const int pc[3] = {i, j, k};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    int n = nn[ax];
+    if (pc[ax] > 3 && pc[ax] < n) continue;  // interior cells own no ghost
+    const int gs[4] = {0, 1, n + 2, n + 3};
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (ghost_source(gs[g], n, P.periodic) != pc[ax]) continue;
+      int ii = (ax == 0) ? gs[g] : i, jj = (ax == 1) ? gs[g] : j, kk = (ax == 2) ? gs[g] : k;
+      store_cell<R>(io, fs, L.idx(ii, jj, kk), qn, uo, e, P0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- the stage kernel
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(256) stage_kernel(const Params P, const StageIO<R> io) {
+  const Lattice& L = P.L;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
+  unsigned st = 0, nit = 0, nreg = 0;
+  float amax = 0.f;
+
+  if (valid) {
+    const long long fs = L.fstride;
+    const long long c = L.idx(i + 2, j + 2, k + 2);
+    const double tau_n = io.d_tau[0];
+    const double tau_src = (STAGE == 1) ? tau_n : tau_n + P.dtau;
+    const double tau_out = tau_n + P.dtau;
+    const R tau = (R)tau_src;
+    const R gnn = P.milne ? tau * tau : R(1);
+
+    R dq[NQ];
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) dq[n] = R(0);
+    R du[4][4];
+    R dv = R(0);
+    direction_pass<R, 0>(P, io, c, gnn, tau, dq, du, dv, amax);
+    direction_pass<R, 1>(P, io, c, gnn, tau, dq, du, dv, amax);
+    direction_pass<R, 2>(P, io, c, gnn, tau, dq, du, dv, amax);
+
+    // ---- b) sources at the cell
+    R uc[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      uc[m] = ld<R>(io.u_in + m * fs, c);
+      du[0][m] = (uc[m] - ld<R>(io.u_prev + m * fs, c)) * R(1.0 / P.dtau);  // backward difference
+    }
+    const double* q = io.q_in;
+    R pi[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        pi[a][b] = ld<R>(q + pix(a, b) * fs, c);
+        pi[b][a] = pi[a][b];
+      }
+    const R Pic = ld<R>(q + 14 * fs, c);
+    const R ec = ld<R>(io.e_in, c), P0c = ld<R>(io.p_in, c);
+    const R Pt = P0c + Pic;
+    const R it = P.milne ? R(1) / tau : R(0);  // Gamma^eta_{tau eta}
+    const R tg = P.milne ? tau : R(0);         // Gamma^tau_{eta eta}
+
+    // geometric sources of the conservation laws, Eqs. (dT001)-(dT0i1)
+    {
+      R Tnn = (ec + Pt) * uc[3] * uc[3] + Pt / gnn + pi[3][3];
+      dq[0] -= ld<R>(q, c) * it + tg * Tnn;
+      dq[1] -= ld<R>(q + fs, c) * it;
+      dq[2] -= ld<R>(q + 2 * fs, c) * it;
+      dq[3] -= R(3) * ld<R>(q + 3 * fs, c) * it;
+    }
+
+    if (P.shear_on || P.bulk_on) {
+      const R glo[4] = {R(1), R(-1), R(-1), -gnn};
+      const R gup[4] = {R(1), R(-1), R(-1), R(-1) / gnn};
+      // u^mu_{;alpha}, alpha = 0..3 (only Gamma^eta_{tau eta} = 1/tau, Gamma^tau_{eta eta} = tau)
+      R cov[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        cov[0][a] = du[a][0] + ((a == 3) ? tg * uc[3] : R(0));
+        cov[1][a] = du[a][1];
+        cov[2][a] = du[a][2];
+        cov[3][a] = du[a][3] + ((a == 0) ? it * uc[3] : ((a == 3) ? it * uc[0] : R(0)));
+      }
+      const R theta = cov[0][0] + cov[1][1] + cov[2][2] + cov[3][3];
+      R Dup[4], Dlo[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        Dup[m] = uc[0] * cov[m][0] + uc[1] * cov[m][1] + uc[2] * cov[m][2] + uc[3] * cov[m][3];
+        Dlo[m] = glo[m] * Dup[m];
+      }
+      // nabla^a u^m = Delta^{a b} u^m_{;b} = g^{aa} u^m_{;a} - u^a D u^m
+      R nab[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) nab[a][m] = gup[a] * cov[m][a] - uc[a] * Dup[m];
+      R sig[4][4], om[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
+          sig[a][b] = R(0.5) * (nab[a][b] + nab[b][a]) - theta * Dab / R(3);
+          om[a][b] = R(0.5) * (nab[b][a] - nab[a][b]);  // App. A convention
+        }
+      R ps = R(0);  // pi^{mu nu} sigma_{mu nu}
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ps += pi[a][b] * sig[a][b] * glo[a] * glo[b];
+
+      // transport coefficients (Sec. 2.2) from T(e), ln(1/3 - c_s^2)(e)
+      R T, lnd;
+      eos_T_lnd<R>(P, ec, T, lnd);
+      const R iu0 = R(1) / uc[0];
+
+      if (P.shear_on) {
+        R eta_tp = (ec + P0c) * R(0.2);
+        R es = coef_value<R>(P.eta, T);
+        R rate_pi = (es > R(0)) ? T / (R(5) * es) : R(INFINITY);
+        rate_pi = fmin(rate_pi, R(P.rate_max));
+        const R tpp = R(P.tpp);
+        R av[4];  // pi^{mu lambda} D u_lambda
+#pragma unroll
+        for (int m = 0; m < 4; ++m) av[m] = pi[m][0] * Dlo[0] + pi[m][1] * Dlo[1] + pi[m][2] * Dlo[2] + pi[m][3] * Dlo[3];
+        // B^{mu nu} = pi^{mu l} g_ll omega^{nu l};  C^{mu nu} = pi^{mu l} g_ll sigma^{nu l}
+        R B[4][4], Cm[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            R sb = R(0), sc = R(0);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              sb += pi[a][l] * glo[l] * om[b][l];
+              sc += pi[a][l] * glo[l] * sig[b][l];
+            }
+            B[a][b] = sb;
+            Cm[a][b] = sc;
+          }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = a; b < 4; ++b) {
+            R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
+            R I1 = av[a] * uc[b] + av[b] * uc[a];
+            R I3 = B[a][b] + B[b][a];
+            R I4 = R(0.5) * (Cm[a][b] + Cm[b][a]) - Dab * ps / R(3);
+            R Ipi = I1 + R(4.0 / 3.0) * theta * pi[a][b] - I3 + tpp * I4 - R(1.2) * Pic * sig[a][b];
+            R S = (R(2) * eta_tp * sig[a][b] - rate_pi * pi[a][b] - Ipi) * iu0 + pi[a][b] * dv;
+            // -G^{ab}/u^tau with G^{ab} = u^c Gamma^a_{cd} pi^{db} + (a <-> b)
+            R ha = (a == 0) ? tg * uc[3] * pi[3][b] : ((a == 3) ? it * (uc[0] * pi[3][b] + uc[3] * pi[0][b]) : R(0));
+            R hb = (b == 0) ? tg * uc[3] * pi[3][a] : ((b == 3) ? it * (uc[0] * pi[3][a] + uc[3] * pi[0][a]) : R(0));
+            dq[pix(a, b)] += S - (ha + hb) * iu0;
+          }
+      }
+      if (P.bulk_on) {
+        R lrate = R(2.70805020110221) + R(2) * lnd + log(T) - coef_log<R>(P.zeta, T);  // ln 15 + ...
+        R rate_Pi = fmin(exp(lrate), R(P.rate_max));
+        R d = exp(lnd);
+        R zt = R(15) * d * d * (ec + P0c);
+        R IPi = R(2.0 / 3.0) * Pic * theta - R(1.6) * d * ps;
+        dq[14] += (-zt * theta - rate_Pi * Pic - IPi) * iu0 + Pic * dv;
+      }
+    }
+
+    // ---- c) Heun update in FP64 (Eqs. step1-finalStep)
+    double qn[NQ];
+    const double dt = P.dtau;
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) {
+      double w = fma(dt, (double)dq[n], __ldg(q + n * fs + c));
+      if (STAGE == 2) w = 0.5 * (io.q_base[n * fs + c] + w);
+      qn[n] = w;
+    }
+
+    // ---- d) inversion at tau^{n+1}
+    double e, P0, uo[4];
+    double guess = (double)ld<R>(io.e_in, c);
+    st |= invert_fp64(P, tau_out, qn, guess, e, P0, uo, nit);
+
+    // ---- e) regulator
+    if (P.regulate) {
+      const R go = P.milne ? (R)(tau_out * tau_out) : R(1);
+      R pr[4][4], ur[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ur[a] = (R)uo[a];
+#pragma unroll
+        for (int b = a; b < 4; ++b) {
+          pr[a][b] = (R)qn[pix(a, b)];
+          pr[b][a] = pr[a][b];
+        }
+      }
+      R f = regulator_factor<R>(P, go, (R)e, (R)P0, ur, pr, (R)qn[14]);
+      if (f < R(0.999)) ++nreg;
+#pragma unroll
+      for (int n = 4; n < 14; ++n) qn[n] *= (double)f;
+    }
+#pragma unroll
+    for (int n = 0; n < NQ; ++n)
+      if (!isfinite(qn[n])) st |= ST_NONFINITE;
+
+    // ---- f) stores
+    store_with_ghosts<R>(P, io, i + 2, j + 2, k + 2, qn, uo, e, P0);
+  }
+
+  // ---- statistics: warp shuffles, then one atomic per block
+  __shared__ unsigned s_st[8], s_max[8], s_it[8], s_reg[8];
+  const unsigned full = 0xffffffffu;
+  unsigned w_st = __reduce_or_sync(full, st);
+  unsigned w_max = __reduce_max_sync(full, __float_as_uint(amax));
+  unsigned w_it = __reduce_add_sync(full, nit);
+  unsigned w_reg = __reduce_add_sync(full, nreg);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int warp = tid >> 5, nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+  if ((tid & 31) == 0) {
+    s_st[warp] = w_st; s_max[warp] = w_max; s_it[warp] = w_it; s_reg[warp] = w_reg;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned a = 0, b = 0, cI = 0, d = 0;
+    for (int w = 0; w < nwarps; ++w) { a |= s_st[w]; b = max(b, s_max[w]); cI += s_it[w]; d += s_reg[w]; }
+    if (a) atomicOr(io.status, a);
+    atomicMax(io.max_speed_bits, b);
+    if (cI) atomicAdd(io.counters + 0, (unsigned long long)cI);
+    if (d) atomicAdd(io.counters + 1, (unsigned long long)d);
+  }
+}
+
+}  // namespace kt

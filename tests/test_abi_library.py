@@ -1,0 +1,71 @@
+"""The C-ABI library loads and exports every symbol that include/*.h declares (no GPU calls)."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(kt_[a-z0-9_]+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1608_06577_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for n in ("kt_init", "kt_set_state", "kt_step", "kt_get_state", "kt_free", "kt_get_stats", "kt_last_error"):
+        assert n in names, n
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", libpath]).decode()
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = _declared_symbols() - exported
+    assert not missing, missing
+
+
+def test_library_loads_and_fails_loudly_without_gpu(libpath):
+    import ctypes
+    from paper_1608_06577_gb300 import binding
+    L = binding.load_library()
+    o = binding.Options()
+    assert L.kt_options_default(ctypes.byref(o)) == 0
+    assert o.theta_limiter == 1.0 and o.regulate == 1
+    import torch
+    if not torch.cuda.is_available():
+        g = binding.Grid(4, 4, 4)
+        eos = binding.Eos(0, 15.6, 0, None, None, None, None, None)
+        z = binding.Coef(0, 0.0, 0.0, 1.0)
+        ctx = ctypes.c_void_p()
+        rc = L.kt_init(ctypes.byref(ctx), ctypes.byref(g), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
+                       ctypes.byref(z), None)
+        assert rc == -2  # KT_ERR_CUDA: no device, and no CPU fallback
+
+
+def test_invalid_arguments_rejected(libpath):
+    import ctypes
+    from paper_1608_06577_gb300 import binding
+    L = binding.load_library()
+    ctx = ctypes.c_void_p()
+    g = binding.Grid(0, 4, 4)
+    eos = binding.Eos(0, 15.6, 0, None, None, None, None, None)
+    z = binding.Coef(0, 0.0, 0.0, 1.0)
+    assert L.kt_init(ctypes.byref(ctx), ctypes.byref(g), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
+                     ctypes.byref(z), None) == -1
+    nb = ctypes.c_size_t()
+    assert L.kt_state_bytes(ctypes.byref(binding.Grid(128, 128, 128)), None, ctypes.byref(nb)) == 0
+    assert nb.value > 30 * 132 * 132 * 132 * 8

@@ -1,0 +1,176 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 mode must match the oracle to a max relative error of 1e-12 per field (normalised by
+the field's max norm, since pi and Pi cross zero) after 10 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from workload.eos import A_SB
+from workload.problem import (HBARC, Problem, bjorken_problem, conformal_eos, gubser_problem, hotspot_problem,
+                              sod_problem)
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("e", "u", "pi", "Pi", "q")
+
+
+PI_ETA_INDICES = [0, 0, 0, 1, 0, 0, 1, 0, 1, 2]  # eta indices of pi^{tt,tx,ty,tn,xx,xy,xn,yy,yn,nn}
+GROUP_FLOOR = 1e-3
+
+
+def field_errors(g, r, milne=True):
+    """Max relative error per field: max|a - b| / max(max|b|, 1e-3 S), where S is the scale of the
+    field's tensor in an orthonormal frame (T^{tau mu}: max T^{tau tau}; pi^{mu nu}: max over
+    components of |pi^{mu nu}| tau^(number of eta indices); u: max u^tau).  The floor only matters
+    for components far below their tensor's size, whose differences are rounding noise of the
+    larger components they are computed from."""
+    tau = r["tau"] if milne else 1.0
+    S_T = np.max(np.abs(r["q"][0]))
+    S_pi = max(np.max(np.abs(r["pi"][k])) * tau ** PI_ETA_INDICES[k] for k in range(10))
+    S_u = np.max(np.abs(r["u"][0]))
+    groups = {"q": [S_T] * 4 + [S_pi * tau ** -PI_ETA_INDICES[k] for k in range(10)] + [0.0],
+              "pi": [S_pi * tau ** -PI_ETA_INDICES[k] for k in range(10)],
+              "u": [S_u, S_u, S_u, S_u / tau], "e": [0.0], "Pi": [0.0]}
+    errs = {}
+    for f in FIELDS:
+        a, b = np.atleast_2d(g[f]), np.atleast_2d(r[f])
+        for k in range(a.shape[0]):
+            scale = max(np.max(np.abs(b[k])), GROUP_FLOOR * groups[f][k])
+            d = np.max(np.abs(a[k] - b[k]))
+            errs[f"{f}[{k}]"] = d / scale if scale > 0 else d
+    return errs
+
+
+def run_pair(p, nsteps, precision=0):
+    from paper_1608_06577_gb300 import KT
+    kt = KT(p, precision=precision)
+    kt.set_problem_state()
+    kt.step(nsteps)
+    g = kt.get_state()
+    o = oracle.Oracle(p)
+    assert o.step(nsteps) == 0
+    r = o.get_state()
+    r["milne"] = p.coords == "milne"
+    return g, r, kt
+
+
+def assert_parity(g, r, tol=1e-12):
+    errs = field_errors(g, r, r.get("milne", True))
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, bad
+    assert abs(g["tau"] - r["tau"]) < 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1608_06577_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def test_gubser_c0_fp64_parity_and_physics():
+    p = gubser_problem()  # 32x32x8, conformal, eta/s = 0.2, theta = 1.8, 20 steps
+    g, r, kt = run_pair(p, 10)
+    assert_parity(g, r)
+    kt.step(10)
+    g = kt.get_state()
+    o = oracle.Oracle(p)
+    o.step(20)
+    assert_parity(g, o.get_state())
+    X, Y, _ = p.coords_xyz()
+    X, Y = X.ravel(), Y.ravel()
+    ref = p.gubser.state(g["tau"], X, Y, A_SB)
+    m = (np.abs(Y - 0.05) < 1e-9) & (np.abs(X) <= 1.2) & (np.arange(len(X)) < p.nx * p.ny)
+    assert np.max(np.abs(g["e"][m] / ref["e"][m] - 1)) < 0.03
+
+
+@pytest.mark.parametrize("shape", [(20, 18, 10), (37, 5, 9), (33, 33, 3)])
+def test_hotspot_fp64_parity_ragged(shape, baseline_eos):
+    nx, ny, nz = shape
+    p = hotspot_problem(nx=nx, ny=ny, neta=nz, nhot=12, seed=3, r_max=0.8, eos_table=baseline_eos)
+    g, r, _ = run_pair(p, 10)
+    assert_parity(g, r)
+
+
+def test_nonconformal_bjorken_bulk_fp64_parity(baseline_eos):
+    p = bjorken_problem(T0_gev=0.22, tau0=0.6, dtau=0.004, nsteps=10, eos="table", zeta=True).replace(
+        tau_relax_min=0.005, eos=baseline_eos)
+    g, r, _ = run_pair(p, 10)
+    assert_parity(g, r)
+    assert np.max(np.abs(g["Pi"])) > 1e-3
+
+
+def test_periodic_cartesian_viscous_parity_and_conservation(baseline_eos):
+    n = 12
+    p = Problem(name="per", nx=n, ny=n - 2, neta=n - 4, dx=0.2, dy=0.2, deta=0.2, dtau=0.02, tau0=1.0, nsteps=10,
+                coords="cartesian", bc="periodic", theta=1.5, eos=baseline_eos, eta_over_s=("const", 0.2, 0, 1),
+                zeta_over_s=("gauss", 0.1, 0.17 / HBARC, 0.03 / HBARC), tau_relax_min=0.02)
+    X, Y, Z = p.coords_xyz()
+    kx, ky, kz = 2 * np.pi / (p.nx * 0.2), 2 * np.pi / (p.ny * 0.2), 2 * np.pi / (p.neta * 0.2)
+    p.e = (1.0 / HBARC) * (1 + 0.5 * np.sin(kx * X) * np.cos(ky * Y) + 0.3 * np.sin(kz * Z)).ravel()
+    p.u = np.stack([0.2 * np.sin(ky * Y).ravel(), 0.1 * np.cos(kx * X).ravel(), 0.15 * np.sin(kx * X + kz * Z).ravel()])
+    g, r, kt = run_pair(p, 10)
+    assert_parity(g, r)
+    kt2_q0 = np.sum(r["q"][:4], axis=1)
+    from paper_1608_06577_gb300 import KT
+    k2 = KT(p)
+    k2.set_problem_state()
+    q0 = np.sum(k2.get_state()["q"][:4], axis=1)
+    k2.step(30)
+    q1 = np.sum(k2.get_state()["q"][:4], axis=1)
+    assert np.max(np.abs(q1 - q0)) < 1e-13 * q0[0]
+    assert kt2_q0 is not None
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sod_fp64_parity(axis):
+    p = sod_problem(nx=64, dx=0.1, t_end=0.5, axis=axis)
+    g, r, _ = run_pair(p, p.nsteps)
+    assert_parity(g, r)
+
+
+def test_milne_flow_with_u_eta_and_shear(baseline_eos):
+    """Hotspots with an initial longitudinal flow and shear stress exercise every source term."""
+    p = hotspot_problem(nx=24, ny=20, neta=12, nhot=8, seed=5, r_max=0.8, eos_table=baseline_eos)
+    X, Y, Z = p.coords_xyz()
+    p.u = np.stack([0.1 * np.tanh(X).ravel(), -0.05 * np.tanh(Y).ravel(), (0.3 * np.tanh(Z) / p.tau0).ravel()])
+    rng = np.random.default_rng(1)
+    pi = np.zeros((10, p.ncells))
+    pi[4] = 0.01 * p.e * (1 + 0.1 * rng.normal(size=p.ncells))
+    pi[7] = -pi[4]
+    p.pi = pi
+    p.Pi = -0.01 * p.e
+    p.u_prev = p.u * 0.99
+    g, r, _ = run_pair(p, 10)
+    assert_parity(g, r)
+
+
+def test_step_counts_and_graph_paths_agree(baseline_eos):
+    """Graph replay (3-step cycles) and direct launches give identical bits; resume after
+    get/set_state round trip is bit-exact (checkpoint / resume)."""
+    from paper_1608_06577_gb300 import KT
+    p = hotspot_problem(nx=20, ny=20, neta=8, nhot=6, seed=9, r_max=0.8, eos_table=baseline_eos)
+    a = KT(p, use_graph=True)
+    a.set_problem_state()
+    a.step(7)
+    b = KT(p, use_graph=False)
+    b.set_problem_state()
+    for _ in range(7):
+        b.step(1)
+    ga, gb = a.get_state(), b.get_state()
+    for f in FIELDS:
+        assert np.array_equal(ga[f], gb[f]), f
+
+
+def test_invalid_state_rejected():
+    from paper_1608_06577_gb300 import KT, KTError
+    p = gubser_problem(nx=8, ny=8, neta=2)
+    kt = KT(p)
+    e = p.e.copy()
+    e[3] = np.nan
+    with pytest.raises(KTError):
+        kt.set_state(p.tau0, e, p.u, p.pi, p.Pi)
