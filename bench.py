@@ -25,9 +25,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell updates/s per RK2 step at 128^3, plain FP64 vs FP32+learned; % HBM peak"
 UNIT = "cell updates/s"
-# algorithmic bytes per cell per RK2 step of the two fused stages (both stages read and write
-# every field once): 107 words; u, e, p are 4-byte words in mixed mode
-BYTES_PER_CELL = {"fp64": 107 * 8, "mixed": 59 * 8 + 48 * 4}
+# Algorithmic bytes per cell per RK2 step of the two fused stages, every field read and written
+# once per stage.  FP64: stage 1 reads q, u, u_prev, e, p (25 words) and writes q*, u*, e, p (21);
+# stage 2 reads q*, q^n, u*, u^n, e, p (40) and writes 21: 107 words = 856 B.  Mixed: u, e, p are
+# FP32 and the stencil reads an FP32 copy of q that each stage also writes:
+# (60+120+16+16+8) + (120+60+16+8) + (60+120+120+16+16+8) + (120+60+16+8) = 968 B.
+BYTES_PER_CELL = {"fp64": 856, "mixed": 968}
 
 
 def parse():

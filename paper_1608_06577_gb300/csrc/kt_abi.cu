@@ -29,6 +29,8 @@ struct Ctx {
   size_t bytes = 0;
   double* q = nullptr;   // 15 fields
   double* qs = nullptr;  // 15 fields
+  float* qf = nullptr;   // mixed mode: FP32 copies of q and qs read by the stencil
+  float* qsf = nullptr;
   void* U[3] = {};       // 3 x 4 fields
   void* E[2] = {};
   void* Pb[2] = {};
@@ -81,6 +83,7 @@ size_t state_bytes(const Lattice& L, int mixed, int eos_n) {
   size_t es = mixed ? 4 : 8;
   size_t b = 0;
   b += align_up(30 * fs * 8, 256);             // q, qs
+  if (mixed) b += align_up(30 * fs * 4, 256);  // FP32 copies of q, qs
   b += align_up(12 * fs * es, 256);            // U[3]
   b += align_up(4 * fs * es, 256);             // E[2], P[2]
   size_t ncell = (size_t)L.nx * L.ny * L.nz;
@@ -99,6 +102,25 @@ void coef_from(Coef& d, const kt_coef* s) {
   d.c1 = s ? s->c1 : 0.0;
   d.c2 = s ? s->c2 : 1.0;
   d.ln_c0 = (d.c0 > 0.0) ? std::log(d.c0) : -INFINITY;
+}
+
+template <typename R>
+void fill_pr(PR<R>& o, const Params& P) {
+  o.inv_d[0] = (R)(1.0 / P.dx);
+  o.inv_d[1] = (R)(1.0 / P.dy);
+  o.inv_d[2] = (R)(1.0 / P.deta);
+  o.theta = (R)P.theta;
+  o.inv_dtau = (R)(1.0 / P.dtau);
+  o.dtau = (R)P.dtau;
+  o.half_dtau = (R)(0.5 * P.dtau);
+  o.rate_max = (R)P.rate_max;
+  o.tpp = (R)P.tpp;
+  o.rho_max = (R)P.rho_max;
+  o.xi0_rho_max = (R)(P.xi0 * P.rho_max);
+  o.eos_a = (R)P.eos_a;
+  o.eta_c0 = (R)P.eta.c0; o.eta_c1 = (R)P.eta.c1; o.eta_inv_c2 = (R)(1.0 / P.eta.c2); o.eta_ln_c0 = (R)P.eta.ln_c0;
+  o.zeta_c0 = (R)P.zeta.c0; o.zeta_c1 = (R)P.zeta.c1; o.zeta_inv_c2 = (R)(1.0 / P.zeta.c2);
+  o.zeta_ln_c0 = (R)P.zeta.ln_c0;
 }
 
 // Per-interval cubic coefficients of the table EOS (see kt_eos in kt.h).
@@ -129,7 +151,8 @@ __device__ __forceinline__ double gnn_at(const Params& P, double tau) { return P
 
 template <typename R>
 __global__ void set_state_kernel(const Params P, const double* __restrict__ in, int has_u, int has_pi, int has_Pi,
-                                 int has_up, double tau, double* q, R* U, R* Up, R* E, R* Pb, unsigned* status) {
+                                 int has_up, double tau, double* q, float* qf, R* U, R* Up, R* E, R* Pb,
+                                 unsigned* status) {
   const Lattice& L = P.L;
   long long ncp = (long long)L.nx * L.ny * L.nz;
   long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -182,6 +205,8 @@ __global__ void set_state_kernel(const Params P, const double* __restrict__ in, 
     }
     long long c = L.idx(ii, jj, kk);
     for (int n = 0; n < NQ; ++n) q[n * fs + c] = qn[n];
+    if (qf)
+      for (int n = 0; n < NQ; ++n) qf[n * fs + c] = (float)qn[n];
     for (int m = 0; m < 4; ++m) { U[m * fs + c] = (R)u4[m]; Up[m * fs + c] = (R)up4[m]; }
     E[c] = (R)e;
     Pb[c] = (R)P0;
@@ -220,6 +245,13 @@ StageIO<R> make_io(Ctx* c, int stage) {
     io.u_in = Uprev; io.u_prev = U0; io.u_out = Usp;          // u^{n+1} into the spare buffer
     io.e_in = (R*)c->E[1]; io.p_in = (R*)c->Pb[1];
     io.e_out = (R*)c->E[0]; io.p_out = (R*)c->Pb[0];
+  }
+  if constexpr (sizeof(R) == 4) {
+    io.qr_in = (stage == 1) ? c->qf : c->qsf;
+    io.qr_out = (stage == 1) ? c->qsf : c->qf;
+  } else {
+    io.qr_in = (const R*)io.q_in;
+    io.qr_out = nullptr;
   }
   io.d_tau = c->d_tau;
   io.status = c->d_stat;
@@ -363,6 +395,8 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   P.e_min = o.e_min;
   P.rate_max = (o.tau_relax_min > 0) ? 1.0 / o.tau_relax_min : INFINITY;
   P.ln_rate_max = std::log(P.rate_max);
+  fill_pr<double>(P.pd, P);
+  fill_pr<float>(P.pf, P);
 
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
@@ -399,6 +433,12 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   char* qq = (char*)carve(30 * fs * 8);
   c->q = (double*)qq;
   c->qs = (double*)(qq + 15 * fs * 8);
+  if (c->mixed) {
+    char* qqf = (char*)carve(30 * fs * 4);
+    c->qf = (float*)qqf;
+    c->qsf = (float*)(qqf + 15 * fs * 4);
+    CK(cudaMemsetAsync(qqf, 0, 30 * fs * 4, c->stream));
+  }
   char* uu = (char*)carve(12 * fs * c->esz);
   for (int b = 0; b < 3; ++b) c->U[b] = uu + (size_t)b * 4 * fs * c->esz;
   char* ep = (char*)carve(4 * fs * c->esz);
@@ -465,11 +505,11 @@ int kt_set_state(kt_ctx* c, double tau, const double* e, const double* u, const 
   int nb = (int)((ncp + 255) / 256);
   if (c->mixed)
     set_state_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, s, u != nullptr, pi != nullptr, Pi != nullptr,
-                                                       u_prev != nullptr, tau, c->q, (float*)c->U[0], (float*)c->U[1],
+                                                       u_prev != nullptr, tau, c->q, c->qf, (float*)c->U[0], (float*)c->U[1],
                                                        (float*)c->E[0], (float*)c->Pb[0], c->d_stat);
   else
     set_state_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, s, u != nullptr, pi != nullptr, Pi != nullptr,
-                                                        u_prev != nullptr, tau, c->q, (double*)c->U[0], (double*)c->U[1],
+                                                        u_prev != nullptr, tau, c->q, nullptr, (double*)c->U[0], (double*)c->U[1],
                                                         (double*)c->E[0], (double*)c->Pb[0], c->d_stat);
   CK(cudaGetLastError());
   unsigned st = 0;

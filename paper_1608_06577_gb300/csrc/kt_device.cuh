@@ -19,6 +19,9 @@ __host__ __device__ constexpr int pix(int a, int b) {
 
 enum : unsigned { ST_INVERSION = 1u, ST_NONFINITE = 2u };
 
+__device__ __forceinline__ double f2d_bits(float f);
+__device__ __forceinline__ float d2f_bits(double d);
+
 struct Lattice {
   int nx, ny, nz;      // physical cells
   int pitch;           // padded row length (>= nx + 4)
@@ -45,6 +48,21 @@ struct Coef {
   double ln_c0;
 };
 
+// Per-run constants in the stencil precision, computed once on the host so that no thread
+// divides or converts them (on GB300 both run on the slow FP64 pipe).
+template <typename R>
+struct PR {
+  R inv_d[3];          // 1/dx, 1/dy, 1/deta
+  R theta;             // minmod parameter
+  R inv_dtau, dtau, half_dtau;
+  R rate_max;          // 1/tau_relax_min (or +inf)
+  R tpp;               // tau_pipi/tau_pi
+  R rho_max, xi0_rho_max;
+  R eos_a;
+  R eta_c0, eta_c1, eta_inv_c2, eta_ln_c0;
+  R zeta_c0, zeta_c1, zeta_inv_c2, zeta_ln_c0;
+};
+
 struct Params {
   Lattice L;
   double dx, dy, deta, dtau;
@@ -65,7 +83,13 @@ struct Params {
   double e_min;
   double rate_max;    // 1 / tau_relax_min (or +inf)
   double ln_rate_max;
+  PR<double> pd;
+  PR<float> pf;
 };
+
+template <typename R> __device__ __forceinline__ const PR<R>& pr(const Params& P);
+template <> __device__ __forceinline__ const PR<double>& pr<double>(const Params& P) { return P.pd; }
+template <> __device__ __forceinline__ const PR<float>& pr<float>(const Params& P) { return P.pf; }
 
 template <typename R> __device__ __forceinline__ const EosSeg<R>* eos_table(const Params& P);
 template <> __device__ __forceinline__ const EosSeg<double>* eos_table<double>(const Params& P) { return P.seg_d; }
@@ -76,7 +100,9 @@ template <> __device__ __forceinline__ const EosSeg<float>* eos_table<float>(con
 template <typename R>
 __device__ __forceinline__ int eos_interval(const Params& P, const EosSeg<R>* seg, R e) {
   int n1 = P.eos_n - 2;
-  float g = (__logf((float)e) - P.lne0) * P.inv_h;
+  float ef;
+  if constexpr (sizeof(R) == 8) ef = d2f_bits(e); else ef = e;
+  float g = (__logf(ef) - P.lne0) * P.inv_h;
   int i = (g > 0.f) ? (int)g : 0;  // NaN compares false -> 0
   i = min(i, n1);
   #pragma unroll 1
@@ -112,7 +138,7 @@ __device__ __forceinline__ R eos_P(const Params& P, R e) {
 template <typename R>
 __device__ __forceinline__ void eos_T_lnd(const Params& P, R e, R& T, R& lnd) {
   if (!P.eos_table) {
-    T = sqrt(sqrt(e / R(P.eos_a)));
+    T = sqrt(sqrt(e / pr<R>(P).eos_a));
     lnd = -R(INFINITY);
     return;
   }
@@ -134,19 +160,58 @@ __device__ __forceinline__ R limited_slope(R qm, R q0, R qp, R theta) {
   return pos ? mn : (neg ? -mn : R(0));
 }
 
+// eta/s(T) and ln(zeta/s)(T): const c0 or c0 exp(-((T - c1)/c2)^2)
 template <typename R>
-__device__ __forceinline__ R coef_value(const Coef& c, R T) {
-  if (c.kind == 0) return R(c.c0);
-  R x = (T - R(c.c1)) / R(c.c2);
-  return R(c.c0) * exp(-x * x);
+__device__ __forceinline__ R eta_over_s(const Params& P, R T) {
+  const PR<R>& p = pr<R>(P);
+  if (P.eta.kind == 0) return p.eta_c0;
+  R x = (T - p.eta_c1) * p.eta_inv_c2;
+  return p.eta_c0 * exp(-x * x);
 }
 
 template <typename R>
-__device__ __forceinline__ R coef_log(const Coef& c, R T) {
-  if (c.kind == 0) return R(c.ln_c0);
-  R x = (T - R(c.c1)) / R(c.c2);
-  return R(c.ln_c0) - x * x;
+__device__ __forceinline__ R ln_zeta_over_s(const Params& P, R T) {
+  const PR<R>& p = pr<R>(P);
+  if (P.zeta.kind == 0) return p.zeta_ln_c0;
+  R x = (T - p.zeta_c1) * p.zeta_inv_c2;
+  return p.zeta_ln_c0 - x * x;
 }
+
+// Conversions between float and double on the integer pipe.  On GB300 the F2F conversion
+// instructions issue on the FP64 pipe, which has 1/64 of the FP32 rate; these bit-level
+// versions leave it free.  float -> double is exact (subnormal floats flush to zero);
+// double -> float rounds to nearest even (results below the smallest normal float flush to
+// zero, overflow gives infinity, NaN stays NaN).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ex = (b >> 23) & 0xffu;
+  const unsigned s = b & 0x80000000u;
+  const unsigned m = b & 0x7fffffu;
+  const unsigned ed = (ex == 0xffu) ? 0x7ffu : ex + 896u;
+  const unsigned hi = (ex == 0u) ? s : (s | (ed << 20) | (m >> 3));
+  const unsigned lo = (ex == 0u) ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f_bits(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned s = hi & 0x80000000u;
+  const int ex = (int)((hi >> 20) & 0x7ffu);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  unsigned bits = ((unsigned)(ex - 896) << 23) + m;
+  bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  if (ex - 896 <= 0) bits = 0u;
+  if (ex - 896 >= 255) bits = 0x7f800000u | ((ex == 0x7ff && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
+  return __uint_as_float(s | bits);
+}
+
+template <typename R> __device__ __forceinline__ double to_f64(R x);
+template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ double to_f64<float>(float x) { return f2d_bits(x); }
+template <typename R> __device__ __forceinline__ R from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_bits(x); }
 
 // per-cell read of an R-typed field from a buffer that may hold double or float
 template <typename R, typename S>

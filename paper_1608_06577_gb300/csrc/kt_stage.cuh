@@ -19,9 +19,11 @@ namespace kt {
 
 template <typename R>
 struct StageIO {
-  const double* q_in;    // 15 fields, stencil input (q^n or q^*)
+  const double* q_in;    // 15 fields, FP64 (q^n or q^*), read at the own cell for the Heun update
   const double* q_base;  // stage 2: q^n, read at the own cell only (aliases q_out)
   double* q_out;
+  const R* qr_in;        // 15 fields in the stencil precision (FP64 mode: q_in itself; mixed: an
+  R* qr_out;             // FP32 copy written by the previous stage); qr_out null in FP64 mode
   const R* u_in;         // 4 fields, stencil input (u^n or u^*)
   const R* u_prev;       // 4 fields, own cell only: u^{n-1} (stage 1) or u^n (stage 2)
   R* u_out;              // may alias u_prev (own cell only)
@@ -43,9 +45,9 @@ __device__ __forceinline__ void direction_pass(const Params& P, const StageIO<R>
   const Lattice& L = P.L;
   const long long fs = L.fstride;
   const long long s = (D == 0) ? 1LL : ((D == 1) ? (long long)L.pitch : L.plane);
-  const R invD = (D == 0) ? R(1.0 / P.dx) : ((D == 1) ? R(1.0 / P.dy) : R(1.0 / P.deta));
+  const R invD = pr<R>(P).inv_d[D];
   const R hinv = R(0.5) * invD;
-  const R th = R(P.theta);
+  const R th = pr<R>(P).theta;
   const R* u = io.u_in;
 
   // u^mu on the stencil
@@ -79,7 +81,7 @@ __device__ __forceinline__ void direction_pass(const Params& P, const StageIO<R>
   dv += (vpl - vmi) * hinv;
 
   // S_c: -d_d (v^d P delta^nu_tau - g^{d nu} P - v^d pi^{tau nu} + pi^{d nu}), P = P0 + Pi
-  const double* q = io.q_in;
+  const R* q = io.qr_in;
   R Ppl = ld<R>(io.p_in, c + s) + ld<R>(q + 14 * fs, c + s);
   R Pmi = ld<R>(io.p_in, c - s) + ld<R>(q + 14 * fs, c - s);
   dq[0] -= (Ppl * vpl - Pmi * vmi) * hinv;
@@ -87,7 +89,7 @@ __device__ __forceinline__ void direction_pass(const Params& P, const StageIO<R>
 
 #pragma unroll
   for (int n = 0; n < NQ; ++n) {
-    const double* qn = q + n * fs;
+    const R* qn = q + n * fs;
     R a2 = ld<R>(qn, c - 2 * s), a1 = ld<R>(qn, c - s), a0 = ld<R>(qn, c), b1 = ld<R>(qn, c + s),
       b2 = ld<R>(qn, c + 2 * s);
     R sm = limited_slope(a2, a1, a0, th), s0 = limited_slope(a1, a0, b1, th), sp = limited_slope(a0, b1, b2, th);
@@ -105,9 +107,79 @@ __device__ __forceinline__ void direction_pass(const Params& P, const StageIO<R>
   (void)tau;
 }
 
+// 1/A to full double precision: a single-precision seed and two Newton-Raphson refinements
+__device__ __forceinline__ double rcp_fp64(double A) {
+  double r = f2d_bits(__frcp_rn(d2f_bits(A)));
+  r = fma(r, fma(-A, r, 1.0), r);
+  return fma(r, fma(-A, r, 1.0), r);
+}
+
 // ------------------------------------------------------------ d) inversion, FP64 (Sec. 2.4)
 // f(e) = e - E + M^2/(E + P0(e) + Pi) = 0 by Newton-Raphson inside the bracket [lo, E],
 // with bisection whenever a step leaves it; stop at |de| <= 2^-50 E (at most 100 steps).
+// The residual f and the iterate are FP64; the step length uses f' = 1 - M^2 c_s^2/A^2 in
+// single precision, which only perturbs the contraction rate, never the root.  u^mu is formed
+// in the stencil precision R.
+template <typename R>
+__device__ __forceinline__ unsigned invert_mixed(const Params& P, double tau, const double (&qn)[NQ], double guess,
+                                                 double& e, double& P0, R (&uo)[4], unsigned& iters) {
+  const double E = qn[0] - qn[4];
+  const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
+  const double Pi = qn[14];
+  const double gnn = P.milne ? tau * tau : 1.0;
+  const double M2 = fma(Mx, Mx, fma(My, My, gnn * Mn * Mn));
+  unsigned st = 0;
+  if (!(E > 0.0) || !isfinite(E) || !isfinite(M2) || !(M2 < E * E)) {
+    st = ST_INVERSION;
+    e = (P.e_min > 0.0) ? P.e_min : 1e-30;
+  } else if (!P.eos_table && (!P.bulk_on || Pi == 0.0)) {
+    double M = sqrt(M2);  // conformal closed form e = sqrt(4E^2 - 3M^2) - E, cancellation-free
+    e = 3.0 * (E - M) * (E + M) / (sqrt(fma(4.0 * E, E, -3.0 * M2)) + E);
+  } else {
+    double lo = (P.e_min > 0.0) ? P.e_min : 1e-300, hi = E;
+    e = (guess >= lo && guess <= hi) ? guess : hi;  // the cell's previous e, else E
+    const float M2f = d2f_bits(M2);
+    int it;
+    for (it = 0; it < 100; ++it) {
+      const int i = eos_interval<double>(P, P.seg_d, e);
+      const EosSeg<double>& s = P.seg_d[i];
+      const double t = (e - s.e0) * s.inv_de;
+      const double p0 = fma(t, fma(t, fma(t, s.cP3, s.cP2), s.mP), s.P0);
+      const EosSeg<float>& sf = P.seg_f[i];
+      const float tf = d2f_bits(t);
+      const float c2 = fmaf(tf, fmaf(tf, 3.f * sf.cP3, 2.f * sf.cP2), sf.mP) * sf.inv_de;
+      const double A = E + p0 + Pi;
+      const double rA = rcp_fp64(A);
+      const double f = (e - E) + M2 * rA;
+      if (f == 0.0) break;
+      if (f < 0.0) lo = e; else hi = e;
+      const float rAf = d2f_bits(rA);
+      const float fp = 1.f - M2f * rAf * rAf * c2;
+      double en = e - f * f2d_bits(__frcp_rn(fp));
+      if (!(en >= lo && en <= hi)) en = 0.5 * (lo + hi);
+      const double de = fabs(en - e);
+      e = en;
+      if (de <= ldexp(E, -50)) { ++it; break; }  // f is known to about one ulp of E
+    }
+    iters += (unsigned)it;
+    if (it >= 100) st |= ST_INVERSION;
+  }
+  if (e < P.e_min) e = P.e_min;
+  P0 = eos_P<double>(P, e);
+  if (st) {
+    uo[0] = R(1); uo[1] = uo[2] = uo[3] = R(0);
+  } else {
+    const double Pt = P0 + Pi;
+    const R ePt = from_f64<R>(e + Pt);
+    const R ut = sqrt(from_f64<R>(E + Pt) / ePt);
+    const R w = R(1) / (ePt * ut);
+    uo[0] = ut; uo[1] = from_f64<R>(Mx) * w; uo[2] = from_f64<R>(My) * w; uo[3] = from_f64<R>(Mn) * w;
+  }
+  if (!isfinite(e) || !isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3]))
+    st |= ST_NONFINITE;
+  return st;
+}
+
 __device__ __forceinline__ unsigned invert_fp64(const Params& P, double tau, const double (&qn)[NQ], double guess,
                                                 double& e, double& P0, double (&uo)[4], unsigned& iters) {
   double E = qn[0] - qn[4];
@@ -175,8 +247,8 @@ __device__ __forceinline__ R regulator_factor(const Params& P, R gnn, R e, R P0,
     }
   if (!(PP > R(0))) return R(1);
   R nPP = sqrt(PP);
-  R rho = nPP / (R(P.rho_max) * sqrt(e * e + R(3) * P0 * P0));
-  R den = R(1) / (R(P.xi0 * P.rho_max) * nPP);
+  R rho = nPP / (pr<R>(P).rho_max * sqrt(e * e + R(3) * P0 * P0));
+  R den = R(1) / (pr<R>(P).xi0_rho_max * nPP);
   R tr = pi[0][0] - pi[1][1] - pi[2][2] - gnn * pi[3][3];
   rho = fmax(rho, fabs(tr) * den);
 #pragma unroll
@@ -192,13 +264,17 @@ __device__ __forceinline__ R regulator_factor(const Params& P, R gnn, R e, R P0,
 // ---------------------------------------------------------------- f) stores with ghosts
 template <typename R>
 __device__ __forceinline__ void store_cell(const StageIO<R>& io, long long fs, long long t, const double (&qn)[NQ],
-                                           const double (&uo)[4], double e, double P0) {
+                                           const R (&qr)[NQ], const R (&uo)[4], R e, R P0) {
 #pragma unroll
   for (int n = 0; n < NQ; ++n) io.q_out[n * fs + t] = qn[n];
+  if (io.qr_out) {
 #pragma unroll
-  for (int m = 0; m < 4; ++m) io.u_out[m * fs + t] = (R)uo[m];
-  io.e_out[t] = (R)e;
-  io.p_out[t] = (R)P0;
+    for (int n = 0; n < NQ; ++n) io.qr_out[n * fs + t] = qr[n];
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) io.u_out[m * fs + t] = uo[m];
+  io.e_out[t] = e;
+  io.p_out[t] = P0;
 }
 
 // padded ghost coordinate g in {0, 1, n+2, n+3} that copies the physical padded coordinate p
@@ -209,10 +285,11 @@ __device__ __forceinline__ int ghost_source(int g, int n, int periodic) {
 
 template <typename R>
 __device__ __forceinline__ void store_with_ghosts(const Params& P, const StageIO<R>& io, int i, int j, int k,
-                                                  const double (&qn)[NQ], const double (&uo)[4], double e, double P0) {
+                                                  const double (&qn)[NQ], const R (&qr)[NQ], const R (&uo)[4], R e,
+                                                  R P0) {
   const Lattice& L = P.L;
   const long long fs = L.fstride;
-  store_cell<R>(io, fs, L.idx(i, j, k), qn, uo, e, P0);
+  store_cell<R>(io, fs, L.idx(i, j, k), qn, qr, uo, e, P0);
   const int nn[3] = {L.nx, L.ny, L.nz};
   const int pc[3] = {i, j, k};
 #pragma unroll
@@ -224,14 +301,14 @@ __device__ __forceinline__ void store_with_ghosts(const Params& P, const StageIO
     for (int g = 0; g < 4; ++g) {
       if (ghost_source(gs[g], n, P.periodic) != pc[ax]) continue;
       int ii = (ax == 0) ? gs[g] : i, jj = (ax == 1) ? gs[g] : j, kk = (ax == 2) ? gs[g] : k;
-      store_cell<R>(io, fs, L.idx(ii, jj, kk), qn, uo, e, P0);
+      store_cell<R>(io, fs, L.idx(ii, jj, kk), qn, qr, uo, e, P0);
     }
   }
 }
 
 // ---------------------------------------------------------------- the stage kernel
 template <typename R, int STAGE>
-__global__ void __launch_bounds__(256) stage_kernel(const Params P, const StageIO<R> io) {
+__global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) stage_kernel(const Params P, const StageIO<R> io) {
   const Lattice& L = P.L;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -263,9 +340,9 @@ __global__ void __launch_bounds__(256) stage_kernel(const Params P, const StageI
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       uc[m] = ld<R>(io.u_in + m * fs, c);
-      du[0][m] = (uc[m] - ld<R>(io.u_prev + m * fs, c)) * R(1.0 / P.dtau);  // backward difference
+      du[0][m] = (uc[m] - ld<R>(io.u_prev + m * fs, c)) * pr<R>(P).inv_dtau;  // backward difference
     }
-    const double* q = io.q_in;
+    const R* q = io.qr_in;
     R pi[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -336,10 +413,10 @@ __global__ void __launch_bounds__(256) stage_kernel(const Params P, const StageI
 
       if (P.shear_on) {
         R eta_tp = (ec + P0c) * R(0.2);
-        R es = coef_value<R>(P.eta, T);
+        R es = eta_over_s<R>(P, T);
         R rate_pi = (es > R(0)) ? T / (R(5) * es) : R(INFINITY);
-        rate_pi = fmin(rate_pi, R(P.rate_max));
-        const R tpp = R(P.tpp);
+        rate_pi = fmin(rate_pi, pr<R>(P).rate_max);
+        const R tpp = pr<R>(P).tpp;
         R av[4];  // pi^{mu lambda} D u_lambda
 #pragma unroll
         for (int m = 0; m < 4; ++m) av[m] = pi[m][0] * Dlo[0] + pi[m][1] * Dlo[1] + pi[m][2] * Dlo[2] + pi[m][3] * Dlo[3];
@@ -375,8 +452,8 @@ __global__ void __launch_bounds__(256) stage_kernel(const Params P, const StageI
           }
       }
       if (P.bulk_on) {
-        R lrate = R(2.70805020110221) + R(2) * lnd + log(T) - coef_log<R>(P.zeta, T);  // ln 15 + ...
-        R rate_Pi = fmin(exp(lrate), R(P.rate_max));
+        R lrate = R(2.70805020110221) + R(2) * lnd + log(T) - ln_zeta_over_s<R>(P, T);  // ln 15 + ...
+        R rate_Pi = fmin(exp(lrate), pr<R>(P).rate_max);
         R d = exp(lnd);
         R zt = R(15) * d * d * (ec + P0c);
         R IPi = R(2.0 / 3.0) * Pic * theta - R(1.6) * d * ps;
@@ -386,43 +463,58 @@ __global__ void __launch_bounds__(256) stage_kernel(const Params P, const StageI
 
     // ---- c) Heun update in FP64 (Eqs. step1-finalStep)
     double qn[NQ];
-    const double dt = P.dtau;
 #pragma unroll
     for (int n = 0; n < NQ; ++n) {
-      double w = fma(dt, (double)dq[n], __ldg(q + n * fs + c));
-      if (STAGE == 2) w = 0.5 * (io.q_base[n * fs + c] + w);
-      qn[n] = w;
+      const double qi = __ldg(io.q_in + n * fs + c);
+      if (STAGE == 1)
+        qn[n] = qi + to_f64<R>(dq[n] * pr<R>(P).dtau);  // q* = q^n + dtau C[q^n]
+      else  // q^{n+1} = (q^n + q* + dtau C[q*]) / 2
+        qn[n] = fma(0.5, io.q_base[n * fs + c] + qi, to_f64<R>(dq[n] * pr<R>(P).half_dtau));
     }
 
     // ---- d) inversion at tau^{n+1}
-    double e, P0, uo[4];
-    double guess = (double)ld<R>(io.e_in, c);
-    st |= invert_fp64(P, tau_out, qn, guess, e, P0, uo, nit);
+    double e, P0;
+    R uo[4];
+    const double guess = to_f64<R>(ld<R>(io.e_in, c));
+    if constexpr (sizeof(R) == 8)
+      st |= invert_fp64(P, tau_out, qn, guess, e, P0, uo, nit);
+    else
+      st |= invert_mixed<R>(P, tau_out, qn, guess, e, P0, uo, nit);
+
+    // the new state in the stencil precision (the copy the next stage's stencil reads)
+    R qr[NQ];
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) qr[n] = from_f64<R>(qn[n]);
+    const R eR = from_f64<R>(e), P0R = from_f64<R>(P0);
 
     // ---- e) regulator
     if (P.regulate) {
-      const R go = P.milne ? (R)(tau_out * tau_out) : R(1);
-      R pr[4][4], ur[4];
+      const R go = P.milne ? from_f64<R>(tau_out * tau_out) : R(1);
+      R pm[4][4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        ur[a] = (R)uo[a];
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = a; b < 4; ++b) {
-          pr[a][b] = (R)qn[pix(a, b)];
-          pr[b][a] = pr[a][b];
+          pm[a][b] = qr[pix(a, b)];
+          pm[b][a] = pm[a][b];
+        }
+      const R f = regulator_factor<R>(P, go, eR, P0R, uo, pm, qr[14]);
+      if (f < R(0.999)) ++nreg;
+      if (f != R(1)) {
+        const double fd = to_f64<R>(f);
+#pragma unroll
+        for (int n = 4; n < 14; ++n) {
+          qn[n] *= fd;
+          qr[n] *= f;
         }
       }
-      R f = regulator_factor<R>(P, go, (R)e, (R)P0, ur, pr, (R)qn[14]);
-      if (f < R(0.999)) ++nreg;
-#pragma unroll
-      for (int n = 4; n < 14; ++n) qn[n] *= (double)f;
     }
 #pragma unroll
     for (int n = 0; n < NQ; ++n)
-      if (!isfinite(qn[n])) st |= ST_NONFINITE;
+      if (!isfinite(qr[n])) st |= ST_NONFINITE;
 
     // ---- f) stores
-    store_with_ghosts<R>(P, io, i + 2, j + 2, k + 2, qn, uo, e, P0);
+    store_with_ghosts<R>(P, io, i + 2, j + 2, k + 2, qn, qr, uo, eR, P0R);
   }
 
   // ---- statistics: warp shuffles, then one atomic per block

@@ -174,3 +174,16 @@ def test_invalid_state_rejected():
     e[3] = np.nan
     with pytest.raises(KTError):
         kt.set_state(p.tau0, e, p.u, p.pi, p.Pi)
+
+
+def test_mixed_mode_error_after_100_steps(baseline_eos):
+    """Mixed precision (FP32 reconstruction, fluxes and sources; FP64 Heun accumulation and
+    FP64 root-find) against the FP64 oracle after 100 steps: pointwise relative error in e
+    <= 1e-4 on every cell; the per-field max-norm errors are reported."""
+    p = hotspot_problem(nx=40, ny=36, neta=20, nhot=10, seed=4, r_max=1.2, eos_table=baseline_eos)
+    g, r, _ = run_pair(p, 100, precision=1)
+    rel_e = np.max(np.abs(g["e"] / r["e"] - 1))
+    errs = field_errors(g, r)
+    print("mixed mode after 100 steps: max rel err e", rel_e, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert rel_e < 1e-4
+    assert errs["e[0]"] < 1e-4 and errs["q[0]"] < 1e-4
