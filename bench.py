@@ -39,7 +39,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--mode", default="learned", choices=["learned", "mixed", "fp64"])
+    ap.add_argument("--only-main", action="store_true", help="time only --mode")
+    ap.add_argument("--train-samples", type=int, default=1_000_000)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -186,12 +189,20 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- our arm
-def time_mode(prob, mode, steps, warmup, stream):
+MODES = {"learned": (1, 1), "mixed": (1, 0), "fp64": (0, 0)}  # (precision, inversion)
+
+
+def make_kt(prob, mode, weights, stream):
     import torch
     from paper_1608_06577_gb300 import KT
-    prec = 1 if mode == "mixed" else 0
+    prec, inv = MODES[mode]
     with torch.cuda.stream(stream):
-        kt = KT(prob, precision=prec)
+        return KT(prob, precision=prec, inversion=inv, mlp_weights=weights if inv else None)
+
+
+def time_mode(prob, mode, weights, steps, warmup, stream):
+    import torch
+    kt = make_kt(prob, mode, weights, stream)
     kt.set_problem_state()
     kt.step(warmup)
     torch.cuda.synchronize()
@@ -200,8 +211,7 @@ def time_mode(prob, mode, steps, warmup, stream):
     kt.step(steps)
     ev1.record(stream)
     ev1.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    return kt, ms
+    return kt, ev0.elapsed_time(ev1)
 
 
 def run_ours(args, world, rank, local):
@@ -213,8 +223,22 @@ def run_ours(args, world, rank, local):
     prob = hotspot_problem(nx=n, ny=n, neta=n, seed=1 + rank)
     cells = prob.ncells
     hbm_peak, peak_kind = measured_peaks()
+
+    weights, train_info = None, None
+    if args.mode == "learned" or not args.only_main:
+        from paper_1608_06577_gb300 import learned
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            params, losses, (X, Y) = learned.train_default(n=n, n_samples=args.train_samples, epochs=args.epochs)
+            mx, rms = learned.evaluate(params, X, Y)
+        torch.cuda.synchronize()
+        weights = params.cpu().numpy()
+        train_info = {"samples": int(X.shape[0]), "epochs": args.epochs, "final_loss": losses[-1], "rms_err_y": rms,
+                      "max_err_y": mx, "seconds": time.perf_counter() - t0,
+                      "data": f"hotspots {n}^3 seeds 2-11, every 10 steps of 100"}
+
     results = {}
-    modes = [args.mode] + [m for m in ("fp64", "mixed") if m != args.mode]
+    modes = [args.mode] + ([] if args.only_main else [m for m in MODES if m != args.mode])
     clocks = None
     for mode in modes:
         steps = args.steps if mode == args.mode else max(3, min(args.steps, 6))
@@ -222,10 +246,10 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         if mode == args.mode:
             with ClockSampler(local) as cs:
-                kt, ms = time_mode(prob, mode, steps, args.warmup, stream)
+                kt, ms = time_mode(prob, mode, weights, steps, args.warmup, stream)
             clocks = cs.summary()
         else:
-            kt, ms = time_mode(prob, mode, steps, args.warmup, stream)
+            kt, ms = time_mode(prob, mode, weights, steps, args.warmup, stream)
         torch.cuda.synchronize()
         barrier(world)
         ms = max_over_ranks(ms, world)
@@ -239,20 +263,17 @@ def run_ours(args, world, rank, local):
     ms_step = main["ms_per_step"]
     # dominant kernel: the fused stage kernel, two launches per step (the tau-advance kernel is ~0.1%)
     stage_ms = ms_step / 2.0
-    bpc = BYTES_PER_CELL[args.mode]
+    bpc = BYTES_PER_CELL["fp64" if args.mode == "fp64" else "mixed"]
     achieved = cells * bpc / 2.0 / (stage_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                "note": "algorithmic bytes per stage launch / average launch time; the kernel is FP64-pipe "
-                        "bound on GB300 (see profiles/)"}
+                "bytes_per_cell_step": bpc,
+                "note": "algorithmic bytes per stage launch / average launch time (2 launches per step)"}
 
     e2e = None
     if not args.no_e2e:
-        from paper_1608_06577_gb300 import KT
         import numpy as np
-        with torch.cuda.stream(stream):
-            kt = KT(prob, precision=1 if args.mode == "mixed" else 0)
-        out = {"e": np.empty(cells), "u": np.empty((4, cells))}
+        kt = make_kt(prob, args.mode, weights, stream)
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
@@ -278,16 +299,19 @@ def run_ours(args, world, rank, local):
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
 
     if rank == 0:
+        ncs = lambda r: cells * 2 * r["steps"]  # noqa: E731
         line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": main["steps"],
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f32+f64", "data": "synthetic",
                 "config": {"workload": f"hotspots {n}x{n}x{n} Milne, nonconformal EOS, eta/s 0.08, "
-                                       f"zeta/s gaussian, {args.mode}", "global_batch": world, "seq_len": None,
+                                       f"zeta/s gaussian, dtau 0.005 fm", "global_batch": world, "seq_len": None,
                            "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)",
-                           "precision_mode": args.mode},
+                           "mode": args.mode},
                 "modes": {m: {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
-                              "newton_iters_per_cell_stage": r["stats"]["newton_iters"] / (cells * 2 * r["steps"])}
+                              "newton_iters_per_cell_stage": r["stats"]["newton_iters"] / ncs(r),
+                              "fallbacks_per_cell_stage": r["stats"]["fallbacks"] / ncs(r)}
                           for m, r in results.items()},
+                "learned_training": train_info,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 3 * main["steps"]}
         print(json.dumps(line), flush=True)

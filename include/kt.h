@@ -149,6 +149,39 @@ int kt_get_stats(kt_ctx* ctx, kt_stats* stats);
 const char* kt_last_error(const kt_ctx* ctx);
 void kt_free(kt_ctx* ctx);
 
+/* ------------------------------------------------------------------ learned root-find start
+ * The paper solves Eq. (eInferred) by Newton-Raphson (Sec. 3.2) and states no starting point.
+ * KT_INV_LEARNED starts it from a small network: features (computed by the library from
+ * E = T^tt - pi^tt, M^2 = Mx^2 + My^2 + tau^2 Meta^2 and Pi):
+ *   x = [(ln E - 1)/6, M^2/E^2, 5 Pi/E, ln(1 - M^2/E^2)/2, e_conf/E, |M|/E],
+ * e_conf = sqrt(4E^2 - 3M^2) - E the conformal root; output y, start e = e_conf exp(y/10).
+ * At most 2 FP64 Newton steps follow; a cell whose residual |f(e)|/E then exceeds 1e-10 falls
+ * back to the plain root-find.  Parameters: KT_MLP_NPARAM floats, layout as documented above
+ * KT_MLP_NPARAM.  All pointers below are device pointers; work goes to `stream`. */
+#define KT_MLP_PACKED_BYTES 3396 /* scratch of kt_mlp_predict: packed BF16 weights + FP32 biases */
+
+/* Training samples from the context's current state: for n physical cells (packed indices
+ * i + nx*(j + ny*k), device int64 array `cells`), write the features x [n][6] (float), the
+ * target y = 10 ln(e/e_conf) (float) and the exact root e (double, plain FP64 root-find). */
+int kt_mlp_features(kt_ctx* ctx, long long n, const long long* cells, float* x, float* y, double* e_exact);
+
+/* Inference on tensor cores (mma.sync BF16, FP32 accumulation) for n feature rows x [n][6]
+ * -> y [n].  scratch: caller-owned device memory of at least KT_MLP_PACKED_BYTES that receives
+ * the packed weights (overwritten; calls that share it must not overlap). */
+int kt_mlp_predict(const float* params, const float* x, long long n, float* y, void* scratch, size_t scratch_bytes,
+                   void* stream);
+
+/* Gradient of the mean squared error over n samples with respect to the KT_MLP_NPARAM
+ * parameters: grad [KT_MLP_NPARAM] and loss [1] are overwritten.  bf16_forward = 1 rounds
+ * weights and activations to BF16 in the forward pass as the tensor-core inference does;
+ * 0 runs it in FP32. */
+int kt_mlp_grad(const float* params, const float* x, const float* y_target, long long n, int bf16_forward,
+                float* grad, float* loss, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step number `step` >= 1; m, v are the
+ * caller's moment buffers of KT_MLP_NPARAM floats (zero before the first step). */
+int kt_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

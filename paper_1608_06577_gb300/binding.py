@@ -220,3 +220,79 @@ class KT:
         s = Stats()
         self._check(self.L.kt_get_stats(self.ctx, C.byref(s)), "kt_get_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+# ------------------------------------------------------------------ learned root-find start
+MLP_PACKED_BYTES = 3396
+
+
+def _mlp_lib():
+    L = load_library()
+    if not getattr(L, "_mlp_ready", False):
+        vp, ll = C.c_void_p, C.c_longlong
+        L.kt_mlp_features.argtypes = [vp, ll, vp, vp, vp, vp]
+        L.kt_mlp_predict.argtypes = [vp, vp, ll, vp, vp, C.c_size_t, vp]
+        L.kt_mlp_grad.argtypes = [vp, vp, vp, ll, C.c_int, vp, vp, vp]
+        L.kt_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, vp]
+        L._mlp_ready = True
+    return L
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_handle():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def mlp_predict(params, x, scratch=None):
+    """Tensor-core inference: params [1313] float32 CUDA, x [n, 6] float32 CUDA -> y [n]."""
+    import torch
+    L = _mlp_lib()
+    n = x.shape[0]
+    y = torch.empty(n, dtype=torch.float32, device=x.device)
+    if scratch is None:
+        scratch = torch.empty(MLP_PACKED_BYTES, dtype=torch.uint8, device=x.device)
+    rc = L.kt_mlp_predict(_p(params), _p(x), n, _p(y), _p(scratch), scratch.numel(), _stream_handle())
+    if rc != KT_OK:
+        raise KTError(rc, "kt_mlp_predict")
+    return y
+
+
+def mlp_grad(params, x, y, bf16_forward=True):
+    import torch
+    L = _mlp_lib()
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    rc = L.kt_mlp_grad(_p(params), _p(x), _p(y), x.shape[0], int(bool(bf16_forward)), _p(grad), _p(loss),
+                       _stream_handle())
+    if rc != KT_OK:
+        raise KTError(rc, "kt_mlp_grad")
+    return grad, loss
+
+
+def mlp_adam(params, grad, m, v, step, lr):
+    L = _mlp_lib()
+    rc = L.kt_mlp_adam(_p(params), _p(grad), _p(m), _p(v), int(step), float(lr), _stream_handle())
+    if rc != KT_OK:
+        raise KTError(rc, "kt_mlp_adam")
+
+
+def _kt_mlp_features(self, cells):
+    """Training samples at physical cells (CUDA int64 tensor): features [n, 6], target [n],
+    exact root e [n] (float64)."""
+    import torch
+    L = _mlp_lib()
+    n = cells.numel()
+    cells = cells.to(dtype=torch.int64).contiguous()
+    x = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    e = torch.empty(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    self._check(L.kt_mlp_features(self.ctx, n, _p(cells), _p(x), _p(y), _p(e)), "kt_mlp_features")
+    return x, y, e
+
+
+KT.mlp_features = _kt_mlp_features

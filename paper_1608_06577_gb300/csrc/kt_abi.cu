@@ -15,7 +15,7 @@ using namespace kt;
 
 namespace {
 
-constexpr int KSTAT_WORDS = 8;  // device stats block: status, max speed bits, pad, 3 counters
+constexpr int KSTAT_WORDS = 12;  // device stats block: status, max speed bits, pad, 3 u64 counters from word 4
 
 struct Ctx {
   kt_options opt;
@@ -40,6 +40,8 @@ struct Ctx {
   double* d_tau = nullptr;
   unsigned* d_stat = nullptr;  // [0] status [1] max speed bits [2..] counters (u64 aligned at +4 words)
   float* d_mlp = nullptr;
+  uint32_t* d_mlp_packed = nullptr;
+  int learned = 0;
   int cur = 0, prev = 1, spare = 2;
   double tau = 0.0;
   long long steps = 0;
@@ -93,6 +95,7 @@ size_t state_bytes(const Lattice& L, int mixed, int eos_n) {
   b += 256;                                    // tau
   b += 256;                                    // stats
   b += align_up(KT_MLP_NPARAM * 4, 256);       // MLP weights
+  b += align_up(KT_MLP_PACKED_BYTES, 256);     // packed MLP weights
   return b;
 }
 
@@ -226,6 +229,39 @@ __global__ void gather_kernel(const Params P, const S* __restrict__ f, double* o
 
 __global__ void advance_tau_kernel(double* tau, double dtau) { tau[0] += dtau; }
 
+// training samples of the learned start: features as the stage kernel forms them, the exact
+// FP64 root and the target 10 ln(e / e_conf)
+__global__ void mlp_features_kernel(const Params P, const double* __restrict__ q, double tau, long long n,
+                                    const long long* __restrict__ cells, float* X, float* Y, double* Eexact,
+                                    unsigned* status) {
+  const Lattice& L = P.L;
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const long long ncp = (long long)L.nx * L.ny * L.nz;
+  const long long o = cells[s];
+  if (o < 0 || o >= ncp) {
+    atomicOr(status, ST_INVERSION);
+    return;
+  }
+  const int i = (int)(o % L.nx), j = (int)((o / L.nx) % L.ny), k = (int)(o / ((long long)L.nx * L.ny));
+  const long long c = L.idx(i + 2, j + 2, k + 2);
+  double qn[NQ];
+  for (int m = 0; m < NQ; ++m) qn[m] = q[m * L.fstride + c];
+  const float Ef = d2f_bits(qn[0] - qn[4]);
+  const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
+  const double g = P.milne ? tau * tau : 1.0;
+  const float M2f = d2f_bits(fma(Mx, Mx, fma(My, My, g * Mn * Mn)));
+  float x[MLP_IN], ecE;
+  mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_bits(qn[14]), x, ecE);
+  double e, P0, uo[4];
+  unsigned it = 0;
+  const unsigned st = invert_fp64(P, tau, qn, qn[0] - qn[4], e, P0, uo, it);
+  if (st) atomicOr(status, st);
+  for (int m = 0; m < MLP_IN; ++m) X[s * MLP_IN + m] = x[m];
+  Y[s] = (float)(10.0 * log(e / ((double)Ef * (double)ecE)));
+  Eexact[s] = e;
+}
+
 // ------------------------------------------------------------------ launches
 template <typename R>
 StageIO<R> make_io(Ctx* c, int stage) {
@@ -257,7 +293,7 @@ StageIO<R> make_io(Ctx* c, int stage) {
   io.status = c->d_stat;
   io.max_speed_bits = c->d_stat + 1;
   io.counters = (unsigned long long*)(c->d_stat + 4);
-  io.mlp = nullptr;
+  io.mlp_packed = c->learned ? c->d_mlp_packed : nullptr;
   return io;
 }
 
@@ -270,12 +306,15 @@ dim3 stage_grid(const Lattice& L) {
 // enqueue one full step (two stages + tau advance) for the current rotation phase, then rotate
 int enqueue_step(Ctx* c) {
   dim3 g = stage_grid(c->P.L), b = stage_block();
-  if (c->mixed) {
-    stage_kernel<float, 1><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 1));
-    stage_kernel<float, 2><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 2));
+  if (c->mixed && c->learned) {
+    stage_kernel<float, 1, true><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 1));
+    stage_kernel<float, 2, true><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 2));
+  } else if (c->mixed) {
+    stage_kernel<float, 1, false><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 1));
+    stage_kernel<float, 2, false><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 2));
   } else {
-    stage_kernel<double, 1><<<g, b, 0, c->stream>>>(c->P, make_io<double>(c, 1));
-    stage_kernel<double, 2><<<g, b, 0, c->stream>>>(c->P, make_io<double>(c, 2));
+    stage_kernel<double, 1, false><<<g, b, 0, c->stream>>>(c->P, make_io<double>(c, 1));
+    stage_kernel<double, 2, false><<<g, b, 0, c->stream>>>(c->P, make_io<double>(c, 2));
   }
   advance_tau_kernel<<<1, 1, 0, c->stream>>>(c->d_tau, c->P.dtau);
   // u^{n-1} <- u^n, u^n <- u^{n+1}; the old u^{n-1} buffer (holding u^*) becomes the spare
@@ -358,7 +397,9 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   if (!(o.theta_limiter >= 1.0 && o.theta_limiter <= 2.0)) return bail(KT_ERR_ARG);
   if (o.coords != KT_MILNE && o.coords != KT_CARTESIAN) return bail(KT_ERR_ARG);
   if (o.bc != KT_BC_COPY && o.bc != KT_BC_PERIODIC) return bail(KT_ERR_ARG);
-  if (o.inversion == KT_INV_LEARNED && !o.mlp_weights) return bail(KT_ERR_ARG);
+  if (o.inversion != KT_INV_PLAIN && o.inversion != KT_INV_LEARNED) return bail(KT_ERR_ARG);
+  // the learned start serves the mixed-precision path
+  if (o.inversion == KT_INV_LEARNED && (!o.mlp_weights || o.precision != KT_MIXED)) return bail(KT_ERR_ARG);
   c->mixed = (o.precision == KT_MIXED);
   c->esz = c->mixed ? 4 : 8;
 
@@ -451,6 +492,7 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   c->d_tau = (double*)carve(256);
   c->d_stat = (unsigned*)carve(256);
   c->d_mlp = (float*)carve(KT_MLP_NPARAM * 4);
+  c->d_mlp_packed = (uint32_t*)carve(KT_MLP_PACKED_BYTES);
   P.seg_d = c->seg_d;
   P.seg_f = c->seg_f;
 
@@ -479,7 +521,10 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   }
   if (o.mlp_weights) {
     CK(cudaMemcpyAsync(c->d_mlp, o.mlp_weights, KT_MLP_NPARAM * 4, cudaMemcpyHostToDevice, c->stream));
+    kt::mlp_pack_kernel<<<1, 256, 0, c->stream>>>(c->d_mlp, c->d_mlp_packed);
+    CK(cudaGetLastError());
   }
+  c->learned = (o.inversion == KT_INV_LEARNED);
   CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *out = c;
@@ -548,8 +593,9 @@ int kt_step(kt_ctx* c, int n_steps) {
   CK(cudaStreamSynchronize(c->stream));
   for (int s = 0; s < n_steps; ++s) c->tau += c->P.dtau;
   c->steps += n_steps;
-  unsigned long long cnt[2];
+  unsigned long long cnt[3];
   memcpy(cnt, &hst[4], sizeof(cnt));
+  c->last.fallbacks = (long long)cnt[2];
   c->last.status = hst[0];
   float ms;
   memcpy(&ms, &hst[1], 4);
@@ -590,6 +636,21 @@ int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, doubl
   }
   CK(cudaStreamSynchronize(c->stream));
   if (tau) *tau = c->tau;
+  return KT_OK;
+}
+
+int kt_mlp_features(kt_ctx* c, long long n, const long long* cells, float* x, float* y, double* e_exact) {
+  if (!c || n < 0 || !cells || !x || !y || !e_exact) return c ? fail(c, KT_ERR_ARG, "kt_mlp_features: bad argument") : KT_ERR_ARG;
+  if (!c->have_state) return fail(c, KT_ERR_ARG, "kt_mlp_features: no state set");
+  if (n == 0) return KT_OK;
+  CK(cudaMemsetAsync(c->d_stat, 0, 4, c->stream));
+  mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->P, c->q, c->tau, n, cells, x, y, e_exact,
+                                                                          c->d_stat);
+  CK(cudaGetLastError());
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, c->d_stat, 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st) return fail(c, KT_ERR_INVERSION, "kt_mlp_features: bad cell index or failed root-find");
   return KT_OK;
 }
 

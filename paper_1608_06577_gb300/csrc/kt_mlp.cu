@@ -1,0 +1,214 @@
+// kt_mlp.cu -- training and stand-alone inference kernels of the learned root-find start.
+//
+// Training (SIMT, FP32 accumulation): the forward pass rounds weights and activations to
+// BF16 exactly as the tensor-core inference does (bf16_forward = 1), or runs in plain FP32
+// (bf16_forward = 0, used to check gradients against the FP64 reference); the backward pass
+// treats the rounding as the identity.  Gradients of a mini-batch are reduced with warp
+// shuffles, then shared-memory and global atomics.  Adam updates FP32 master weights.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "../../include/kt.h"
+#include "kt_mlp.cuh"
+
+using namespace kt;
+
+namespace {
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) mlp_grad_kernel(const float* __restrict__ params, const float* __restrict__ X,
+                                                       const float* __restrict__ Y, long long n, float inv_n,
+                                                       float* grad, float* loss) {
+  __shared__ float sw[MLP_NPARAM];
+  __shared__ float sg[MLP_NPARAM];
+  for (int p = threadIdx.x; p < MLP_NPARAM; p += blockDim.x) {
+    sw[p] = BF16 ? bf16r(params[p]) : params[p];
+    sg[p] = 0.f;
+  }
+  // biases are applied in FP32 by the tensor-core path too
+  for (int p = threadIdx.x; p < MLP_H; p += blockDim.x) {
+    sw[OFF_B1 + p] = params[OFF_B1 + p];
+    sw[OFF_B2 + p] = params[OFF_B2 + p];
+  }
+  if (threadIdx.x == 0) sw[OFF_B3] = params[OFF_B3];
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < n;
+  float x[MLP_IN];
+#pragma unroll
+  for (int k = 0; k < MLP_IN; ++k) x[k] = valid ? (BF16 ? bf16r(X[i * MLP_IN + k]) : X[i * MLP_IN + k]) : 0.f;
+  const float yt = valid ? Y[i] : 0.f;
+  // forward
+  float h1[MLP_H], h2[MLP_H];
+#pragma unroll 4
+  for (int j = 0; j < MLP_H; ++j) {
+    float s = sw[OFF_B1 + j];
+#pragma unroll
+    for (int k = 0; k < MLP_IN; ++k) s += sw[OFF_W1 + j * MLP_IN + k] * x[k];
+    s = fmaxf(s, 0.f);
+    h1[j] = BF16 ? bf16r(s) : s;
+  }
+#pragma unroll 2
+  for (int j = 0; j < MLP_H; ++j) {
+    float s = sw[OFF_B2 + j];
+#pragma unroll
+    for (int k = 0; k < MLP_H; ++k) s += sw[OFF_W2 + j * MLP_H + k] * h1[k];
+    s = fmaxf(s, 0.f);
+    h2[j] = BF16 ? bf16r(s) : s;
+  }
+  float y = sw[OFF_B3];
+#pragma unroll
+  for (int k = 0; k < MLP_H; ++k) y += sw[OFF_W3 + k] * h2[k];
+  // mean squared error
+  const float r = valid ? (y - yt) : 0.f;
+  const float dy = 2.f * r * inv_n;
+  const float lsum = warp_sum(r * r * inv_n);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) atomicAdd(loss, lsum);
+  // backward, each parameter's contribution summed over the warp
+  {
+    float s = warp_sum(dy);
+    if (lane == 0) atomicAdd(&sg[OFF_B3], s);
+  }
+  float d2[MLP_H];
+#pragma unroll 1
+  for (int k = 0; k < MLP_H; ++k) {
+    float s = warp_sum(dy * h2[k]);
+    if (lane == 0) atomicAdd(&sg[OFF_W3 + k], s);
+  }
+#pragma unroll
+  for (int k = 0; k < MLP_H; ++k) d2[k] = (h2[k] > 0.f) ? dy * sw[OFF_W3 + k] : 0.f;
+#pragma unroll 1
+  for (int j = 0; j < MLP_H; ++j) {
+    float s = warp_sum(d2[j]);
+    if (lane == 0) atomicAdd(&sg[OFF_B2 + j], s);
+#pragma unroll 1
+    for (int k = 0; k < MLP_H; ++k) {
+      float t = warp_sum(d2[j] * h1[k]);
+      if (lane == 0) atomicAdd(&sg[OFF_W2 + j * MLP_H + k], t);
+    }
+  }
+  float d1[MLP_H];
+#pragma unroll 1
+  for (int k = 0; k < MLP_H; ++k) {
+    float s = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < MLP_H; ++j) s += d2[j] * sw[OFF_W2 + j * MLP_H + k];
+    d1[k] = (h1[k] > 0.f) ? s : 0.f;
+  }
+#pragma unroll 1
+  for (int j = 0; j < MLP_H; ++j) {
+    float s = warp_sum(d1[j]);
+    if (lane == 0) atomicAdd(&sg[OFF_B1 + j], s);
+#pragma unroll
+    for (int k = 0; k < MLP_IN; ++k) {
+      float t = warp_sum(d1[j] * x[k]);
+      if (lane == 0) atomicAdd(&sg[OFF_W1 + j * MLP_IN + k], t);
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < MLP_NPARAM; p += blockDim.x) atomicAdd(&grad[p], sg[p]);
+}
+
+__global__ void mlp_adam_kernel(float* params, const float* __restrict__ grad, float* m, float* v, float lr,
+                                float c1, float c2) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= MLP_NPARAM) return;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float gp = grad[p];
+  const float mp = b1 * m[p] + (1.f - b1) * gp;
+  const float vp = b2 * v[p] + (1.f - b2) * gp * gp;
+  m[p] = mp;
+  v[p] = vp;
+  params[p] -= lr * (mp * c1) / (sqrtf(vp * c2) + eps);
+}
+
+}  // namespace
+
+namespace kt {
+// FP32 parameters -> packed BF16 fragments + FP32 biases (see kt_mlp.cuh)
+__global__ void mlp_pack_kernel(const float* __restrict__ params, uint32_t* packed) {
+  for (int i = threadIdx.x; i < PK_WORDS; i += blockDim.x) {
+    uint32_t v = 0u;
+    if (i < PK_W2) {  // W1 rows of 4 words
+      const int n = i / 4, w = i % 4, k = 2 * w;
+      const float lo = (k < MLP_IN) ? params[OFF_W1 + n * MLP_IN + k] : 0.f;
+      const float hi = (k + 1 < MLP_IN) ? params[OFF_W1 + n * MLP_IN + k + 1] : 0.f;
+      v = pack_bf16x2(lo, hi);
+    } else if (i < PK_W3) {  // W2 rows of 20 words (16 used)
+      const int n = (i - PK_W2) / PK_W2_STRIDE, w = (i - PK_W2) % PK_W2_STRIDE;
+      if (w < 16) v = pack_bf16x2(params[OFF_W2 + n * MLP_H + 2 * w], params[OFF_W2 + n * MLP_H + 2 * w + 1]);
+    } else if (i < PK_B1) {
+      const int w = i - PK_W3;
+      v = pack_bf16x2(params[OFF_W3 + 2 * w], params[OFF_W3 + 2 * w + 1]);
+    } else if (i < PK_B2) {
+      v = __float_as_uint(params[OFF_B1 + (i - PK_B1)]);
+    } else if (i < PK_B3) {
+      v = __float_as_uint(params[OFF_B2 + (i - PK_B2)]);
+    } else {
+      v = __float_as_uint(params[OFF_B3]);
+    }
+    packed[i] = v;
+  }
+}
+
+// tensor-core inference over an array of feature rows
+__global__ void __launch_bounds__(256) mlp_predict_kernel(const uint32_t* __restrict__ packed,
+                                                          const float* __restrict__ X, long long n, float* Y) {
+  __shared__ uint32_t sw[PK_WORDS];
+  mlp_load_shared(sw, packed);
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float x[MLP_IN];
+#pragma unroll
+  for (int k = 0; k < MLP_IN; ++k) x[k] = (i < n) ? X[i * MLP_IN + k] : 0.f;
+  const float y = mlp_warp_infer(sw, x);  // every lane of the warp takes part
+  if (i < n) Y[i] = y;
+}
+}  // namespace kt
+
+extern "C" {
+
+int kt_mlp_predict(const float* params, const float* x, long long n, float* y, void* scratch, size_t scratch_bytes,
+                   void* stream) {
+  if (!params || !x || !y || n < 0 || !scratch || scratch_bytes < (size_t)KT_MLP_PACKED_BYTES) return KT_ERR_ARG;
+  if (n == 0) return KT_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  kt::mlp_pack_kernel<<<1, 256, 0, s>>>(params, (uint32_t*)scratch);
+  kt::mlp_predict_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const uint32_t*)scratch, x, n, y);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
+}
+
+int kt_mlp_grad(const float* params, const float* x, const float* y_target, long long n, int bf16_forward,
+                float* grad, float* loss, void* stream) {
+  if (!params || !x || !y_target || !grad || !loss || n <= 0) return KT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(grad, 0, KT_MLP_NPARAM * sizeof(float), s) != cudaSuccess) return KT_ERR_CUDA;
+  if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return KT_ERR_CUDA;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  const float inv_n = (float)(1.0 / (double)n);
+  if (bf16_forward)
+    mlp_grad_kernel<true><<<nb, 256, 0, s>>>(params, x, y_target, n, inv_n, grad, loss);
+  else
+    mlp_grad_kernel<false><<<nb, 256, 0, s>>>(params, x, y_target, n, inv_n, grad, loss);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
+}
+
+int kt_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, void* stream) {
+  if (!params || !grad || !m || !v || step < 1 || !(lr > 0.f)) return KT_ERR_ARG;
+  const double c1 = 1.0 / (1.0 - std::pow(0.9, step)), c2 = 1.0 / (1.0 - std::pow(0.999, step));
+  mlp_adam_kernel<<<(KT_MLP_NPARAM + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, grad, m, v, lr, (float)c1,
+                                                                                 (float)c2);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -14,6 +14,7 @@
 // R is the arithmetic type of a) and b): double (KT_FP64) or float (KT_MIXED).
 #pragma once
 #include "kt_device.cuh"
+#include "kt_mlp.cuh"
 
 namespace kt {
 
@@ -35,7 +36,7 @@ struct StageIO {
   unsigned* status;
   unsigned* max_speed_bits;
   unsigned long long* counters;  // [0] Newton iterations, [1] regulated cells, [2] fallbacks
-  const float* mlp;      // learned start (null: plain)
+  const uint32_t* mlp_packed;  // learned start: packed weights (see kt_mlp.cuh), or null
 };
 
 // ------------------------------------------------------------------ one direction of a)
@@ -180,6 +181,58 @@ __device__ __forceinline__ unsigned invert_mixed(const Params& P, double tau, co
   return st;
 }
 
+// Learned start: from e_start (the network's prediction) at most two FP64 Newton steps; the
+// cell is accepted as soon as its residual |f(e)| <= 1e-10 E, else it falls back to the plain
+// root-find of invert_mixed, started from the last iterate.
+template <typename R>
+__device__ __forceinline__ unsigned invert_learned(const Params& P, double tau, const double (&qn)[NQ],
+                                                   double e_start, double& e, double& P0, R (&uo)[4],
+                                                   unsigned& iters, unsigned& fallbacks) {
+  const double E = qn[0] - qn[4];
+  const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
+  const double Pi = qn[14];
+  const double gnn = P.milne ? tau * tau : 1.0;
+  const double M2 = fma(Mx, Mx, fma(My, My, gnn * Mn * Mn));
+  const bool closed_form = !P.eos_table && (!P.bulk_on || Pi == 0.0);
+  if (!(E > 0.0) || !isfinite(E) || !isfinite(M2) || !(M2 < E * E) || closed_form)
+    return invert_mixed<R>(P, tau, qn, e_start, e, P0, uo, iters);
+  const double lo = (P.e_min > 0.0) ? P.e_min : 1e-300;
+  e = (e_start >= lo && e_start <= E) ? e_start : E;
+  const float M2f = d2f_bits(M2);
+  const double tol = 1e-10 * E;
+  bool ok = false;
+  double p0 = 0.0;
+  for (int kk = 0; kk < 3; ++kk) {
+    const int i = eos_interval<double>(P, P.seg_d, e);
+    const EosSeg<double>& s = P.seg_d[i];
+    const double t = (e - s.e0) * s.inv_de;
+    p0 = fma(t, fma(t, fma(t, s.cP3, s.cP2), s.mP), s.P0);
+    const double rA = rcp_fp64(E + p0 + Pi);
+    const double f = (e - E) + M2 * rA;
+    if (fabs(f) <= tol) { ok = true; break; }
+    if (kk == 2) break;
+    const EosSeg<float>& sf = P.seg_f[i];
+    const float tf = d2f_bits(t);
+    const float c2 = fmaf(tf, fmaf(tf, 3.f * sf.cP3, 2.f * sf.cP2), sf.mP) * sf.inv_de;
+    const float rAf = d2f_bits(rA);
+    e = fmin(fmax(e - f * f2d_bits(__frcp_rn(1.f - M2f * rAf * rAf * c2)), lo), E);
+    ++iters;
+  }
+  if (!ok) {
+    ++fallbacks;
+    return invert_mixed<R>(P, tau, qn, e, e, P0, uo, iters);
+  }
+  P0 = p0;
+  const double Pt = P0 + Pi;
+  const R ePt = from_f64<R>(e + Pt);
+  const R ut = sqrt(from_f64<R>(E + Pt) / ePt);
+  const R w = R(1) / (ePt * ut);
+  uo[0] = ut; uo[1] = from_f64<R>(Mx) * w; uo[2] = from_f64<R>(My) * w; uo[3] = from_f64<R>(Mn) * w;
+  unsigned st = 0;
+  if (!isfinite(e) || !isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3])) st |= ST_NONFINITE;
+  return st;
+}
+
 __device__ __forceinline__ unsigned invert_fp64(const Params& P, double tau, const double (&qn)[NQ], double guess,
                                                 double& e, double& P0, double (&uo)[4], unsigned& iters) {
   double E = qn[0] - qn[4];
@@ -307,22 +360,31 @@ __device__ __forceinline__ void store_with_ghosts(const Params& P, const StageIO
 }
 
 // ---------------------------------------------------------------- the stage kernel
-template <typename R, int STAGE>
+template <typename R, int STAGE, bool LEARNED>
 __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) stage_kernel(const Params P, const StageIO<R> io) {
   const Lattice& L = P.L;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
   const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
-  unsigned st = 0, nit = 0, nreg = 0;
+  unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
   float amax = 0.f;
+  __shared__ uint32_t s_mlp[LEARNED ? PK_WORDS : 1];
+  if constexpr (LEARNED) {
+    mlp_load_shared(s_mlp, io.mlp_packed);
+    __syncthreads();
+  }
+
+  const long long fs = L.fstride;
+  const long long c = L.idx(i + 2, j + 2, k + 2);
+  const double tau_n = io.d_tau[0];
+  const double tau_src = (STAGE == 1) ? tau_n : tau_n + P.dtau;
+  const double tau_out = tau_n + P.dtau;
+  double qn[NQ];  // the new conserved state (a harmless rest state on lanes past the edge)
+#pragma unroll
+  for (int n = 0; n < NQ; ++n) qn[n] = (n == 0) ? 1.0 : 0.0;
 
   if (valid) {
-    const long long fs = L.fstride;
-    const long long c = L.idx(i + 2, j + 2, k + 2);
-    const double tau_n = io.d_tau[0];
-    const double tau_src = (STAGE == 1) ? tau_n : tau_n + P.dtau;
-    const double tau_out = tau_n + P.dtau;
     const R tau = (R)tau_src;
     const R gnn = P.milne ? tau * tau : R(1);
 
@@ -462,7 +524,6 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) stage_kernel(co
     }
 
     // ---- c) Heun update in FP64 (Eqs. step1-finalStep)
-    double qn[NQ];
 #pragma unroll
     for (int n = 0; n < NQ; ++n) {
       const double qi = __ldg(io.q_in + n * fs + c);
@@ -471,13 +532,30 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) stage_kernel(co
       else  // q^{n+1} = (q^n + q* + dtau C[q*]) / 2
         qn[n] = fma(0.5, io.q_base[n * fs + c] + qi, to_f64<R>(dq[n] * pr<R>(P).half_dtau));
     }
+  }
 
+  // learned start of the root-find: one warp-wide tensor-core pass for 32 cells
+  double e_start = -1.0;
+  if constexpr (LEARNED) {
+    const float Ef = d2f_bits(qn[0] - qn[4]);
+    const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
+    const double gnn_o = P.milne ? tau_out * tau_out : 1.0;
+    const float M2f = d2f_bits(fma(Mx, Mx, fma(My, My, gnn_o * Mn * Mn)));
+    float x[MLP_IN], ecE;
+    mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_bits(qn[14]), x, ecE);
+    const float y = mlp_warp_infer(s_mlp, x);
+    e_start = f2d_bits(Ef * ecE * __expf(0.1f * y));
+  }
+
+  if (valid) {
     // ---- d) inversion at tau^{n+1}
     double e, P0;
     R uo[4];
     const double guess = to_f64<R>(ld<R>(io.e_in, c));
     if constexpr (sizeof(R) == 8)
       st |= invert_fp64(P, tau_out, qn, guess, e, P0, uo, nit);
+    else if constexpr (LEARNED)
+      st |= invert_learned<R>(P, tau_out, qn, e_start, e, P0, uo, nit, nfb);
     else
       st |= invert_mixed<R>(P, tau_out, qn, guess, e, P0, uo, nit);
 
@@ -518,25 +596,29 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) stage_kernel(co
   }
 
   // ---- statistics: warp shuffles, then one atomic per block
-  __shared__ unsigned s_st[8], s_max[8], s_it[8], s_reg[8];
+  __shared__ unsigned s_st[8], s_max[8], s_it[8], s_reg[8], s_fb[8];
   const unsigned full = 0xffffffffu;
   unsigned w_st = __reduce_or_sync(full, st);
   unsigned w_max = __reduce_max_sync(full, __float_as_uint(amax));
   unsigned w_it = __reduce_add_sync(full, nit);
   unsigned w_reg = __reduce_add_sync(full, nreg);
+  unsigned w_fb = __reduce_add_sync(full, nfb);
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int warp = tid >> 5, nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
   if ((tid & 31) == 0) {
-    s_st[warp] = w_st; s_max[warp] = w_max; s_it[warp] = w_it; s_reg[warp] = w_reg;
+    s_st[warp] = w_st; s_max[warp] = w_max; s_it[warp] = w_it; s_reg[warp] = w_reg; s_fb[warp] = w_fb;
   }
   __syncthreads();
   if (tid == 0) {
-    unsigned a = 0, b = 0, cI = 0, d = 0;
-    for (int w = 0; w < nwarps; ++w) { a |= s_st[w]; b = max(b, s_max[w]); cI += s_it[w]; d += s_reg[w]; }
+    unsigned a = 0, b = 0, cI = 0, d = 0, fb = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      a |= s_st[w]; b = max(b, s_max[w]); cI += s_it[w]; d += s_reg[w]; fb += s_fb[w];
+    }
     if (a) atomicOr(io.status, a);
     atomicMax(io.max_speed_bits, b);
     if (cI) atomicAdd(io.counters + 0, (unsigned long long)cI);
     if (d) atomicAdd(io.counters + 1, (unsigned long long)d);
+    if (fb) atomicAdd(io.counters + 2, (unsigned long long)fb);
   }
 }
 
