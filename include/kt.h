@@ -171,6 +171,22 @@ int kt_mlp_features(kt_ctx* ctx, long long n, const long long* cells, float* x, 
 int kt_mlp_predict(const float* params, const float* x, long long n, float* y, void* scratch, size_t scratch_bytes,
                    void* stream);
 
+/* Same inference as kt_mlp_predict without a caller-provided scratch buffer and without any
+ * device allocation.  (The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc, for example code whose device memory is budgeted up front by a host
+ * application or a custom allocator, or latency-critical loops where an allocation and the
+ * synchronisation it may imply are not acceptable.)  The packed weights go to a file-scope
+ * device array of KT_MLP_PACKED_BYTES bytes that every GPU loading the library holds until
+ * the process exits.  The first call on a device looks up that array's device address with
+ * cudaGetSymbolAddress (the current device must be the one the pointers live on); make that
+ * first call before any stream capture.  All calls on a device share the array and it keeps
+ * the last call's contents; each call overwrites all of it before use, so nothing needs
+ * clearing, but calls that overlap on the GPU (other streams, other host threads) race on it.
+ * n is limited to KT_MLP_STATIC_MAX_ROWS rows; larger n, negative n or null pointers return
+ * KT_ERR_ARG with a message on stderr. */
+#define KT_MLP_STATIC_MAX_ROWS 2147483647LL
+int kt_mlp_predict_static(const float* params, const float* x, long long n, float* y, void* stream);
+
 /* Gradient of the mean squared error over n samples with respect to the KT_MLP_NPARAM
  * parameters: grad [KT_MLP_NPARAM] and loss [1] are overwritten.  bf16_forward = 1 rounds
  * weights and activations to BF16 in the forward pass as the tensor-core inference does;

@@ -8,11 +8,44 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
+#include <mutex>
 
 #include "../../include/kt.h"
 #include "kt_mlp.cuh"
 
 using namespace kt;
+
+// Scratch of kt_mlp_predict_static: one packed weight set, KT_MLP_PACKED_BYTES bytes, in a
+// file-scope device array.  Every GPU that loads this library holds it until the process
+// exits.  In host code `g_predict_scratch` is only a host-side stand-in for the symbol: its
+// device address comes from cudaGetSymbolAddress (once per device, cached below).
+static __device__ __align__(256) uint32_t g_predict_scratch[kt::PK_WORDS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+uint32_t* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
+
+// device address of g_predict_scratch on the current device (looked up on first use)
+int static_scratch_address(uint32_t** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return KT_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return KT_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_predict_scratch);
+    if (e != cudaSuccess || !p) {
+      fprintf(stderr, "kt_mlp_predict_static: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+      return KT_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = (uint32_t*)p;
+  }
+  *out = g_scratch_addr[dev];
+  return KT_OK;
+}
+}  // namespace
 
 namespace {
 
@@ -185,6 +218,27 @@ int kt_mlp_predict(const float* params, const float* x, long long n, float* y, v
   cudaStream_t s = (cudaStream_t)stream;
   kt::mlp_pack_kernel<<<1, 256, 0, s>>>(params, (uint32_t*)scratch);
   kt::mlp_predict_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const uint32_t*)scratch, x, n, y);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
+}
+
+int kt_mlp_predict_static(const float* params, const float* x, long long n, float* y, void* stream) {
+  if (!params || !x || !y || n < 0) {
+    fprintf(stderr, "kt_mlp_predict_static: null pointer or negative row count\n");
+    return KT_ERR_ARG;
+  }
+  if (n > KT_MLP_STATIC_MAX_ROWS) {
+    fprintf(stderr, "kt_mlp_predict_static: %lld rows exceed the maximum of %lld\n", n,
+            (long long)KT_MLP_STATIC_MAX_ROWS);
+    return KT_ERR_ARG;
+  }
+  if (n == 0) return KT_OK;
+  uint32_t* scratch = nullptr;
+  const int rc = static_scratch_address(&scratch);
+  if (rc != KT_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the pack kernel overwrites every word of the scratch, so nothing needs clearing first
+  kt::mlp_pack_kernel<<<1, 256, 0, s>>>(params, scratch);
+  kt::mlp_predict_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(scratch, x, n, y);
   return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
 }
 
