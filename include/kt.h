@@ -91,6 +91,8 @@ typedef struct {
   size_t arena_bytes;    /* its size, at least kt_state_bytes() */
   const float* mlp_weights; /* KT_INV_LEARNED: host pointer to KT_MLP_NPARAM floats (see below) */
   int use_graph;         /* 1 (default): kt_step replays a captured CUDA graph of the step loop */
+  int autotune;          /* 1 (default): the first kt_step times the candidate tile shapes (side-effect
+                            free first-stage launches) and keeps the fastest; 0: 32 x 4 x 2 */
 } kt_options;
 
 /* Learned inversion start: an MLP 6 -> 32 -> 32 -> 1 with ReLU; weights row-major
@@ -148,6 +150,25 @@ int kt_get_state(kt_ctx* ctx, double* tau, double* e, double* u, double* pi, dou
 int kt_get_stats(kt_ctx* ctx, kt_stats* stats);
 const char* kt_last_error(const kt_ctx* ctx);
 void kt_free(kt_ctx* ctx);
+
+/* ------------------------------------------------------------------ batches of events
+ * Many independent events (fluctuating initial conditions, uneven grids) share one context:
+ * every field array holds all events, each event's padded lattice at its own offset, and one
+ * persistent launch per Runge-Kutta stage walks a table of (event, tile) work items.  All
+ * events share the physics parameters, dtau and tau.  kt_init is kt_init_batch with one event;
+ * kt_set_state / kt_get_state address event 0.  kt_step advances every event; each event must
+ * have been given a state first.  The results of an event do not depend on the batch it is in. */
+int kt_state_bytes_batch(int n_events, const kt_grid* grids, const kt_options* opt, size_t* bytes);
+int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, double deta, double dtau,
+                  const kt_eos* eos, const kt_coef* eta_over_s, const kt_coef* zeta_over_s, const kt_options* opt);
+int kt_set_state_event(kt_ctx* ctx, int event, double tau, const double* e, const double* u, const double* pi,
+                       const double* Pi, const double* u_prev, int on_device);
+int kt_get_state_event(kt_ctx* ctx, int event, double* tau, double* e, double* u, double* pi, double* Pi, double* q,
+                       int on_device);
+/* The tile shape in use (threads per block x, y, z), the persistent grid size in blocks and,
+ * after autotuning, the measured first-stage time in ms of each candidate shape (up to
+ * *n_candidates entries; *n_candidates is set to the number of candidates). */
+int kt_get_tuning(kt_ctx* ctx, int* block_xyz, int* grid_blocks, float* candidate_ms, int* n_candidates);
 
 /* ------------------------------------------------------------------ learned root-find start
  * The paper solves Eq. (eInferred) by Newton-Raphson (Sec. 3.2) and states no starting point.

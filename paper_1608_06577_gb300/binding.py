@@ -46,7 +46,7 @@ class Options(C.Structure):
                 ("inversion", C.c_int), ("tau_pipi_on", C.c_int), ("regulate", C.c_int), ("rho_max", C.c_double),
                 ("xi0", C.c_double), ("e_min", C.c_double), ("tau_relax_min", C.c_double),
                 ("stream", C.c_void_p), ("arena", C.c_void_p), ("arena_bytes", C.c_size_t),
-                ("mlp_weights", C.POINTER(C.c_float)), ("use_graph", C.c_int)]
+                ("mlp_weights", C.POINTER(C.c_float)), ("use_graph", C.c_int), ("autotune", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -80,6 +80,12 @@ def load_library():
     L.kt_last_error.argtypes = [vp]
     L.kt_free.argtypes = [vp]
     L.kt_free.restype = None
+    L.kt_state_bytes_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Options), C.POINTER(C.c_size_t)]
+    L.kt_init_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Grid), C.c_double, C.c_double, C.c_double,
+                                C.POINTER(Eos), C.POINTER(Coef), C.POINTER(Coef), C.POINTER(Options)]
+    L.kt_set_state_event.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, vp, C.c_int]
+    L.kt_get_state_event.argtypes = [vp, C.c_int, dp, vp, vp, vp, vp, vp, C.c_int]
+    L.kt_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int)]
     _LIB = L
     return L
 
@@ -94,16 +100,22 @@ def _coef(t):
 
 
 class KT:
-    """One libkt context for a problem description (a workload.Problem or a compatible object)."""
+    """One libkt context for a problem description (a workload.Problem or a compatible object),
+    or for a batch: a list of problems that differ only in grid and initial state."""
 
     def __init__(self, prob, precision: int = KT_FP64, inversion: int = KT_INV_PLAIN, mlp_weights=None,
-                 use_graph: bool = True, device_arena: bool = True):
+                 use_graph: bool = True, device_arena: bool = True, autotune: bool = True):
         import torch
         self.torch = torch
         L = load_library()
-        self.prob = prob
-        self.ncells = prob.nx * prob.ny * prob.neta
-        g = Grid(prob.nx, prob.ny, prob.neta)
+        probs = list(prob) if isinstance(prob, (list, tuple)) else [prob]
+        self.probs = probs
+        self.prob = probs[0]
+        prob = probs[0]
+        self.nev = len(probs)
+        self.ncells_ev = [p.nx * p.ny * p.neta for p in probs]
+        self.ncells = self.ncells_ev[0]
+        grids = (Grid * self.nev)(*[Grid(p.nx, p.ny, p.neta) for p in probs])
         o = Options()
         L.kt_options_default(C.byref(o))
         o.theta_limiter = prob.theta
@@ -116,6 +128,7 @@ class KT:
         o.rho_max, o.xi0 = prob.rho_max, prob.xi0
         o.e_min, o.tau_relax_min = prob.e_min, prob.tau_relax_min
         o.use_graph = int(bool(use_graph))
+        o.autotune = int(bool(autotune))
         self.stream = torch.cuda.current_stream()
         o.stream = C.c_void_p(self.stream.cuda_stream)
         self._keep = []
@@ -126,9 +139,9 @@ class KT:
             o.mlp_weights = w.ctypes.data_as(C.POINTER(C.c_float))
         if device_arena:
             nb = C.c_size_t()
-            rc = L.kt_state_bytes(C.byref(g), C.byref(o), C.byref(nb))
+            rc = L.kt_state_bytes_batch(self.nev, grids, C.byref(o), C.byref(nb))
             if rc != KT_OK:
-                raise KTError(rc, "kt_state_bytes")
+                raise KTError(rc, "kt_state_bytes_batch")
             self.arena = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
             o.arena, o.arena_bytes = C.c_void_p(self.arena.data_ptr()), nb.value
         if isinstance(prob.eos, tuple):
@@ -141,8 +154,8 @@ class KT:
             eos = Eos(1, 0.0, t.n, *[a.ctypes.data_as(P) for a in cols])
         ce, cz = _coef(prob.eta_over_s), _coef(prob.zeta_over_s)
         ctx = C.c_void_p()
-        rc = L.kt_init(C.byref(ctx), C.byref(g), prob.dx, prob.deta, prob.dtau, C.byref(eos), C.byref(ce),
-                       C.byref(cz), C.byref(o))
+        rc = L.kt_init_batch(C.byref(ctx), self.nev, grids, prob.dx, prob.deta, prob.dtau, C.byref(eos), C.byref(ce),
+                             C.byref(cz), C.byref(o))
         if rc != KT_OK:
             raise KTError(rc, "kt_init failed")
         self.ctx = ctx
@@ -162,7 +175,7 @@ class KT:
             pass
 
     # ----------------------------------------------------------------------- state
-    def set_state(self, tau, e, u=None, pi=None, Pi=None, u_prev=None):
+    def set_state(self, tau, e, u=None, pi=None, Pi=None, u_prev=None, event=0):
         """Host numpy arrays (physical cells, x fastest) or CUDA torch tensors."""
         torch = self.torch
         arrs = [e, u, pi, Pi, u_prev]
@@ -182,12 +195,12 @@ class KT:
                 h = np.ascontiguousarray(a, dtype=np.float64)
                 keep.append(h)
                 ptrs.append(_dptr(h))
-        rc = self.L.kt_set_state(self.ctx, float(tau), *ptrs, int(on_dev))
+        rc = self.L.kt_set_state_event(self.ctx, int(event), float(tau), *ptrs, int(on_dev))
         return self._check(rc, "kt_set_state")
 
     def set_problem_state(self):
-        p = self.prob
-        return self.set_state(p.tau0, p.e, p.u, p.pi, p.Pi, p.u_prev)
+        for ev, p in enumerate(self.probs):
+            self.set_state(p.tau0, p.e, p.u, p.pi, p.Pi, p.u_prev, event=ev)
 
     def step(self, n=1, check=True):
         rc = self.L.kt_step(self.ctx, int(n))
@@ -195,24 +208,25 @@ class KT:
             self._check(rc, "kt_step")
         return rc
 
-    def get_state(self, fields=("e", "u", "pi", "Pi", "q")):
-        N = self.ncells
+    def get_state(self, fields=("e", "u", "pi", "Pi", "q"), event=0):
+        N = self.ncells_ev[event]
         out = {}
         shapes = {"e": (N,), "u": (4, N), "pi": (10, N), "Pi": (N,), "q": (15, N)}
         for f in ("e", "u", "pi", "Pi", "q"):
             out[f] = np.empty(shapes[f]) if f in fields else None
         tau = C.c_double()
-        rc = self.L.kt_get_state(self.ctx, C.byref(tau), *[_dptr(out[f]) for f in ("e", "u", "pi", "Pi", "q")], 0)
+        rc = self.L.kt_get_state_event(self.ctx, int(event), C.byref(tau),
+                                       *[_dptr(out[f]) for f in ("e", "u", "pi", "Pi", "q")], 0)
         self._check(rc, "kt_get_state")
         out["tau"] = tau.value
         return out
 
-    def get_state_device(self, e=None, u=None, pi=None, Pi=None, q=None):
+    def get_state_device(self, e=None, u=None, pi=None, Pi=None, q=None, event=0):
         """Copy into preallocated CUDA float64 tensors (any may be None)."""
         ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())  # noqa: E731
         self.torch.cuda.synchronize()
         tau = C.c_double()
-        rc = self.L.kt_get_state(self.ctx, C.byref(tau), ptr(e), ptr(u), ptr(pi), ptr(Pi), ptr(q), 1)
+        rc = self.L.kt_get_state_event(self.ctx, int(event), C.byref(tau), ptr(e), ptr(u), ptr(pi), ptr(Pi), ptr(q), 1)
         self._check(rc, "kt_get_state")
         return tau.value
 
@@ -220,6 +234,14 @@ class KT:
         s = Stats()
         self._check(self.L.kt_get_stats(self.ctx, C.byref(s)), "kt_get_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def tuning(self) -> dict:
+        blk = (C.c_int * 3)()
+        grid = C.c_int()
+        ms = (C.c_float * 16)()
+        n = C.c_int(16)
+        self._check(self.L.kt_get_tuning(self.ctx, blk, C.byref(grid), ms, C.byref(n)), "kt_get_tuning")
+        return {"block": tuple(blk), "grid_blocks": grid.value, "candidate_ms": list(ms)[:n.value]}
 
 
 # ------------------------------------------------------------------ learned root-find start

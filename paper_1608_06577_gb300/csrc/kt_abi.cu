@@ -1,6 +1,11 @@
 // kt_abi.cu -- host side of libkt: the C ABI declared in include/kt.h.
+//
+// A context holds one or more events.  Every field array spans all events: component n of
+// event e starts at n * gs + base_e (gs = sum of the events' padded sizes), so one persistent
+// launch per Runge-Kutta stage can walk a table of (event, tile) work items.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -17,35 +22,56 @@ namespace {
 
 constexpr int KSTAT_WORDS = 12;  // device stats block: status, max speed bits, pad, 3 u64 counters from word 4
 
+struct Shape {
+  int x, y, z;
+};
+// candidate tile shapes of the autotuner (threads per block; x stays 32 so a warp is one x-row)
+constexpr Shape kShapes[] = {{32, 4, 2}, {32, 8, 1}, {32, 2, 4}, {32, 1, 8}, {32, 4, 1}, {32, 2, 2}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
 struct Ctx {
   kt_options opt;
   Params P;
-  int mixed;             // 1: float u, e, p and float stencil
-  size_t esz;            // bytes per u/e/p element
-  cudaStream_t stream;
+  int mixed = 0;         // 1: float u, e, p and float stencil
+  size_t esz = 8;        // bytes per u/e/p element
+  cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // events
+  int nev = 0;
+  std::vector<Lattice> lat;
+  long long gs = 0;      // component stride of every field array
+  size_t max_cells = 0;  // physical cells of the largest event
+  std::vector<char> ev_set;
   // device memory
   void* base = nullptr;  // owned allocation (null if caller arena)
   size_t bytes = 0;
-  double* q = nullptr;   // 15 fields
-  double* qs = nullptr;  // 15 fields
+  double* q = nullptr;   // 15 components
+  double* qs = nullptr;  // 15 components
   float* qf = nullptr;   // mixed mode: FP32 copies of q and qs read by the stencil
   float* qsf = nullptr;
-  void* U[3] = {};       // 3 x 4 fields
+  void* U[3] = {};       // 3 x 4 components
   void* E[2] = {};
   void* Pb[2] = {};
-  double* stage = nullptr;  // staging: 18 packed fields
+  double* stage = nullptr;  // staging: 18 packed fields of the largest event
   EosSeg<double>* seg_d = nullptr;
   EosSeg<float>* seg_f = nullptr;
   double* d_tau = nullptr;
-  unsigned* d_stat = nullptr;  // [0] status [1] max speed bits [2..] counters (u64 aligned at +4 words)
+  unsigned* d_stat = nullptr;
   float* d_mlp = nullptr;
   uint32_t* d_mlp_packed = nullptr;
+  Lattice* d_lat = nullptr;
+  Tile* d_tiles = nullptr;
+  int max_tiles = 0;
+  // work decomposition
+  int shape = 0;
+  int ntiles = 0;
+  int grid_blocks = 0;
+  bool tuned = false;
+  float tune_ms[kNumShapes] = {};
   int learned = 0;
   int cur = 0, prev = 1, spare = 2;
   double tau = 0.0;
   long long steps = 0;
-  bool have_state = false;
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // 3-step graph per rotation phase
   kt_stats last{};
   char err[512] = {0};
@@ -61,41 +87,77 @@ int fail(Ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
-#define CK(call)                                                                              \
-  do {                                                                                        \
-    cudaError_t e_ = (call);                                                                  \
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
     if (e_ != cudaSuccess) return fail(c, KT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-Lattice make_lattice(const kt_grid* g) {
-  Lattice L;
-  L.nx = g->nx; L.ny = g->ny; L.nz = g->neta;
-  L.pitch = (int)align_up((size_t)g->nx + 4, 4);
-  L.NY = g->ny + 4;
-  L.NZ = g->neta + 4;
-  L.plane = (long long)L.pitch * L.NY;
-  L.fstride = (long long)align_up((size_t)(L.plane * L.NZ), 32);
-  return L;
+bool grids_ok(int nev, const kt_grid* grids) {
+  if (nev < 1 || !grids) return false;
+  for (int e = 0; e < nev; ++e)
+    if (grids[e].nx < 1 || grids[e].ny < 1 || grids[e].neta < 1) return false;
+  return true;
 }
 
-size_t state_bytes(const Lattice& L, int mixed, int eos_n) {
-  size_t fs = (size_t)L.fstride;
-  size_t es = mixed ? 4 : 8;
+// padded lattices of all events and the shared component stride
+void layout(int nev, const kt_grid* grids, std::vector<Lattice>& lat, long long& gs, size_t& max_cells) {
+  lat.resize(nev);
+  long long off = 0;
+  max_cells = 0;
+  for (int e = 0; e < nev; ++e) {
+    Lattice& L = lat[e];
+    L.nx = grids[e].nx; L.ny = grids[e].ny; L.nz = grids[e].neta;
+    L.pitch = (int)align_up((size_t)L.nx + 4, 4);
+    L.NY = L.ny + 4;
+    L.NZ = L.nz + 4;
+    L.plane = (long long)L.pitch * L.NY;
+    L.base = off;
+    off += (long long)align_up((size_t)(L.plane * L.NZ), 32);
+    max_cells = std::max(max_cells, (size_t)L.nx * L.ny * L.nz);
+  }
+  gs = off;
+  for (auto& L : lat) L.fstride = gs;
+}
+
+int tiles_for(const std::vector<Lattice>& lat, const Shape& s) {
+  long long n = 0;
+  for (const auto& L : lat)
+    n += (long long)((L.nx + s.x - 1) / s.x) * ((L.ny + s.y - 1) / s.y) * ((L.nz + s.z - 1) / s.z);
+  return (int)n;
+}
+
+void build_tiles(const std::vector<Lattice>& lat, const Shape& s, std::vector<Tile>& out) {
+  out.clear();
+  for (int e = 0; e < (int)lat.size(); ++e) {
+    const Lattice& L = lat[e];
+    for (int k = 0; k < L.nz; k += s.z)
+      for (int j = 0; j < L.ny; j += s.y)
+        for (int i = 0; i < L.nx; i += s.x) out.push_back(Tile{e, i, j, k});
+  }
+}
+
+size_t state_bytes(const std::vector<Lattice>& lat, long long gs, size_t max_cells, int mixed, int eos_n) {
+  const size_t fs = (size_t)gs;
+  const size_t es = mixed ? 4 : 8;
+  int max_tiles = 0;
+  for (const auto& s : kShapes) max_tiles = std::max(max_tiles, tiles_for(lat, s));
   size_t b = 0;
   b += align_up(30 * fs * 8, 256);             // q, qs
   if (mixed) b += align_up(30 * fs * 4, 256);  // FP32 copies of q, qs
   b += align_up(12 * fs * es, 256);            // U[3]
   b += align_up(4 * fs * es, 256);             // E[2], P[2]
-  size_t ncell = (size_t)L.nx * L.ny * L.nz;
-  b += align_up(18 * ncell * 8, 256);          // staging
+  b += align_up(18 * max_cells * 8, 256);      // staging
   b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(EosSeg<double>), 256);
   b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(EosSeg<float>), 256);
   b += 256;                                    // tau
   b += 256;                                    // stats
   b += align_up(KT_MLP_NPARAM * 4, 256);       // MLP weights
   b += align_up(KT_MLP_PACKED_BYTES, 256);     // packed MLP weights
+  b += align_up(lat.size() * sizeof(Lattice), 256);
+  b += align_up((size_t)max_tiles * sizeof(Tile), 256);
   return b;
 }
 
@@ -152,11 +214,11 @@ void build_segments(const kt_eos* eos, std::vector<EosSeg<R>>& out) {
 // ------------------------------------------------------------------ small kernels
 __device__ __forceinline__ double gnn_at(const Params& P, double tau) { return P.milne ? tau * tau : 1.0; }
 
+// conserved variables from primaries (Eqs. Ttt, Tti) for one event, with its ghost copies
 template <typename R>
-__global__ void set_state_kernel(const Params P, const double* __restrict__ in, int has_u, int has_pi, int has_Pi,
-                                 int has_up, double tau, double* q, float* qf, R* U, R* Up, R* E, R* Pb,
+__global__ void set_state_kernel(const Params P, const Lattice L, const double* __restrict__ in, int has_u, int has_pi,
+                                 int has_Pi, int has_up, double tau, double* q, float* qf, R* U, R* Up, R* E, R* Pb,
                                  unsigned* status) {
-  const Lattice& L = P.L;
   long long ncp = (long long)L.nx * L.ny * L.nz;
   long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= ncp) return;
@@ -176,7 +238,6 @@ __global__ void set_state_kernel(const Params P, const double* __restrict__ in, 
   double P0 = eos_P<double>(P, e);
   double Pt = P0 + Pi;
   double qn[NQ];
-  // Eqs. (Ttt), (Tti)
   qn[0] = (e + Pt) * ut * ut - Pt + pi[0];
   qn[1] = (e + Pt) * ut * ux + pi[1];
   qn[2] = (e + Pt) * ut * uy + pi[2];
@@ -194,7 +255,6 @@ __global__ void set_state_kernel(const Params P, const double* __restrict__ in, 
   bool bad = !isfinite(e) || !(e >= 0.0) || !isfinite(ut) || !isfinite(Pi) || !isfinite(up4[0]);
   for (int m = 0; m < 10; ++m) bad |= !isfinite(pi[m]);
   if (bad) atomicOr(status, ST_NONFINITE);
-  // store own cell and the ghosts it owns
   const long long fs = L.fstride;
   const int pc[3] = {i + 2, j + 2, k + 2};
   const int nn[3] = {L.nx, L.ny, L.nz};
@@ -216,10 +276,9 @@ __global__ void set_state_kernel(const Params P, const double* __restrict__ in, 
   }
 }
 
-// gather one padded field (double or float) into a packed physical array
+// gather one component of one event (double or float) into a packed physical array
 template <typename S>
-__global__ void gather_kernel(const Params P, const S* __restrict__ f, double* out) {
-  const Lattice& L = P.L;
+__global__ void gather_kernel(const Lattice L, const S* __restrict__ f, double* out) {
   long long ncp = (long long)L.nx * L.ny * L.nz;
   long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= ncp) return;
@@ -231,10 +290,9 @@ __global__ void advance_tau_kernel(double* tau, double dtau) { tau[0] += dtau; }
 
 // training samples of the learned start: features as the stage kernel forms them, the exact
 // FP64 root and the target 10 ln(e / e_conf)
-__global__ void mlp_features_kernel(const Params P, const double* __restrict__ q, double tau, long long n,
-                                    const long long* __restrict__ cells, float* X, float* Y, double* Eexact,
-                                    unsigned* status) {
-  const Lattice& L = P.L;
+__global__ void mlp_features_kernel(const Params P, const Lattice L, const double* __restrict__ q, double tau,
+                                    long long n, const long long* __restrict__ cells, float* X, float* Y,
+                                    double* Eexact, unsigned* status) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const long long ncp = (long long)L.nx * L.ny * L.nz;
@@ -266,8 +324,6 @@ __global__ void mlp_features_kernel(const Params P, const double* __restrict__ q
 template <typename R>
 StageIO<R> make_io(Ctx* c, int stage) {
   StageIO<R> io;
-  const long long fs = c->P.L.fstride;
-  (void)fs;
   R* U0 = (R*)c->U[c->cur];
   R* Uprev = (R*)c->U[c->prev];
   R* Usp = (R*)c->U[c->spare];
@@ -297,25 +353,24 @@ StageIO<R> make_io(Ctx* c, int stage) {
   return io;
 }
 
-dim3 stage_block() { return dim3(32, 4, 2); }
-dim3 stage_grid(const Lattice& L) {
-  dim3 b = stage_block();
-  return dim3((L.nx + b.x - 1) / b.x, (L.ny + b.y - 1) / b.y, (L.nz + b.z - 1) / b.z);
+template <typename R, int STAGE, bool LEARNED>
+void launch_stage(Ctx* c, const StageIO<R>& io) {
+  const Shape& s = kShapes[c->shape];
+  stage_kernel<R, STAGE, LEARNED><<<c->grid_blocks, dim3(s.x, s.y, s.z), 0, c->stream>>>(c->P, io, c->d_lat,
+                                                                                         c->d_tiles, c->ntiles);
+}
+
+template <typename R, bool LEARNED>
+void launch_step_stages(Ctx* c) {
+  launch_stage<R, 1, LEARNED>(c, make_io<R>(c, 1));
+  launch_stage<R, 2, LEARNED>(c, make_io<R>(c, 2));
 }
 
 // enqueue one full step (two stages + tau advance) for the current rotation phase, then rotate
 int enqueue_step(Ctx* c) {
-  dim3 g = stage_grid(c->P.L), b = stage_block();
-  if (c->mixed && c->learned) {
-    stage_kernel<float, 1, true><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 1));
-    stage_kernel<float, 2, true><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 2));
-  } else if (c->mixed) {
-    stage_kernel<float, 1, false><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 1));
-    stage_kernel<float, 2, false><<<g, b, 0, c->stream>>>(c->P, make_io<float>(c, 2));
-  } else {
-    stage_kernel<double, 1, false><<<g, b, 0, c->stream>>>(c->P, make_io<double>(c, 1));
-    stage_kernel<double, 2, false><<<g, b, 0, c->stream>>>(c->P, make_io<double>(c, 2));
-  }
+  if (c->mixed && c->learned) launch_step_stages<float, true>(c);
+  else if (c->mixed) launch_step_stages<float, false>(c);
+  else launch_step_stages<double, false>(c);
   advance_tau_kernel<<<1, 1, 0, c->stream>>>(c->d_tau, c->P.dtau);
   // u^{n-1} <- u^n, u^n <- u^{n+1}; the old u^{n-1} buffer (holding u^*) becomes the spare
   int ncur = c->spare, nprev = c->cur, nspare = c->prev;
@@ -325,9 +380,73 @@ int enqueue_step(Ctx* c) {
   return KT_OK;
 }
 
-int phase_of(const Ctx* c) {
-  // three rotation phases, identified by which buffer is current
-  return c->cur;
+// persistent grid: as many blocks as fit on the device at once, at most one per tile
+template <typename R, bool LEARNED>
+int occupancy_blocks(const Shape& s) {
+  int nb = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<R, 1, LEARNED>, s.x * s.y * s.z, 0);
+  return std::max(1, nb) * std::max(1, sms);
+}
+
+int select_shape(Ctx* c, int shape) {
+  std::vector<Tile> tiles;
+  build_tiles(c->lat, kShapes[shape], tiles);
+  if ((int)tiles.size() > c->max_tiles) return fail(c, KT_ERR_OOM, "tile table overflow");
+  CK(cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->shape = shape;
+  c->ntiles = (int)tiles.size();
+  int cap;
+  if (c->mixed && c->learned) cap = occupancy_blocks<float, true>(kShapes[shape]);
+  else if (c->mixed) cap = occupancy_blocks<float, false>(kShapes[shape]);
+  else cap = occupancy_blocks<double, false>(kShapes[shape]);
+  c->grid_blocks = std::max(1, std::min(cap, c->ntiles));
+  for (int p = 0; p < 3; ++p)
+    if (c->graph[p]) { cudaGraphExecDestroy(c->graph[p]); c->graph[p] = nullptr; }
+  return KT_OK;
+}
+
+// Autotuner: time a first-stage launch for every candidate tile shape.  The launches write only
+// scratch buffers (q*, its FP32 copy, e*, p*, and u* redirected to the spare buffer), so the
+// state is untouched; the fastest shape is kept.
+template <typename R, bool LEARNED>
+int time_first_stage(Ctx* c, float* ms) {
+  StageIO<R> io = make_io<R>(c, 1);
+  io.u_out = (R*)c->U[c->spare];
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  launch_stage<R, 1, LEARNED>(c, io);  // warm-up
+  CK(cudaEventRecord(a, c->stream));
+  launch_stage<R, 1, LEARNED>(c, io);
+  CK(cudaEventRecord(b, c->stream));
+  CK(cudaEventSynchronize(b));
+  CK(cudaEventElapsedTime(ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return KT_OK;
+}
+
+int autotune(Ctx* c) {
+  int best = 0;
+  for (int s = 0; s < kNumShapes; ++s) {
+    int rc = select_shape(c, s);
+    if (rc != KT_OK) return rc;
+    float ms = 0.f;
+    if (c->mixed && c->learned) rc = time_first_stage<float, true>(c, &ms);
+    else if (c->mixed) rc = time_first_stage<float, false>(c, &ms);
+    else rc = time_first_stage<double, false>(c, &ms);
+    if (rc != KT_OK) return rc;
+    c->tune_ms[s] = ms;
+    if (ms < c->tune_ms[best]) best = s;
+  }
+  int rc = select_shape(c, best);
+  if (rc != KT_OK) return rc;
+  CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
+  c->tuned = true;
+  return KT_OK;
 }
 
 int build_graph(Ctx* c, int phase) {
@@ -368,26 +487,35 @@ int kt_options_default(kt_options* o) {
   o->e_min = 0.0;
   o->tau_relax_min = 0.0;
   o->use_graph = 1;
+  o->autotune = 1;
+  return KT_OK;
+}
+
+int kt_state_bytes_batch(int n_events, const kt_grid* grids, const kt_options* opt, size_t* bytes) {
+  if (!bytes || !grids_ok(n_events, grids)) return KT_ERR_ARG;
+  kt_options d;
+  kt_options_default(&d);
+  const kt_options* o = opt ? opt : &d;
+  std::vector<Lattice> lat;
+  long long gs;
+  size_t mc;
+  layout(n_events, grids, lat, gs, mc);
+  *bytes = state_bytes(lat, gs, mc, o->precision == KT_MIXED, 4097);
   return KT_OK;
 }
 
 int kt_state_bytes(const kt_grid* grid, const kt_options* opt, size_t* bytes) {
-  if (!grid || !bytes || grid->nx < 1 || grid->ny < 1 || grid->neta < 1) return KT_ERR_ARG;
-  kt_options d;
-  kt_options_default(&d);
-  const kt_options* o = opt ? opt : &d;
-  *bytes = state_bytes(make_lattice(grid), o->precision == KT_MIXED, 4097);
-  return KT_OK;
+  return kt_state_bytes_batch(1, grid, opt, bytes);
 }
 
-int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dtau, const kt_eos* eos,
-            const kt_coef* eta_over_s, const kt_coef* zeta_over_s, const kt_options* opt) {
+int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, double deta, double dtau,
+                  const kt_eos* eos, const kt_coef* eta_over_s, const kt_coef* zeta_over_s, const kt_options* opt) {
   if (!out) return KT_ERR_ARG;
   *out = nullptr;
   kt_ctx* c = new (std::nothrow) kt_ctx();
   if (!c) return KT_ERR_OOM;
   auto bail = [&](int code) { kt_free(c); return code; };
-  if (!grid || grid->nx < 1 || grid->ny < 1 || grid->neta < 1 || !(dx > 0) || !(deta > 0) || !(dtau > 0) || !eos) {
+  if (!grids_ok(n_events, grids) || !(dx > 0) || !(deta > 0) || !(dtau > 0) || !eos) {
     fprintf(stderr, "kt_init: invalid grid, spacing or eos\n");
     return bail(KT_ERR_ARG);
   }
@@ -402,10 +530,13 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   if (o.inversion == KT_INV_LEARNED && (!o.mlp_weights || o.precision != KT_MIXED)) return bail(KT_ERR_ARG);
   c->mixed = (o.precision == KT_MIXED);
   c->esz = c->mixed ? 4 : 8;
+  c->learned = (o.inversion == KT_INV_LEARNED);
+  c->nev = n_events;
+  layout(n_events, grids, c->lat, c->gs, c->max_cells);
+  c->ev_set.assign(n_events, 0);
 
   Params& P = c->P;
   memset(&P, 0, sizeof(P));
-  P.L = make_lattice(grid);
   P.dx = dx; P.dy = dx; P.deta = deta; P.dtau = dtau;
   P.theta = o.theta_limiter;
   P.milne = (o.coords == KT_MILNE);
@@ -445,7 +576,6 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
     fprintf(stderr, "kt_init: no CUDA device (libkt has no CPU fallback)\n");
     return bail(KT_ERR_CUDA);
   }
-
   // every call synchronises its stream before returning, so a context-owned stream is safe when
   // the caller passes none (the legacy default stream cannot be captured into a graph)
   c->stream = (cudaStream_t)o.stream;
@@ -458,7 +588,7 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   }
 
   // ---- device memory, carved from one block
-  size_t need = state_bytes(P.L, c->mixed, P.eos_n);
+  size_t need = state_bytes(c->lat, c->gs, c->max_cells, c->mixed, P.eos_n);
   char* base;
   if (o.arena) {
     if (o.arena_bytes < need) return bail(KT_ERR_OOM);
@@ -470,7 +600,7 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   c->bytes = need;
   size_t off = 0;
   auto carve = [&](size_t b) { void* p = base + off; off += align_up(b, 256); return p; };
-  const size_t fs = (size_t)P.L.fstride;
+  const size_t fs = (size_t)c->gs;
   char* qq = (char*)carve(30 * fs * 8);
   c->q = (double*)qq;
   c->qs = (double*)(qq + 15 * fs * 8);
@@ -484,8 +614,7 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   for (int b = 0; b < 3; ++b) c->U[b] = uu + (size_t)b * 4 * fs * c->esz;
   char* ep = (char*)carve(4 * fs * c->esz);
   c->E[0] = ep; c->E[1] = ep + fs * c->esz; c->Pb[0] = ep + 2 * fs * c->esz; c->Pb[1] = ep + 3 * fs * c->esz;
-  size_t ncell = (size_t)P.L.nx * P.L.ny * P.L.nz;
-  c->stage = (double*)carve(18 * ncell * 8);
+  c->stage = (double*)carve(18 * c->max_cells * 8);
   int nseg = P.eos_n > 0 ? P.eos_n : 1;
   c->seg_d = (EosSeg<double>*)carve(nseg * sizeof(EosSeg<double>));
   c->seg_f = (EosSeg<float>*)carve(nseg * sizeof(EosSeg<float>));
@@ -493,22 +622,24 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
   c->d_stat = (unsigned*)carve(256);
   c->d_mlp = (float*)carve(KT_MLP_NPARAM * 4);
   c->d_mlp_packed = (uint32_t*)carve(KT_MLP_PACKED_BYTES);
+  c->d_lat = (Lattice*)carve(c->lat.size() * sizeof(Lattice));
+  for (const auto& s : kShapes) c->max_tiles = std::max(c->max_tiles, tiles_for(c->lat, s));
+  c->d_tiles = (Tile*)carve((size_t)c->max_tiles * sizeof(Tile));
   P.seg_d = c->seg_d;
   P.seg_f = c->seg_f;
 
   CK(cudaMemsetAsync(qq, 0, 30 * fs * 8, c->stream));
   CK(cudaMemsetAsync(ep, 0, 4 * fs * c->esz, c->stream));
-  // unused corner ghosts hold a fluid at rest (u^tau = 1); they are never read
-  {
-    std::vector<unsigned char> one(4 * fs * c->esz, 0);
+  {  // unused corner ghosts hold a fluid at rest (u^tau = 1); they are never read
+    std::vector<unsigned char> one(fs * c->esz, 0);
     for (size_t i = 0; i < fs; ++i) {
       if (c->mixed) { float v = 1.f; memcpy(&one[i * 4], &v, 4); }
       else { double v = 1.0; memcpy(&one[i * 8], &v, 8); }
     }
-    for (int b = 0; b < 3; ++b) CK(cudaMemcpyAsync(c->U[b], one.data(), one.size(), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync((char*)c->U[0] + fs * c->esz, 0, 3 * fs * c->esz, c->stream));
-    CK(cudaMemsetAsync((char*)c->U[1] + fs * c->esz, 0, 3 * fs * c->esz, c->stream));
-    CK(cudaMemsetAsync((char*)c->U[2] + fs * c->esz, 0, 3 * fs * c->esz, c->stream));
+    for (int b = 0; b < 3; ++b) {
+      CK(cudaMemcpyAsync(c->U[b], one.data(), one.size(), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemsetAsync((char*)c->U[b] + fs * c->esz, 0, 3 * fs * c->esz, c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
   }
   if (P.eos_table) {
@@ -524,17 +655,26 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
     kt::mlp_pack_kernel<<<1, 256, 0, c->stream>>>(c->d_mlp, c->d_mlp_packed);
     CK(cudaGetLastError());
   }
-  c->learned = (o.inversion == KT_INV_LEARNED);
+  CK(cudaMemcpyAsync(c->d_lat, c->lat.data(), c->lat.size() * sizeof(Lattice), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  int rc = select_shape(c, 0);
+  if (rc != KT_OK) return bail(rc);
   *out = c;
   return KT_OK;
 }
 
-int kt_set_state(kt_ctx* c, double tau, const double* e, const double* u, const double* pi, const double* Pi,
-                 const double* u_prev, int on_device) {
-  if (!c || !e || !(tau > 0 || !c->P.milne)) return c ? fail(c, KT_ERR_ARG, "kt_set_state: bad argument") : KT_ERR_ARG;
-  const Lattice& L = c->P.L;
+int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dtau, const kt_eos* eos,
+            const kt_coef* eta_over_s, const kt_coef* zeta_over_s, const kt_options* opt) {
+  return kt_init_batch(out, 1, grid, dx, deta, dtau, eos, eta_over_s, zeta_over_s, opt);
+}
+
+int kt_set_state_event(kt_ctx* c, int event, double tau, const double* e, const double* u, const double* pi,
+                       const double* Pi, const double* u_prev, int on_device) {
+  if (!c) return KT_ERR_ARG;
+  if (event < 0 || event >= c->nev || !e || !(tau > 0 || !c->P.milne))
+    return fail(c, KT_ERR_ARG, "kt_set_state: bad argument");
+  const Lattice& L = c->lat[event];
   size_t ncp = (size_t)L.nx * L.ny * L.nz;
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   double* s = c->stage;
@@ -546,42 +686,53 @@ int kt_set_state(kt_ctx* c, double tau, const double* e, const double* u, const 
   CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
   double tau_h = tau;
   CK(cudaMemcpyAsync(c->d_tau, &tau_h, 8, cudaMemcpyHostToDevice, c->stream));
-  c->cur = 0; c->prev = 1; c->spare = 2;
   int nb = (int)((ncp + 255) / 256);
+  // the state goes into the buffers that hold u^n and u^{n-1} in the current rotation
   if (c->mixed)
-    set_state_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, s, u != nullptr, pi != nullptr, Pi != nullptr,
-                                                       u_prev != nullptr, tau, c->q, c->qf, (float*)c->U[0], (float*)c->U[1],
-                                                       (float*)c->E[0], (float*)c->Pb[0], c->d_stat);
+    set_state_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, L, s, u != nullptr, pi != nullptr, Pi != nullptr,
+                                                       u_prev != nullptr, tau, c->q, c->qf, (float*)c->U[c->cur],
+                                                       (float*)c->U[c->prev], (float*)c->E[0], (float*)c->Pb[0],
+                                                       c->d_stat);
   else
-    set_state_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, s, u != nullptr, pi != nullptr, Pi != nullptr,
-                                                        u_prev != nullptr, tau, c->q, nullptr, (double*)c->U[0], (double*)c->U[1],
-                                                        (double*)c->E[0], (double*)c->Pb[0], c->d_stat);
+    set_state_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, L, s, u != nullptr, pi != nullptr, Pi != nullptr,
+                                                        u_prev != nullptr, tau, c->q, nullptr, (double*)c->U[c->cur],
+                                                        (double*)c->U[c->prev], (double*)c->E[0], (double*)c->Pb[0],
+                                                        c->d_stat);
   CK(cudaGetLastError());
   unsigned st = 0;
   CK(cudaMemcpyAsync(&st, c->d_stat, 4, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->tau = tau;
   c->steps = 0;
-  c->have_state = true;
+  c->ev_set[event] = 1;
   if (st) return fail(c, KT_ERR_STATE, "kt_set_state: non-finite or negative input");
   return KT_OK;
 }
 
+int kt_set_state(kt_ctx* c, double tau, const double* e, const double* u, const double* pi, const double* Pi,
+                 const double* u_prev, int on_device) {
+  return kt_set_state_event(c, 0, tau, e, u, pi, Pi, u_prev, on_device);
+}
+
 int kt_step(kt_ctx* c, int n_steps) {
   if (!c || n_steps < 0) return KT_ERR_ARG;
-  if (!c->have_state) return fail(c, KT_ERR_ARG, "kt_step: no state set");
+  for (int e = 0; e < c->nev; ++e)
+    if (!c->ev_set[e]) return fail(c, KT_ERR_ARG, "kt_step: event %d has no state", e);
+  if (c->opt.autotune && !c->tuned && n_steps > 0) {
+    int rc = autotune(c);
+    if (rc != KT_OK) return rc;
+  }
   CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
   int done = 0;
   if (c->opt.use_graph) {
     while (n_steps - done >= 3) {
-      int ph = phase_of(c);
+      int ph = c->cur;  // the three rotation phases are told apart by the current u buffer
       if (!c->graph[ph]) {
         int rc = build_graph(c, ph);
         if (rc != KT_OK) return rc;
       }
       CK(cudaGraphLaunch(c->graph[ph], c->stream));
-      // three steps return the rotation to the same phase
-      done += 3;
+      done += 3;  // three steps return the rotation to the same phase
     }
   }
   for (; done < n_steps; ++done) {
@@ -595,26 +746,28 @@ int kt_step(kt_ctx* c, int n_steps) {
   c->steps += n_steps;
   unsigned long long cnt[3];
   memcpy(cnt, &hst[4], sizeof(cnt));
-  c->last.fallbacks = (long long)cnt[2];
   c->last.status = hst[0];
   float ms;
   memcpy(&ms, &hst[1], 4);
   c->last.max_speed = ms;
   c->last.newton_iters = (long long)cnt[0];
   c->last.regulated = (long long)cnt[1];
+  c->last.fallbacks = (long long)cnt[2];
   if (hst[0] & ST_NONFINITE) return fail(c, KT_ERR_NONFINITE, "kt_step: non-finite value");
   if (hst[0] & ST_INVERSION) return fail(c, KT_ERR_INVERSION, "kt_step: inversion failed in some cell");
   return KT_OK;
 }
 
-int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, double* Pi, double* q, int on_device) {
+int kt_get_state_event(kt_ctx* c, int event, double* tau, double* e, double* u, double* pi, double* Pi, double* q,
+                       int on_device) {
   if (!c) return KT_ERR_ARG;
-  const Lattice& L = c->P.L;
+  if (event < 0 || event >= c->nev) return fail(c, KT_ERR_ARG, "kt_get_state: bad event");
+  const Lattice& L = c->lat[event];
   size_t ncp = (size_t)L.nx * L.ny * L.nz;
-  const long long fs = L.fstride;
+  const long long fs = c->gs;
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   int nb = (int)((ncp + 255) / 256);
-  // (source field, destination) pairs, gathered through the staging area in groups
+  // (source component, destination) pairs, gathered through the staging area in groups
   struct Job { const void* f; int is_r; double* dst; };
   std::vector<Job> jobs;
   const char* Ucur = (const char*)c->U[c->cur];
@@ -628,8 +781,8 @@ int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, doubl
     for (size_t t = 0; t < nj; ++t) {
       const Job& jb = jobs[b + t];
       double* dst = c->stage + t * ncp;
-      if (jb.is_r && c->mixed) gather_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, (const float*)jb.f, dst);
-      else gather_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, (const double*)jb.f, dst);
+      if (jb.is_r && c->mixed) gather_kernel<float><<<nb, 256, 0, c->stream>>>(L, (const float*)jb.f, dst);
+      else gather_kernel<double><<<nb, 256, 0, c->stream>>>(L, (const double*)jb.f, dst);
     }
     CK(cudaGetLastError());
     for (size_t t = 0; t < nj; ++t) CK(cudaMemcpyAsync(jobs[b + t].dst, c->stage + t * ncp, ncp * 8, kind, c->stream));
@@ -639,18 +792,39 @@ int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, doubl
   return KT_OK;
 }
 
+int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, double* Pi, double* q, int on_device) {
+  return kt_get_state_event(c, 0, tau, e, u, pi, Pi, q, on_device);
+}
+
 int kt_mlp_features(kt_ctx* c, long long n, const long long* cells, float* x, float* y, double* e_exact) {
-  if (!c || n < 0 || !cells || !x || !y || !e_exact) return c ? fail(c, KT_ERR_ARG, "kt_mlp_features: bad argument") : KT_ERR_ARG;
-  if (!c->have_state) return fail(c, KT_ERR_ARG, "kt_mlp_features: no state set");
+  if (!c || n < 0 || !cells || !x || !y || !e_exact)
+    return c ? fail(c, KT_ERR_ARG, "kt_mlp_features: bad argument") : KT_ERR_ARG;
+  if (!c->ev_set[0]) return fail(c, KT_ERR_ARG, "kt_mlp_features: no state set");
   if (n == 0) return KT_OK;
   CK(cudaMemsetAsync(c->d_stat, 0, 4, c->stream));
-  mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->P, c->q, c->tau, n, cells, x, y, e_exact,
-                                                                          c->d_stat);
+  mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->P, c->lat[0], c->q, c->tau, n, cells, x,
+                                                                          y, e_exact, c->d_stat);
   CK(cudaGetLastError());
   unsigned st = 0;
   CK(cudaMemcpyAsync(&st, c->d_stat, 4, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (st) return fail(c, KT_ERR_INVERSION, "kt_mlp_features: bad cell index or failed root-find");
+  return KT_OK;
+}
+
+int kt_get_tuning(kt_ctx* c, int* block_xyz, int* grid_blocks, float* candidate_ms, int* n_candidates) {
+  if (!c) return KT_ERR_ARG;
+  if (block_xyz) {
+    block_xyz[0] = kShapes[c->shape].x;
+    block_xyz[1] = kShapes[c->shape].y;
+    block_xyz[2] = kShapes[c->shape].z;
+  }
+  if (grid_blocks) *grid_blocks = c->grid_blocks;
+  if (n_candidates) {
+    if (candidate_ms)
+      for (int s = 0; s < std::min(*n_candidates, kNumShapes); ++s) candidate_ms[s] = c->tuned ? c->tune_ms[s] : 0.f;
+    *n_candidates = kNumShapes;
+  }
   return KT_OK;
 }
 

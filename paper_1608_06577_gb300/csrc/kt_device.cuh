@@ -22,15 +22,24 @@ enum : unsigned { ST_INVERSION = 1u, ST_NONFINITE = 2u };
 __device__ __forceinline__ double f2d_bits(float f);
 __device__ __forceinline__ float d2f_bits(double d);
 
+// One event's padded lattice inside the field arrays.  A field array holds every component of
+// every event: component n of event e starts at n * fstride + base (fstride is shared by all
+// events of a context; a single event has base 0).
 struct Lattice {
   int nx, ny, nz;      // physical cells
   int pitch;           // padded row length (>= nx + 4)
   int NY, NZ;          // ny + 4, nz + 4
   long long plane;     // pitch * NY
-  long long fstride;   // elements per field (>= plane * NZ, multiple of 32)
+  long long fstride;   // elements between components (sum of all events' padded sizes)
+  long long base;      // first element of this event
   __host__ __device__ long long idx(int i, int j, int k) const {
-    return (long long)i + (long long)pitch * ((long long)j + (long long)NY * (long long)k);
+    return base + (long long)i + (long long)pitch * ((long long)j + (long long)NY * (long long)k);
   }
+};
+
+// a block-shaped tile of one event: the persistent stage kernel walks a table of these
+struct Tile {
+  int event, i0, j0, k0;
 };
 
 // Table EOS: one record per interval [e_i, e_{i+1}], cubic polynomials in t = (e - e_i)/(e_{i+1} - e_i)
@@ -64,7 +73,6 @@ struct PR {
 };
 
 struct Params {
-  Lattice L;
   double dx, dy, deta, dtau;
   double theta;
   int milne;          // 1 Milne, 0 Cartesian

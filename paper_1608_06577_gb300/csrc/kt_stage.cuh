@@ -41,9 +41,8 @@ struct StageIO {
 
 // ------------------------------------------------------------------ one direction of a)
 template <typename R, int D>
-__device__ __forceinline__ void direction_pass(const Params& P, const StageIO<R>& io, long long c, R gnn,
-                                               R tau, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax) {
-  const Lattice& L = P.L;
+__device__ __forceinline__ void direction_pass(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
+                                               R gnn, R tau, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax) {
   const long long fs = L.fstride;
   const long long s = (D == 0) ? 1LL : ((D == 1) ? (long long)L.pitch : L.plane);
   const R invD = pr<R>(P).inv_d[D];
@@ -337,10 +336,9 @@ __device__ __forceinline__ int ghost_source(int g, int n, int periodic) {
 }
 
 template <typename R>
-__device__ __forceinline__ void store_with_ghosts(const Params& P, const StageIO<R>& io, int i, int j, int k,
-                                                  const double (&qn)[NQ], const R (&qr)[NQ], const R (&uo)[4], R e,
-                                                  R P0) {
-  const Lattice& L = P.L;
+__device__ __forceinline__ void store_with_ghosts(const Params& P, const Lattice& L, const StageIO<R>& io, int i,
+                                                  int j, int k, const double (&qn)[NQ], const R (&qr)[NQ],
+                                                  const R (&uo)[4], R e, R P0) {
   const long long fs = L.fstride;
   store_cell<R>(io, fs, L.idx(i, j, k), qn, qr, uo, e, P0);
   const int nn[3] = {L.nx, L.ny, L.nz};
@@ -359,22 +357,14 @@ __device__ __forceinline__ void store_with_ghosts(const Params& P, const StageIO
   }
 }
 
-// ---------------------------------------------------------------- the stage kernel
+// ---------------------------------------------------------------- one cell of a tile
+// All threads of a warp call this together (the learned start is a warp-wide MMA); cells past
+// the edge of the event (valid = false) compute nothing and store nothing.
 template <typename R, int STAGE, bool LEARNED>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) stage_kernel(const Params P, const StageIO<R> io) {
-  const Lattice& L = P.L;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+__device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, const StageIO<R>& io, int i, int j,
+                                           int k, const uint32_t* s_mlp, unsigned& st, unsigned& nit, unsigned& nreg,
+                                           unsigned& nfb, float& amax) {
   const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
-  unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
-  float amax = 0.f;
-  __shared__ uint32_t s_mlp[LEARNED ? PK_WORDS : 1];
-  if constexpr (LEARNED) {
-    mlp_load_shared(s_mlp, io.mlp_packed);
-    __syncthreads();
-  }
-
   const long long fs = L.fstride;
   const long long c = L.idx(i + 2, j + 2, k + 2);
   const double tau_n = io.d_tau[0];
@@ -393,9 +383,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) stage_kernel(co
     for (int n = 0; n < NQ; ++n) dq[n] = R(0);
     R du[4][4];
     R dv = R(0);
-    direction_pass<R, 0>(P, io, c, gnn, tau, dq, du, dv, amax);
-    direction_pass<R, 1>(P, io, c, gnn, tau, dq, du, dv, amax);
-    direction_pass<R, 2>(P, io, c, gnn, tau, dq, du, dv, amax);
+    direction_pass<R, 0>(P, L, io, c, gnn, tau, dq, du, dv, amax);
+    direction_pass<R, 1>(P, L, io, c, gnn, tau, dq, du, dv, amax);
+    direction_pass<R, 2>(P, L, io, c, gnn, tau, dq, du, dv, amax);
 
     // ---- b) sources at the cell
     R uc[4];
@@ -592,7 +582,29 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) stage_kernel(co
       if (!isfinite(qr[n])) st |= ST_NONFINITE;
 
     // ---- f) stores
-    store_with_ghosts<R>(P, io, i + 2, j + 2, k + 2, qn, qr, uo, eR, P0R);
+    store_with_ghosts<R>(P, L, io, i + 2, j + 2, k + 2, qn, qr, uo, eR, P0R);
+  }
+}
+
+// ---------------------------------------------------------------- the stage kernel
+// Persistent: every block walks the tile table with stride gridDim.x; a tile is one block-shaped
+// patch of one event, so one launch per Runge-Kutta stage advances every event of the context.
+template <typename R, int STAGE, bool LEARNED>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1)
+    stage_kernel(const Params P, const StageIO<R> io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
+                 int ntiles) {
+  unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
+  float amax = 0.f;
+  __shared__ uint32_t s_mlp[LEARNED ? PK_WORDS : 1];
+  if constexpr (LEARNED) {
+    mlp_load_shared(s_mlp, io.mlp_packed);
+    __syncthreads();
+  }
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const Lattice L = lats[tl.event];
+    stage_cell<R, STAGE, LEARNED>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y,
+                                  tl.k0 + (int)threadIdx.z, s_mlp, st, nit, nreg, nfb, amax);
   }
 
   // ---- statistics: warp shuffles, then one atomic per block
