@@ -91,8 +91,9 @@ typedef struct {
   size_t arena_bytes;    /* its size, at least kt_state_bytes() */
   const float* mlp_weights; /* KT_INV_LEARNED: host pointer to KT_MLP_NPARAM floats (see below) */
   int use_graph;         /* 1 (default): kt_step replays a captured CUDA graph of the step loop */
-  int autotune;          /* 1 (default): the first kt_step times the candidate tile shapes (side-effect
-                            free first-stage launches) and keeps the fastest; 0: 32 x 4 x 2 */
+  int autotune;          /* 1 (default): the first kt_step times the candidate tile shapes and grid
+                            sizes (side-effect-free first-stage launches) and keeps the fastest;
+                            0: 32 x 4 x 2 tiles on a persistent grid */
 } kt_options;
 
 /* Learned inversion start: an MLP 6 -> 32 -> 32 -> 1 with ReLU; weights row-major
@@ -165,9 +166,11 @@ int kt_set_state_event(kt_ctx* ctx, int event, double tau, const double* e, cons
                        const double* Pi, const double* u_prev, int on_device);
 int kt_get_state_event(kt_ctx* ctx, int event, double* tau, double* e, double* u, double* pi, double* Pi, double* q,
                        int on_device);
-/* The tile shape in use (threads per block x, y, z), the persistent grid size in blocks and,
- * after autotuning, the measured first-stage time in ms of each candidate shape (up to
- * *n_candidates entries; *n_candidates is set to the number of candidates). */
+/* The tile shape in use (threads per block x, y, z), the grid size in blocks and, after
+ * autotuning, the measured first-stage time in ms of each candidate (up to *n_candidates
+ * entries; *n_candidates is set to the number of candidates).  Candidate 2 s + g is tile shape s
+ * of (32,4,2), (32,8,1), (32,2,4), (32,1,8), (32,4,1), (32,2,2) with g = 0 a persistent grid (as
+ * many blocks as are resident at once, each walking the tile table) or g = 1 one block per tile. */
 int kt_get_tuning(kt_ctx* ctx, int* block_xyz, int* grid_blocks, float* candidate_ms, int* n_candidates);
 
 /* ------------------------------------------------------------------ learned root-find start

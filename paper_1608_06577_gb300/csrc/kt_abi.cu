@@ -28,6 +28,8 @@ struct Shape {
 // candidate tile shapes of the autotuner (threads per block; x stays 32 so a warp is one x-row)
 constexpr Shape kShapes[] = {{32, 4, 2}, {32, 8, 1}, {32, 2, 4}, {32, 1, 8}, {32, 4, 1}, {32, 2, 2}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+// candidates: every shape with a persistent grid (blocks resident at once) and with one block per tile
+constexpr int kNumCandidates = 2 * kNumShapes;
 
 struct Ctx {
   kt_options opt;
@@ -67,7 +69,8 @@ struct Ctx {
   int ntiles = 0;
   int grid_blocks = 0;
   bool tuned = false;
-  float tune_ms[kNumShapes] = {};
+  int cand = 0;
+  float tune_ms[kNumCandidates] = {};
   int learned = 0;
   int cur = 0, prev = 1, spare = 2;
   double tau = 0.0;
@@ -390,7 +393,8 @@ int occupancy_blocks(const Shape& s) {
   return std::max(1, nb) * std::max(1, sms);
 }
 
-int select_shape(Ctx* c, int shape) {
+int select_shape(Ctx* c, int cand) {
+  const int shape = cand / 2, one_per_tile = cand % 2;
   std::vector<Tile> tiles;
   build_tiles(c->lat, kShapes[shape], tiles);
   if ((int)tiles.size() > c->max_tiles) return fail(c, KT_ERR_OOM, "tile table overflow");
@@ -402,13 +406,14 @@ int select_shape(Ctx* c, int shape) {
   if (c->mixed && c->learned) cap = occupancy_blocks<float, true>(kShapes[shape]);
   else if (c->mixed) cap = occupancy_blocks<float, false>(kShapes[shape]);
   else cap = occupancy_blocks<double, false>(kShapes[shape]);
-  c->grid_blocks = std::max(1, std::min(cap, c->ntiles));
+  c->grid_blocks = one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles));
+  c->cand = cand;
   for (int p = 0; p < 3; ++p)
     if (c->graph[p]) { cudaGraphExecDestroy(c->graph[p]); c->graph[p] = nullptr; }
   return KT_OK;
 }
 
-// Autotuner: time a first-stage launch for every candidate tile shape.  The launches write only
+// Autotuner: time a first-stage launch for every candidate (tile shape, grid size).  The launches write only
 // scratch buffers (q*, its FP32 copy, e*, p*, and u* redirected to the spare buffer), so the
 // state is untouched; the fastest shape is kept.
 template <typename R, bool LEARNED>
@@ -431,7 +436,7 @@ int time_first_stage(Ctx* c, float* ms) {
 
 int autotune(Ctx* c) {
   int best = 0;
-  for (int s = 0; s < kNumShapes; ++s) {
+  for (int s = 0; s < kNumCandidates; ++s) {
     int rc = select_shape(c, s);
     if (rc != KT_OK) return rc;
     float ms = 0.f;
@@ -822,8 +827,9 @@ int kt_get_tuning(kt_ctx* c, int* block_xyz, int* grid_blocks, float* candidate_
   if (grid_blocks) *grid_blocks = c->grid_blocks;
   if (n_candidates) {
     if (candidate_ms)
-      for (int s = 0; s < std::min(*n_candidates, kNumShapes); ++s) candidate_ms[s] = c->tuned ? c->tune_ms[s] : 0.f;
-    *n_candidates = kNumShapes;
+      for (int s = 0; s < std::min(*n_candidates, kNumCandidates); ++s)
+        candidate_ms[s] = c->tuned ? c->tune_ms[s] : 0.f;
+    *n_candidates = kNumCandidates;
   }
   return KT_OK;
 }
