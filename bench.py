@@ -200,17 +200,24 @@ def make_kt(prob, mode, weights, stream):
         return KT(prob, precision=prec, inversion=inv, mlp_weights=weights if inv else None)
 
 
-def time_mode(prob, mode, weights, steps, warmup, stream):
+def time_mode(prob, mode, weights, steps, warmup, stream, profile_range=False):
+    """Times `steps` RK2 steps with CUDA events on the launching stream.  With profile_range the
+    timed steps sit between cudaProfilerStart/Stop, so `ncu --profile-from-start off` lists
+    exactly the launches of the timed region."""
     import torch
     kt = make_kt(prob, mode, weights, stream)
     kt.set_problem_state()
     kt.step(warmup)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if profile_range:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     kt.step(steps)
     ev1.record(stream)
     ev1.synchronize()
+    if profile_range:
+        torch.cuda.profiler.stop()
     return kt, ev0.elapsed_time(ev1)
 
 
