@@ -11,10 +11,10 @@ namespace kt {
 
 constexpr int NQ = 15;  // T^{tau mu} (4), pi^{mu nu} (10), Pi (1): Eq. (qComponents)
 
-// q index of pi^{mu nu}
-__host__ __device__ constexpr int pix(int a, int b) {
-  return (a > b) ? pix(b, a)
-                 : (a == 0 ? 4 + b : (a == 1 ? 7 + b : (a == 2 ? 9 + b : 13)));
+// q index of pi^{mu nu} (not recursive, so that it always inlines)
+__host__ __device__ __forceinline__ constexpr int pix(int a, int b) {
+  const int lo = (a < b) ? a : b, hi = (a < b) ? b : a;
+  return lo == 0 ? 4 + hi : (lo == 1 ? 7 + hi : (lo == 2 ? 9 + hi : 13));
 }
 
 enum : unsigned { ST_INVERSION = 1u, ST_NONFINITE = 2u };
@@ -157,16 +157,22 @@ __device__ __forceinline__ void eos_T_lnd(const Params& P, R e, R& T, R& lnd) {
   lnd = fma(t, s.dl, s.l0);
 }
 
-// Generalised minmod of (theta dm, (dm + dp)/2, theta dp), Sec. 3.1, with sgn(0) = 0:
-// the common-sign smallest magnitude, or 0.  This is the slope times the cell size.
+// Generalised minmod of (theta dl, (dl + dr)/2, theta dr), Sec. 3.1, with sgn(0) = 0, from the
+// one-sided differences dl = q_i - q_{i-1}, dr = q_{i+1} - q_i: the three arguments share a sign
+// exactly when dl and dr do, and then the result is that sign times the smallest magnitude.
+// This is the slope times the cell size.  (The product test loses slopes whose one-sided
+// differences multiply below the smallest subnormal, ~1e-45 in FP32 and ~1e-323 in FP64.)
 template <typename R>
-__device__ __forceinline__ R limited_slope(R qm, R q0, R qp, R theta) {
-  R a = theta * (q0 - qm), b = R(0.5) * (qp - qm), c = theta * (qp - q0);
-  R mn = fmin(fabs(a), fmin(fabs(b), fabs(c)));
-  bool pos = (a > R(0)) & (b > R(0)) & (c > R(0));
-  bool neg = (a < R(0)) & (b < R(0)) & (c < R(0));
-  return pos ? mn : (neg ? -mn : R(0));
+__device__ __forceinline__ R limited_slope_d(R dl, R dr, R theta) {
+  R mn = fmin(theta * fabs(dl), theta * fabs(dr));
+  mn = fmin(mn, R(0.5) * fabs(dl + dr));
+  return (dl * dr > R(0)) ? copysign(mn, dl) : R(0);
 }
+
+// a / b in the stencil precision: IEEE division in FP64; in FP32 the two-ulp fast division
+// (the operands are velocities and u^tau >= 1, far from the range where it degrades)
+__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
 
 // eta/s(T) and ln(zeta/s)(T): const c0 or c0 exp(-((T - c1)/c2)^2)
 template <typename R>

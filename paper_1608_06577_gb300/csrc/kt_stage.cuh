@@ -39,72 +39,156 @@ struct StageIO {
   const uint32_t* mlp_packed;  // learned start: packed weights (see kt_mlp.cuh), or null
 };
 
-// ------------------------------------------------------------------ one direction of a)
+// ------------------------------------------------------------------ a) the stencil
+// Per direction d the cell has two faces, L = i-1/2 and R = i+1/2, each with a left (m) and a
+// right (p) state.  With F = v q the central-upwind flux of Eq. (Hflux) is linear in the face
+// states, H = (v^p - a)/2 q^p + (v^m + a)/2 q^m, so the velocities and speeds of a face are
+// folded once into four weights per direction (times 1/dx, the R-face weights negated) and
+// every component then costs its reconstruction and four multiply-adds.
+template <typename R>
+struct Faces {
+  R wLp, wLm, wRp, wRm;  // -(H_R - H_L)/dx = wLp q_L^p + wLm q_L^m + wRp q_R^p + wRm q_R^m
+  R vpl_h, vmi_h;        // v^d at i+1 and i-1, times 1/(2 dx)
+  R hinv;                // 1/(2 dx)
+  int s;                 // element stride of direction d
+};
+
+// Velocity part of direction D: limited face states of u^tau and u^d and their ratio v^d
+// (Sec. 3.1), the local speeds a = max(|v^p|, |v^m|) (Eq. ax), the central differences
+// d_d u^mu and d_d v^d, and the pressure part of S_c (App. B):
+// -d_d (v^d P delta^nu_tau - g^{d nu} P), P = P0 + Pi.
 template <typename R, int D>
-__device__ __forceinline__ void direction_pass(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
-                                               R gnn, R tau, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax) {
+__device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
+                                           R inv_gnn, R sfac, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax,
+                                           Faces<R>& F) {
   const long long fs = L.fstride;
-  const long long s = (D == 0) ? 1LL : ((D == 1) ? (long long)L.pitch : L.plane);
+  const int s = (D == 0) ? 1 : ((D == 1) ? L.pitch : (int)L.plane);
   const R invD = pr<R>(P).inv_d[D];
   const R hinv = R(0.5) * invD;
   const R th = pr<R>(P).theta;
   const R* u = io.u_in;
 
-  // u^mu on the stencil
   R um1[4], up1[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     um1[m] = ld<R>(u + m * fs, c - s);
     up1[m] = ld<R>(u + m * fs, c + s);
   }
-  R u0t = ld<R>(u, c), u0d = ld<R>(u + (D + 1) * fs, c);
-  R um2t = ld<R>(u, c - 2 * s), um2d = ld<R>(u + (D + 1) * fs, c - 2 * s);
-  R up2t = ld<R>(u, c + 2 * s), up2d = ld<R>(u + (D + 1) * fs, c + 2 * s);
-  // face states of u^tau and u^d; faces L = i-1/2, R = i+1/2; m = left state, p = right state
-  R st_m = limited_slope(um2t, um1[0], u0t, th), st_0 = limited_slope(um1[0], u0t, up1[0], th),
-    st_p = limited_slope(u0t, up1[0], up2t, th);
-  R sd_m = limited_slope(um2d, um1[D + 1], u0d, th), sd_0 = limited_slope(um1[D + 1], u0d, up1[D + 1], th),
-    sd_p = limited_slope(u0d, up1[D + 1], up2d, th);
+  const R u0t = ld<R>(u, c), u0d = ld<R>(u + (D + 1) * fs, c);
+  const R um2t = ld<R>(u, c - 2 * s), um2d = ld<R>(u + (D + 1) * fs, c - 2 * s);
+  const R up2t = ld<R>(u, c + 2 * s), up2d = ld<R>(u + (D + 1) * fs, c + 2 * s);
+  R t0 = um1[0] - um2t, t1 = u0t - um1[0], t2 = up1[0] - u0t, t3 = up2t - up1[0];
+  R d0 = um1[D + 1] - um2d, d1 = u0d - um1[D + 1], d2 = up1[D + 1] - u0d, d3 = up2d - up1[D + 1];
+  const R st_m = limited_slope_d(t0, t1, th), st_0 = limited_slope_d(t1, t2, th), st_p = limited_slope_d(t2, t3, th);
+  const R sd_m = limited_slope_d(d0, d1, th), sd_0 = limited_slope_d(d1, d2, th), sd_p = limited_slope_d(d2, d3, th);
   const R h = R(0.5);
-  R vLm = (um1[D + 1] + h * sd_m) / (um1[0] + h * st_m);
-  R vLp = (u0d - h * sd_0) / (u0t - h * st_0);
-  R vRm = (u0d + h * sd_0) / (u0t + h * st_0);
-  R vRp = (up1[D + 1] - h * sd_p) / (up1[0] - h * st_p);
-  R aL = fmax(fabs(vLp), fabs(vLm));
-  R aR = fmax(fabs(vRp), fabs(vRm));
-  amax = fmaxf(amax, (float)((D == 2) ? aR * sqrt(gnn) : aR));
+  const R vLm = sdiv(fma(h, sd_m, um1[D + 1]), fma(h, st_m, um1[0]));
+  const R vLp = sdiv(fma(-h, sd_0, u0d), fma(-h, st_0, u0t));
+  const R vRm = sdiv(fma(h, sd_0, u0d), fma(h, st_0, u0t));
+  const R vRp = sdiv(fma(-h, sd_p, up1[D + 1]), fma(-h, st_p, up1[0]));
+  const R aL = fmax(fabs(vLp), fabs(vLm));
+  const R aR = fmax(fabs(vRp), fabs(vRm));
+  amax = fmaxf(amax, (float)((D == 2) ? aR * sfac : aR));
+  F.wLp = (vLp - aL) * hinv;
+  F.wLm = (vLm + aL) * hinv;
+  F.wRp = (aR - vRp) * hinv;
+  F.wRm = -(vRm + aR) * hinv;
 
-  // d_d u^mu and d_i v^i by central differences (Sec. 3.1)
 #pragma unroll
   for (int m = 0; m < 4; ++m) du[D + 1][m] = (up1[m] - um1[m]) * hinv;
-  R vpl = up1[D + 1] / up1[0], vmi = um1[D + 1] / um1[0];
+  const R vpl = sdiv(up1[D + 1], up1[0]), vmi = sdiv(um1[D + 1], um1[0]);
   dv += (vpl - vmi) * hinv;
+  F.vpl_h = vpl * hinv;
+  F.vmi_h = vmi * hinv;
+  F.hinv = hinv;
+  F.s = s;
 
-  // S_c: -d_d (v^d P delta^nu_tau - g^{d nu} P - v^d pi^{tau nu} + pi^{d nu}), P = P0 + Pi
   const R* q = io.qr_in;
-  R Ppl = ld<R>(io.p_in, c + s) + ld<R>(q + 14 * fs, c + s);
-  R Pmi = ld<R>(io.p_in, c - s) + ld<R>(q + 14 * fs, c - s);
-  dq[0] -= (Ppl * vpl - Pmi * vmi) * hinv;
-  dq[D + 1] -= ((D == 2) ? (Ppl - Pmi) / gnn : (Ppl - Pmi)) * hinv;
+  const R Ppl = ld<R>(io.p_in, c + s) + ld<R>(q + 14 * fs, c + s);
+  const R Pmi = ld<R>(io.p_in, c - s) + ld<R>(q + 14 * fs, c - s);
+  dq[0] -= Ppl * F.vpl_h - Pmi * F.vmi_h;
+  dq[D + 1] -= ((D == 2) ? (Ppl - Pmi) * inv_gnn : (Ppl - Pmi)) * hinv;
+}
 
+// row nu of T^{tau nu} that component n feeds through -d_d(-v^d pi^{tau nu}) (first == true:
+// n = pi^{tau nu}) or -d_d(pi^{d nu}) (n = pi^{d nu}); -1 if none
+template <int D>
+__device__ __forceinline__ int cross_row(int n, bool first) {
+  if (first) return (n >= 4 && n <= 7) ? n - 4 : -1;
 #pragma unroll
-  for (int n = 0; n < NQ; ++n) {
-    const R* qn = q + n * fs;
-    R a2 = ld<R>(qn, c - 2 * s), a1 = ld<R>(qn, c - s), a0 = ld<R>(qn, c), b1 = ld<R>(qn, c + s),
-      b2 = ld<R>(qn, c + 2 * s);
-    R sm = limited_slope(a2, a1, a0, th), s0 = limited_slope(a1, a0, b1, th), sp = limited_slope(a0, b1, b2, th);
-    R qLm = a1 + h * sm, qLp = a0 - h * s0, qRm = a0 + h * s0, qRp = b1 - h * sp;
-    // H = (F(q+) + F(q-))/2 - a (q+ - q-)/2 with F = v q (Eq. Hflux)
-    R HL = h * (vLp * qLp + vLm * qLm) - h * aL * (qLp - qLm);
-    R HR = h * (vRp * qRp + vRm * qRm) - h * aR * (qRp - qRm);
-    dq[n] -= (HR - HL) * invD;
-#pragma unroll
-    for (int nu = 0; nu < 4; ++nu) {
-      if (n == pix(0, nu)) dq[nu] += (vpl * b1 - vmi * a1) * hinv;
-      if (n == pix(D + 1, nu)) dq[nu] -= (b1 - a1) * hinv;
+  for (int nu = 0; nu < 4; ++nu)
+    if (n == pix(D + 1, nu)) return nu;
+  return -1;
+}
+
+// dq[r] += v for a warp-uniform runtime row r (the switch keeps dq in registers)
+template <typename R>
+__device__ __forceinline__ void add_row(R (&dq)[NQ], int r, R v) {
+  switch (r) {
+    case 0: dq[0] += v; break;
+    case 1: dq[1] += v; break;
+    case 2: dq[2] += v; break;
+    case 3: dq[3] += v; break;
+    case 4: dq[4] += v; break;
+    case 5: dq[5] += v; break;
+    case 6: dq[6] += v; break;
+    case 7: dq[7] += v; break;
+    case 8: dq[8] += v; break;
+    case 9: dq[9] += v; break;
+    case 10: dq[10] += v; break;
+    case 11: dq[11] += v; break;
+    case 12: dq[12] += v; break;
+    case 13: dq[13] += v; break;
+    case 14: dq[14] += v; break;
+    default: break;
+  }
+}
+
+// one component along direction D: generalised-minmod reconstruction from the five-point
+// stencil p[-2s..2s] (a0 = p[0] given) and the flux difference -(H_R - H_L)/dx; a1, b1 return
+// the neighbours for the central differences of the S_c terms
+template <typename R, int D>
+__device__ __forceinline__ R component_flux(const R* p, R a0, R th, const Faces<R>& F, R& a1, R& b1) {
+  const int s = F.s;
+  const R a2 = ld<R>(p, -2 * s), b2 = ld<R>(p, 2 * s);
+  a1 = ld<R>(p, -s);
+  b1 = ld<R>(p, s);
+  const R d0 = a1 - a2, d1 = a0 - a1, d2 = b1 - a0, d3 = b2 - b1;
+  const R sm = limited_slope_d(d0, d1, th), s0 = limited_slope_d(d1, d2, th), sp = limited_slope_d(d2, d3, th);
+  const R h = R(0.5);
+  const R qLm = fma(h, sm, a1), qLp = fma(-h, s0, a0), qRm = fma(h, s0, a0), qRp = fma(-h, sp, b1);
+  return fma(F.wLp, qLp, fma(F.wLm, qLm, fma(F.wRp, qRp, F.wRm * qRm)));
+}
+
+// The 15 conserved components: -div H in x, y, eta and the remaining S_c terms
+// -d_d(-v^d pi^{tau nu} + pi^{d nu}) by central differences.  The component loop is not
+// unrolled: one compact body keeps the instruction stream of the whole kernel small.
+template <typename R>
+__device__ __forceinline__ void conserved_fluxes(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
+                                                 const Faces<R>& Fx, const Faces<R>& Fy, const Faces<R>& Fz,
+                                                 R (&dq)[NQ]) {
+  const long long fs = L.fstride;
+  const R th = pr<R>(P).theta;
+  const R* p = io.qr_in + c;
+#pragma unroll 1
+  for (int n = 0; n < NQ; ++n, p += fs) {
+    const R a0 = ld<R>(p, 0);
+    R a1x, b1x, a1y, b1y, a1z, b1z;
+    R acc = component_flux<R, 0>(p, a0, th, Fx, a1x, b1x);
+    acc += component_flux<R, 1>(p, a0, th, Fy, a1y, b1y);
+    acc += component_flux<R, 2>(p, a0, th, Fz, a1z, b1z);
+    add_row(dq, n, acc);
+    if (n >= 4 && n <= 13) {  // pi components
+      const int r0 = cross_row<0>(n, true);
+      if (r0 >= 0)
+        add_row(dq, r0, (Fx.vpl_h * b1x - Fx.vmi_h * a1x) + (Fy.vpl_h * b1y - Fy.vmi_h * a1y) +
+                            (Fz.vpl_h * b1z - Fz.vmi_h * a1z));
+      const int rx = cross_row<0>(n, false), ry = cross_row<1>(n, false), rz = cross_row<2>(n, false);
+      if (rx >= 0) add_row(dq, rx, -(b1x - a1x) * Fx.hinv);
+      if (ry >= 0) add_row(dq, ry, -(b1y - a1y) * Fy.hinv);
+      if (rz >= 0) add_row(dq, rz, -(b1z - a1z) * Fz.hinv);
     }
   }
-  (void)tau;
 }
 
 // 1/A to full double precision: a single-precision seed and two Newton-Raphson refinements
@@ -383,9 +467,15 @@ __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, co
     for (int n = 0; n < NQ; ++n) dq[n] = R(0);
     R du[4][4];
     R dv = R(0);
-    direction_pass<R, 0>(P, L, io, c, gnn, tau, dq, du, dv, amax);
-    direction_pass<R, 1>(P, L, io, c, gnn, tau, dq, du, dv, amax);
-    direction_pass<R, 2>(P, L, io, c, gnn, tau, dq, du, dv, amax);
+    {
+      const R inv_gnn = P.milne ? sdiv(R(1), gnn) : R(1);
+      const R sfac = P.milne ? tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
+      Faces<R> Fx, Fy, Fz;
+      face_setup<R, 0>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fx);
+      face_setup<R, 1>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fy);
+      face_setup<R, 2>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fz);
+      conserved_fluxes<R>(P, L, io, c, Fx, Fy, Fz, dq);
+    }
 
     // ---- b) sources at the cell
     R uc[4];
