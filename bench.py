@@ -25,12 +25,26 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell updates/s per RK2 step at 128^3, plain FP64 vs FP32+learned; % HBM peak"
 UNIT = "cell updates/s"
-# Algorithmic bytes per cell per RK2 step of the two fused stages, every field read and written
-# once per stage.  FP64: stage 1 reads q, u, u_prev, e, p (25 words) and writes q*, u*, e, p (21);
-# stage 2 reads q*, q^n, u*, u^n, e, p (40) and writes 21: 107 words = 856 B.  Mixed: u, e, p are
-# FP32 and the stencil reads an FP32 copy of q that each stage also writes:
-# (60+120+16+16+8) + (120+60+16+8) + (60+120+120+16+16+8) + (120+60+16+8) = 968 B.
-BYTES_PER_CELL = {"fp64": 856, "mixed": 968}
+# Algorithmic bytes per cell per RK2 step, every field read and written once per launch.
+# FP64 (one fused kernel per stage): stage 1 reads q, u, u_prev, e, p (25 words) and writes q*, u*,
+# e, p (21); stage 2 reads q*, q^n, u*, u^n, e, p (40) and writes 21: 107 words = 856 B.
+# Mixed (per stage an FP32 right-hand-side kernel and an update kernel):
+#   rhs 1:    qf 60 + u 16 + u_prev 16 + e, p 8 -> k1 60                         = 160
+#   update 1: q (T, pi^{tau mu}, Pi) 72 + k1 60 + qf 60 + e 4 -> qsf 60 + u 16 + e, p 8
+#             + regulated k1 (pi) 40                                            = 320
+#   rhs 2:    qsf 60 + u 16 + u_prev 16 + e, p 8 -> k2 60                        = 160
+#   update 2: q 120 + k1 60 + k2 60 + e 4 -> q 120 + qf 60 + u 16 + e, p 8       = 448
+# = 1088 B (the learned start skips the 4-byte e reads: 1080 B).
+BYTES_PER_CELL = {"fp64": 856, "mixed": 1088, "learned": 1080}
+# per launch slot of kt_time_kernels (bytes per cell); FP64: the fused stage kernels
+SLOT_BYTES = {
+    "fp64": {"stage1_rhs": 368, "stage2_rhs": 488},
+    "mixed": {"stage1_rhs": 160, "stage1_update": 320, "stage2_rhs": 160, "stage2_update": 448},
+    "learned": {"stage1_rhs": 160, "stage1_update": 316, "stage2_rhs": 160, "stage2_update": 444},
+}
+SLOT_KERNEL = {"stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel", "stage1_update": "update_kernel",
+               "stage2_update": "update_kernel", "tau_advance": "advance_tau_kernel"}
+LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
 
 
 def parse():
@@ -253,7 +267,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         if mode == args.mode:
             with ClockSampler(local) as cs:
-                kt, ms = time_mode(prob, mode, weights, steps, args.warmup, stream)
+                kt, ms = time_mode(prob, mode, weights, steps, args.warmup, stream, profile_range=True)
             clocks = cs.summary()
         else:
             kt, ms = time_mode(prob, mode, weights, steps, args.warmup, stream)
@@ -263,19 +277,37 @@ def run_ours(args, world, rank, local):
         st = kt.stats()
         results[mode] = {"ms_per_step": ms / steps, "value": cells * world * steps / (ms * 1e-3), "steps": steps,
                          "stats": st}
+        if mode == args.mode:  # per-launch durations (CUDA events between launches, after the timed steps)
+            results[mode]["slots_ms"] = kt.time_kernels(max(3, min(steps, 10)))
         del kt
         torch.cuda.empty_cache()
 
     main = results[args.mode]
     ms_step = main["ms_per_step"]
-    # dominant kernel: the fused stage kernel, two launches per step (the tau-advance kernel is ~0.1%)
-    stage_ms = ms_step / 2.0
-    bpc = BYTES_PER_CELL["fp64" if args.mode == "fp64" else "mixed"]
-    achieved = cells * bpc / 2.0 / (stage_ms * 1e-3) / 1e9
+    bpc = BYTES_PER_CELL[args.mode]
+    # per kernel: launches per step, average launch time, algorithmic bytes per launch, GB/s
+    kernels = {}
+    for slot, t in main["slots_ms"].items():
+        if t <= 0.0:
+            continue
+        k = kernels.setdefault("stage_kernel" if args.mode == "fp64" and slot.endswith("rhs") else SLOT_KERNEL[slot],
+                               {"launches_per_step": 0, "ms_per_step": 0.0, "bytes_per_step": 0.0})
+        k["launches_per_step"] += 1
+        k["ms_per_step"] += t
+        k["bytes_per_step"] += cells * SLOT_BYTES[args.mode].get(slot, 8.0 / cells)
+    for k in kernels.values():
+        k["avg_launch_ms"] = k["ms_per_step"] / k["launches_per_step"]
+        k["gbs"] = k["bytes_per_step"] / (k["ms_per_step"] * 1e-3) / 1e9
+        k["share"] = k["ms_per_step"] / sum(v["ms_per_step"] for v in kernels.values())
+    dom = max(kernels, key=lambda n: kernels[n]["ms_per_step"])
+    achieved = kernels[dom]["gbs"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_cell_step": bpc,
-                "note": "algorithmic bytes per stage launch / average launch time (2 launches per step)"}
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind, "kernel": dom,
+                "bytes_per_launch": kernels[dom]["bytes_per_step"] / kernels[dom]["launches_per_step"],
+                "avg_launch_ms": kernels[dom]["avg_launch_ms"], "bytes_per_cell_step": bpc,
+                "step_gbs": cells * bpc / (ms_step * 1e-3) / 1e9,
+                "note": "achieved = algorithmic bytes per launch / average launch time (CUDA events between "
+                        "launches on the context stream); step_gbs = all kernels' algorithmic bytes / step time"}
 
     e2e = None
     if not args.no_e2e:
@@ -319,8 +351,8 @@ def run_ours(args, world, rank, local):
                               "fallbacks_per_cell_stage": r["stats"]["fallbacks"] / ncs(r)}
                           for m, r in results.items()},
                 "learned_training": train_info,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 3 * main["steps"]}
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": LAUNCHES_PER_STEP["fp64" if args.mode == "fp64" else "mixed"] * main["steps"]}
         print(json.dumps(line), flush=True)
 
 

@@ -173,6 +173,16 @@ int kt_get_state_event(kt_ctx* ctx, int event, double* tau, double* e, double* u
  * many blocks as are resident at once, each walking the tile table) or g = 1 one block per tile. */
 int kt_get_tuning(kt_ctx* ctx, int* block_xyz, int* grid_blocks, float* candidate_ms, int* n_candidates);
 
+/* Measurement (the paper has no counterpart): advance n_steps >= 1 steps exactly as kt_step does
+ * but launch by launch, without the CUDA graph, with CUDA events on the context's stream between
+ * the launches, and return in ms[0..4] the average duration per step of: the stage-1 right-hand-
+ * side launch (FP64: the fused stage-1 launch), the stage-1 update launch (FP64: 0), the stage-2
+ * right-hand-side launch (FP64: the fused stage-2 launch), the stage-2 update launch (FP64: 0)
+ * and the tau advance.  *n_kernels must be >= 5 on entry and is set to 5.  The state, tau and
+ * statistics advance as with kt_step; errors are those of kt_step.  The per-step event
+ * synchronisation makes these steps slower in total than kt_step's. */
+int kt_time_kernels(kt_ctx* ctx, int n_steps, float* ms, int* n_kernels);
+
 /* ------------------------------------------------------------------ learned root-find start
  * The paper solves Eq. (eInferred) by Newton-Raphson (Sec. 3.2) and states no starting point.
  * KT_INV_LEARNED starts it from a small network: features (computed by the library from

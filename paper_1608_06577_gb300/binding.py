@@ -86,6 +86,7 @@ def load_library():
     L.kt_set_state_event.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, vp, C.c_int]
     L.kt_get_state_event.argtypes = [vp, C.c_int, dp, vp, vp, vp, vp, vp, C.c_int]
     L.kt_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int)]
+    L.kt_time_kernels.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int)]
     _LIB = L
     return L
 
@@ -242,6 +243,17 @@ class KT:
         n = C.c_int(16)
         self._check(self.L.kt_get_tuning(self.ctx, blk, C.byref(grid), ms, C.byref(n)), "kt_get_tuning")
         return {"block": tuple(blk), "grid_blocks": grid.value, "candidate_ms": list(ms)[:n.value]}
+
+    KERNEL_SLOTS = ("stage1_rhs", "stage1_update", "stage2_rhs", "stage2_update", "tau_advance")
+
+    def time_kernels(self, n_steps: int) -> dict:
+        """Advances n_steps steps launch by launch with CUDA events between the launches
+        (kt_time_kernels) and returns the average ms per step of each launch slot; in FP64 mode
+        the rhs slots hold the fused stage kernels and the update slots are 0."""
+        ms = (C.c_float * 5)()
+        n = C.c_int(5)
+        self._check(self.L.kt_time_kernels(self.ctx, int(n_steps), ms, C.byref(n)), "kt_time_kernels")
+        return dict(zip(self.KERNEL_SLOTS, list(ms)[:n.value]))
 
 
 # ------------------------------------------------------------------ learned root-find start

@@ -14,7 +14,7 @@
 #include <vector>
 
 #include "../../include/kt.h"
-#include "kt_stage.cuh"
+#include "kt_split.cuh"
 
 using namespace kt;
 
@@ -67,7 +67,9 @@ struct Ctx {
   // work decomposition
   int shape = 0;
   int ntiles = 0;
-  int grid_blocks = 0;
+  int grid_blocks = 0;    // fused stage kernel (FP64)
+  int grid_rhs = 0;       // mixed precision: right-hand-side kernel
+  int grid_upd = 0;       // mixed precision: update kernel
   bool tuned = false;
   int cand = 0;
   float tune_ms[kNumCandidates] = {};
@@ -136,9 +138,10 @@ void build_tiles(const std::vector<Lattice>& lat, const Shape& s, std::vector<Ti
   out.clear();
   for (int e = 0; e < (int)lat.size(); ++e) {
     const Lattice& L = lat[e];
-    for (int k = 0; k < L.nz; k += s.z)
-      for (int j = 0; j < L.ny; j += s.y)
-        for (int i = 0; i < L.nx; i += s.x) out.push_back(Tile{e, i, j, k});
+    // eta fastest: a block of a persistent grid walks a contiguous run of tiles up an eta column
+    for (int j = 0; j < L.ny; j += s.y)
+      for (int i = 0; i < L.nx; i += s.x)
+        for (int k = 0; k < L.nz; k += s.z) out.push_back(Tile{e, i, j, k});
   }
 }
 
@@ -208,6 +211,8 @@ void build_segments(const kt_eos* eos, std::vector<EosSeg<R>>& out) {
     s.P0 = (R)P0; s.mP = (R)m0; s.cP2 = (R)(3.0 * (P1 - P0) - 2.0 * m0 - m1); s.cP3 = (R)(2.0 * (P0 - P1) + m0 + m1);
     s.T0 = (R)T0; s.mT = (R)s0; s.cT2 = (R)(3.0 * (T1 - T0) - 2.0 * s0 - s1); s.cT3 = (R)(2.0 * (T0 - T1) + s0 + s1);
     s.l0 = (R)eos->lndelta[i]; s.dl = (R)(eos->lndelta[i + 1] - eos->lndelta[i]);
+    const double c2 = 3.0 * (P1 - P0) - 2.0 * m0 - m1, c3 = 2.0 * (P0 - P1) + m0 + m1;
+    s.a1 = (R)(m0 / de); s.a2 = (R)(c2 / (de * de)); s.a3 = (R)(c3 / (de * de * de));
     out[i] = s;
   }
   out[n - 1] = out[n - 2];
@@ -356,25 +361,88 @@ StageIO<R> make_io(Ctx* c, int stage) {
   return io;
 }
 
-template <typename R, int STAGE, bool LEARNED>
-void launch_stage(Ctx* c, const StageIO<R>& io) {
+// Mixed precision: the Runge-Kutta increments k_1, k_2 (FP32, 15 components each) live in the
+// memory of the FP64 q* array, which that path never stores.
+float* k_buf(Ctx* c, int stage) { return (float*)c->qs + (stage == 1 ? 0 : 15 * c->gs); }
+
+UpdIO make_uio(Ctx* c, int stage) {
+  UpdIO u;
+  StageIO<float> io = make_io<float>(c, stage);
+  u.q = c->q;
+  u.qf_n = c->qf;
+  u.k1 = k_buf(c, 1);
+  u.k2 = k_buf(c, 2);
+  u.qr_out = io.qr_out;
+  u.u_out = io.u_out;
+  u.e_out = io.e_out;
+  u.p_out = io.p_out;
+  u.e_guess = io.e_in;
+  u.d_tau = c->d_tau;
+  u.status = c->d_stat;
+  u.counters = (unsigned long long*)(c->d_stat + 4);
+  u.mlp_packed = c->learned ? c->d_mlp_packed : nullptr;
+  return u;
+}
+
+template <int STAGE>
+void launch_stage(Ctx* c, const StageIO<double>& io) {
   const Shape& s = kShapes[c->shape];
-  stage_kernel<R, STAGE, LEARNED><<<c->grid_blocks, dim3(s.x, s.y, s.z), 0, c->stream>>>(c->P, io, c->d_lat,
-                                                                                         c->d_tiles, c->ntiles);
+  stage_kernel<double, STAGE><<<c->grid_blocks, dim3(s.x, s.y, s.z), 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles,
+                                                                                    c->ntiles);
+}
+
+template <int STAGE, bool LEARNED>
+void launch_split_stage(Ctx* c, const StageIO<float>& io, const UpdIO& uio) {
+  const Shape& s = kShapes[c->shape];
+  const dim3 blk(s.x, s.y, s.z);
+  rhs_kernel<STAGE><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k_buf(c, STAGE), c->d_lat, c->d_tiles, c->ntiles);
+  update_kernel<STAGE, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
+}
+
+// ev (optional, kNumTimed + 1 events): recorded between the launches of one step, in the order
+// stage-1 rhs (or fused stage 1), stage-1 update, stage-2 rhs (or fused stage 2), stage-2 update,
+// tau advance; the FP64 path has no update launches, so their intervals are empty.
+constexpr int kNumTimed = 5;
+void mark(Ctx* c, cudaEvent_t* ev, int i) {
+  if (ev) cudaEventRecord(ev[i], c->stream);
 }
 
 template <typename R, bool LEARNED>
-void launch_step_stages(Ctx* c) {
-  launch_stage<R, 1, LEARNED>(c, make_io<R>(c, 1));
-  launch_stage<R, 2, LEARNED>(c, make_io<R>(c, 2));
+void launch_step_stages(Ctx* c, cudaEvent_t* ev) {
+  if constexpr (sizeof(R) == 4) {
+    const Shape& s = kShapes[c->shape];
+    const dim3 blk(s.x, s.y, s.z);
+    mark(c, ev, 0);
+    rhs_kernel<1><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, make_io<float>(c, 1), k_buf(c, 1), c->d_lat, c->d_tiles,
+                                                      c->ntiles);
+    mark(c, ev, 1);
+    update_kernel<1, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, make_uio(c, 1), c->d_lat, c->d_tiles,
+                                                                  c->ntiles);
+    mark(c, ev, 2);
+    rhs_kernel<2><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, make_io<float>(c, 2), k_buf(c, 2), c->d_lat, c->d_tiles,
+                                                      c->ntiles);
+    mark(c, ev, 3);
+    update_kernel<2, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, make_uio(c, 2), c->d_lat, c->d_tiles,
+                                                                  c->ntiles);
+    mark(c, ev, 4);
+  } else {
+    mark(c, ev, 0);
+    launch_stage<1>(c, make_io<double>(c, 1));
+    mark(c, ev, 1);
+    mark(c, ev, 2);
+    launch_stage<2>(c, make_io<double>(c, 2));
+    mark(c, ev, 3);
+    mark(c, ev, 4);
+  }
 }
 
 // enqueue one full step (two stages + tau advance) for the current rotation phase, then rotate
-int enqueue_step(Ctx* c) {
-  if (c->mixed && c->learned) launch_step_stages<float, true>(c);
-  else if (c->mixed) launch_step_stages<float, false>(c);
-  else launch_step_stages<double, false>(c);
+int enqueue_step(Ctx* c, cudaEvent_t* ev = nullptr) {
+  if (c->mixed && c->learned) launch_step_stages<float, true>(c, ev);
+  else if (c->mixed) launch_step_stages<float, false>(c, ev);
+  else launch_step_stages<double, false>(c, ev);
   advance_tau_kernel<<<1, 1, 0, c->stream>>>(c->d_tau, c->P.dtau);
+  mark(c, ev, 5);
   // u^{n-1} <- u^n, u^n <- u^{n+1}; the old u^{n-1} buffer (holding u^*) becomes the spare
   int ncur = c->spare, nprev = c->cur, nspare = c->prev;
   c->cur = ncur; c->prev = nprev; c->spare = nspare;
@@ -383,13 +451,13 @@ int enqueue_step(Ctx* c) {
   return KT_OK;
 }
 
-// persistent grid: as many blocks as fit on the device at once, at most one per tile
-template <typename R, bool LEARNED>
-int occupancy_blocks(const Shape& s) {
+// persistent grid: as many blocks of kernel K as fit on the device at once
+template <typename K>
+int occupancy_blocks(K kernel, const Shape& s) {
   int nb = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<R, 1, LEARNED>, s.x * s.y * s.z, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, s.x * s.y * s.z, 0);
   return std::max(1, nb) * std::max(1, sms);
 }
 
@@ -402,11 +470,16 @@ int select_shape(Ctx* c, int cand) {
   CK(cudaStreamSynchronize(c->stream));
   c->shape = shape;
   c->ntiles = (int)tiles.size();
-  int cap;
-  if (c->mixed && c->learned) cap = occupancy_blocks<float, true>(kShapes[shape]);
-  else if (c->mixed) cap = occupancy_blocks<float, false>(kShapes[shape]);
-  else cap = occupancy_blocks<double, false>(kShapes[shape]);
-  c->grid_blocks = one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles));
+  const Shape& sh = kShapes[shape];
+  auto grid = [&](int cap) { return one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles)); };
+  if (c->mixed) {
+    c->grid_rhs = grid(occupancy_blocks(rhs_kernel<1>, sh));
+    c->grid_upd = grid(c->learned ? occupancy_blocks(update_kernel<1, true>, sh)
+                                  : occupancy_blocks(update_kernel<1, false>, sh));
+    c->grid_blocks = c->grid_rhs;
+  } else {
+    c->grid_blocks = grid(occupancy_blocks(stage_kernel<double, 1>, sh));
+  }
   c->cand = cand;
   for (int p = 0; p < 3; ++p)
     if (c->graph[p]) { cudaGraphExecDestroy(c->graph[p]); c->graph[p] = nullptr; }
@@ -420,12 +493,21 @@ template <typename R, bool LEARNED>
 int time_first_stage(Ctx* c, float* ms) {
   StageIO<R> io = make_io<R>(c, 1);
   io.u_out = (R*)c->U[c->spare];
+  auto launch = [&]() {
+    if constexpr (sizeof(R) == 4) {  // writes k_1, q*'s FP32 copy, e*, P*, u* (spare buffer)
+      UpdIO u = make_uio(c, 1);
+      u.u_out = (float*)c->U[c->spare];
+      launch_split_stage<1, LEARNED>(c, io, u);
+    } else {
+      launch_stage<1>(c, io);
+    }
+  };
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
-  launch_stage<R, 1, LEARNED>(c, io);  // warm-up
+  launch();  // warm-up
   CK(cudaEventRecord(a, c->stream));
-  launch_stage<R, 1, LEARNED>(c, io);
+  launch();
   CK(cudaEventRecord(b, c->stream));
   CK(cudaEventSynchronize(b));
   CK(cudaEventElapsedTime(ms, a, b));
@@ -719,8 +801,11 @@ int kt_set_state(kt_ctx* c, double tau, const double* e, const double* u, const 
   return kt_set_state_event(c, 0, tau, e, u, pi, Pi, u_prev, on_device);
 }
 
-int kt_step(kt_ctx* c, int n_steps) {
-  if (!c || n_steps < 0) return KT_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+int begin_steps(Ctx* c, int n_steps) {
   for (int e = 0; e < c->nev; ++e)
     if (!c->ev_set[e]) return fail(c, KT_ERR_ARG, "kt_step: event %d has no state", e);
   if (c->opt.autotune && !c->tuned && n_steps > 0) {
@@ -728,22 +813,11 @@ int kt_step(kt_ctx* c, int n_steps) {
     if (rc != KT_OK) return rc;
   }
   CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
-  int done = 0;
-  if (c->opt.use_graph) {
-    while (n_steps - done >= 3) {
-      int ph = c->cur;  // the three rotation phases are told apart by the current u buffer
-      if (!c->graph[ph]) {
-        int rc = build_graph(c, ph);
-        if (rc != KT_OK) return rc;
-      }
-      CK(cudaGraphLaunch(c->graph[ph], c->stream));
-      done += 3;  // three steps return the rotation to the same phase
-    }
-  }
-  for (; done < n_steps; ++done) {
-    int rc = enqueue_step(c);
-    if (rc != KT_OK) return rc;
-  }
+  return KT_OK;
+}
+
+// read the statistics of the steps just enqueued (one synchronisation) and advance the host tau
+int finish_steps(Ctx* c, int n_steps) {
   unsigned hst[KSTAT_WORDS];
   CK(cudaMemcpyAsync(hst, c->d_stat, sizeof(hst), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -761,6 +835,58 @@ int kt_step(kt_ctx* c, int n_steps) {
   if (hst[0] & ST_NONFINITE) return fail(c, KT_ERR_NONFINITE, "kt_step: non-finite value");
   if (hst[0] & ST_INVERSION) return fail(c, KT_ERR_INVERSION, "kt_step: inversion failed in some cell");
   return KT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kt_step(kt_ctx* c, int n_steps) {
+  if (!c || n_steps < 0) return KT_ERR_ARG;
+  int rc = begin_steps(c, n_steps);
+  if (rc != KT_OK) return rc;
+  int done = 0;
+  if (c->opt.use_graph) {
+    while (n_steps - done >= 3) {
+      int ph = c->cur;  // the three rotation phases are told apart by the current u buffer
+      if (!c->graph[ph]) {
+        rc = build_graph(c, ph);
+        if (rc != KT_OK) return rc;
+      }
+      CK(cudaGraphLaunch(c->graph[ph], c->stream));
+      done += 3;  // three steps return the rotation to the same phase
+    }
+  }
+  for (; done < n_steps; ++done) {
+    rc = enqueue_step(c);
+    if (rc != KT_OK) return rc;
+  }
+  return finish_steps(c, n_steps);
+}
+
+int kt_time_kernels(kt_ctx* c, int n_steps, float* ms, int* n_kernels) {
+  if (!c || n_steps < 1 || !ms || !n_kernels || *n_kernels < kNumTimed) return KT_ERR_ARG;
+  int rc = begin_steps(c, n_steps);
+  if (rc != KT_OK) return rc;
+  cudaEvent_t ev[kNumTimed + 1];
+  for (int k = 0; k <= kNumTimed; ++k) CK(cudaEventCreate(&ev[k]));
+  double acc[kNumTimed] = {0.0};
+  for (int s = 0; s < n_steps && rc == KT_OK; ++s) {
+    rc = enqueue_step(c, ev);
+    if (rc != KT_OK) break;
+    cudaError_t e = cudaEventSynchronize(ev[kNumTimed]);
+    if (e != cudaSuccess) { rc = fail(c, KT_ERR_CUDA, "kt_time_kernels: %s", cudaGetErrorString(e)); break; }
+    for (int k = 0; k < kNumTimed; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+  }
+  for (int k = 0; k <= kNumTimed; ++k) cudaEventDestroy(ev[k]);
+  if (rc != KT_OK) return rc;
+  for (int k = 0; k < kNumTimed; ++k) ms[k] = (float)(acc[k] / n_steps);
+  *n_kernels = kNumTimed;
+  return finish_steps(c, n_steps);
 }
 
 int kt_get_state_event(kt_ctx* c, int event, double* tau, double* e, double* u, double* pi, double* Pi, double* q,

@@ -49,6 +49,7 @@ struct EosSeg {
   R P0, mP, cP2, cP3;   // P(t) = P0 + t (mP + t (cP2 + t cP3)); c_s^2 = P'(t) inv_de
   R T0, mT, cT2, cT3;   // T(t), same form
   R l0, dl;             // ln(1/3 - c_s^2) = l0 + t dl
+  R a1, a2, a3;         // the same P in d = e - e0: P = P0 + d (a1 + d (a2 + d a3)), c_s^2 = P'(d)
 };
 
 struct Coef {

@@ -26,12 +26,13 @@ constexpr int PK_W2_STRIDE = 20;
 // Features of one cell from E = T^tt - pi^tt, M^2 and Pi (FP32), with fixed physics scalings.
 // Also returns e_conf / E.
 __device__ __forceinline__ void mlp_features(float E, float M2, float Pi, float (&x)[MLP_IN], float& econf_over_E) {
-  float r2 = fminf(fmaxf(M2 / (E * E), 0.f), 0.999999f);
+  const float iE = __fdividef(1.f, E);
+  float r2 = fminf(fmaxf(M2 * iE * iE, 0.f), 0.999999f);
   float r = sqrtf(r2);
-  float ec = 3.f * (1.f - r) * (1.f + r) / (sqrtf(4.f - 3.f * r2) + 1.f);
+  float ec = __fdividef(3.f * (1.f - r) * (1.f + r), sqrtf(4.f - 3.f * r2) + 1.f);
   x[0] = (__logf(E) - 1.f) * (1.f / 6.f);
   x[1] = r2;
-  x[2] = 5.f * Pi / E;
+  x[2] = 5.f * Pi * iE;
   x[3] = 0.5f * __logf(1.f - r2);
   x[4] = ec;
   x[5] = r;

@@ -1,0 +1,349 @@
+// kt_split.cuh -- the mixed-precision Runge-Kutta stage as two launches.
+//
+// rhs_kernel<S>:    k_S = dtau C[q] in FP32 (a, b of the stage: stencil, fluxes, sources; Sec. 3.1,
+//                   App. B).  No FP64 arithmetic, so it runs at the occupancy of the FP32 code.
+// update_kernel<S>: the FP64 Heun accumulation, the root-find (learned start on the tensor cores,
+//                   or the plain safeguarded Newton), the regulator and the stores (c-f).
+//
+// Heun (Eqs. step1-finalStep) in increment form:
+//     q*      = q^n + k_1,            k_1 = dtau C[q^n]
+//     q^{n+1} = (q^n + q* + k_2) / 2 = q^n + (k_1 + k_2) / 2,   k_2 = dtau C[q*],
+// summed in FP64 onto q^n.  q* itself is never stored in FP64: the root-find of stage 1 forms the
+// components it needs (T^{tau mu}, pi^{tau mu}, Pi) in FP64, the stage-2 stencil reads the FP32
+// copy of q*, and the regulator's rescaling q* -> f q* of the pi components is carried in k_1 as
+// f k_1 + (f - 1) q^n.
+#pragma once
+#include "kt_stage.cuh"
+
+namespace kt {
+
+struct UpdIO {
+  double* q;                // q^n, FP64; stage 2 overwrites it with q^{n+1} (own cell only)
+  const float* qf_n;        // FP32 copy of q^n
+  float* k1;                // dtau C[q^n]; stage 1 rewrites its pi components with the regulated increment
+  const float* k2;          // dtau C[q*] (stage 2)
+  float* qr_out;            // FP32 copy of the new state: q* (stage 1) or q^{n+1} (stage 2), with ghosts
+  float* u_out;
+  float* e_out;
+  float* p_out;
+  const float* e_guess;     // the cell's previous energy density: the plain root-find's start
+  const double* d_tau;      // tau^n
+  unsigned* status;
+  unsigned long long* counters;
+  const uint32_t* mlp_packed;
+};
+
+// inversion inputs of q: T^{tau mu} (0-3), pi^{tau mu} (4-7), Pi (14)
+__device__ __forceinline__ constexpr bool inversion_component(int n) { return n < 8 || n == 14; }
+
+template <int STAGE>
+__global__ void __launch_bounds__(256, 2)
+    rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
+               const Tile* __restrict__ tiles, int ntiles) {
+  float amax = 0.f;
+  const double tau_n = io.d_tau[0];
+  const double tau_src = (STAGE == 1) ? tau_n : tau_n + P.dtau;
+  int t0, t1;
+  tile_range(ntiles, t0, t1);
+  for (int t = t0; t < t1; ++t) {
+    const Tile tl = tiles[t];
+    const Lattice L = lats[tl.event];
+    const int i = tl.i0 + (int)threadIdx.x, j = tl.j0 + (int)threadIdx.y, k = tl.k0 + (int)threadIdx.z;
+    if (i < L.nx && j < L.ny && k < L.nz) {
+      const long long c = L.idx(i + 2, j + 2, k + 2);
+      float dq[NQ];
+      cell_rhs<float>(P, L, io, c, tau_src, dq, amax);
+      const float dt = pr<float>(P).dtau;
+#pragma unroll
+      for (int n = 0; n < NQ; ++n) k_out[n * L.fstride + c] = dq[n] * dt;
+    }
+  }
+  block_stats(io.status, io.max_speed_bits, io.counters, 0u, amax, 0u, 0u, 0u);
+}
+
+// ------------------------------------------------------------- d) the root-find (Sec. 2.4)
+// Positive doubles are ordered like their bit patterns read as integers, so the brackets and
+// tolerances below are compared with integer instructions and the slow FP64 pipe only does
+// arithmetic.
+__device__ __forceinline__ long long obits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long abits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+__device__ __forceinline__ double clamp_pos(double x, double lo, double hi) {  // lo, hi > 0; NaN -> hi
+  return (obits(x) < obits(lo)) ? lo : ((obits(x) <= obits(hi)) ? x : hi);
+}
+
+// interval of e > 0 in the FP64 table: the rule of eos_interval with integer comparisons
+__device__ __forceinline__ int eos_interval_pos(const Params& P, double e) {
+  const EosSeg<double>* seg = P.seg_d;
+  const int n1 = P.eos_n - 2;
+  const float g = (__logf(d2f_bits(e)) - P.lne0) * P.inv_h;
+  int i = (g > 0.f) ? (int)g : 0;  // NaN compares false -> 0
+  i = min(i, n1);
+  const long long b = obits(e);
+#pragma unroll 1
+  for (int it = 0; it < 64 && i > 0 && b < obits(seg[i].e0); ++it) --i;
+#pragma unroll 1
+  for (int it = 0; it < 64 && i < n1 && b >= obits(seg[i + 1].e0); ++it) ++i;
+  return i;
+}
+
+// The residual in product form g(e) = (e - E) A(e) + M^2 = f(e) A(e), A = E + P0(e) + Pi > 0:
+// the root and the sign of f(e) = e - E + M^2 / A of Eq. (eInferred), without a reciprocal.
+// Also A, P0(e) and, in single precision, A f'(e) = A - M^2 c_s^2 / A: the Newton step on f,
+// e - f/f' = e - g/(A f'), then needs the FP64 product of g with a single-precision factor
+// (which only sets the step length; f is nearly linear in e where M is small, g is not).
+struct Resid {
+  double g, A, p0;
+  float gp;
+};
+__device__ __forceinline__ Resid residual(const Params& P, double e, double E, double EPi, double M2, float M2f) {
+  const int i = eos_interval_pos(P, e);
+  const EosSeg<double>& s = P.seg_d[i];
+  const double d = e - s.e0;
+  Resid r;
+  r.p0 = fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
+  r.A = EPi + r.p0;
+  const double em = e - E;
+  r.g = fma(em, r.A, M2);
+  const EosSeg<float>& sf = P.seg_f[i];
+  const float df = d2f_bits(d);
+  const float c2 = fmaf(df, fmaf(df, 3.f * sf.a3, 2.f * sf.a2), sf.a1);
+  const float Af = d2f_bits(r.A);
+  r.gp = Af - __fdividef(M2f * c2, Af);
+  return r;
+}
+
+// one Newton step on f: e - g / (A f')
+__device__ __forceinline__ double newton_step(double e, const Resid& r) {
+  return fma(-r.g, f2d_bits(__frcp_rn(r.gp)), e);
+}
+
+// P0(e) on the FP64 table
+__device__ __forceinline__ double eos_P_pos(const Params& P, double e) {
+  const EosSeg<double>& s = P.seg_d[eos_interval_pos(P, e)];
+  const double d = e - s.e0;
+  return fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
+}
+
+// Plain root-find: safeguarded Newton inside the bracket [e_min, E] (a step that leaves it
+// bisects), from `start` if it lies inside, else from E; stop at |de| <= 2^-50 E (g is known to
+// about one ulp of E A), at most 100 steps.  Table EOS only.
+__device__ __forceinline__ unsigned rootfind_plain(const Params& P, double E, double EPi, double M2, float M2f,
+                                                   double start, double& e, double& P0, unsigned& iters) {
+  double lo = (P.e_min > 0.0) ? P.e_min : 1e-300, hi = E;
+  e = (obits(start) >= obits(lo) && obits(start) <= obits(hi)) ? start : hi;
+  const long long stop = obits(E * 0x1p-50);
+  int it;
+  for (it = 0; it < 100; ++it) {
+    const Resid r = residual(P, e, E, EPi, M2, M2f);
+    if (abits(r.g) == 0) break;
+    if (obits(r.g) < 0) lo = e; else hi = e;
+    double en = newton_step(e, r);
+    if (!(obits(en) >= obits(lo) && obits(en) <= obits(hi))) en = 0.5 * (lo + hi);
+    const double de = en - e;
+    e = en;
+    if (abits(de) <= stop) { ++it; break; }
+  }
+  iters += (unsigned)it;
+  if (obits(e) < obits(P.e_min)) e = P.e_min;
+  P0 = eos_P_pos(P, e);
+  return (it >= 100) ? ST_INVERSION : 0u;
+}
+
+// Learned start: from e_start at most two Newton steps; the root is accepted as soon as
+// |f(e)| <= 1e-10 E, i.e. |g| <= 1e-10 E A; otherwise the plain root-find continues from the
+// last iterate and the cell counts as a fallback.
+__device__ __forceinline__ unsigned rootfind_learned(const Params& P, double E, double EPi, double M2, float M2f,
+                                                     double e_start, double& e, double& P0, unsigned& iters,
+                                                     unsigned& fallbacks) {
+  const double lo = (P.e_min > 0.0) ? P.e_min : 1e-300;
+  const double tol = 1e-10 * E;
+  e = clamp_pos(e_start, lo, E);
+#pragma unroll 1
+  for (int kk = 0; kk < 3; ++kk) {
+    const Resid r = residual(P, e, E, EPi, M2, M2f);
+    if (abits(r.g) <= obits(tol * r.A)) {
+      P0 = r.p0;
+      return 0u;
+    }
+    if (kk == 2) break;
+    e = clamp_pos(newton_step(e, r), lo, E);
+    ++iters;
+  }
+  ++fallbacks;
+  return rootfind_plain(P, E, EPi, M2, M2f, e, e, P0, iters);
+}
+
+// T^{tau mu} -> (e, P0, u^mu) at tau^{n+1} for the mixed path (Eqs. eInferred-uiInferred).  With
+// the conformal EOS and no bulk pressure the closed form e = sqrt(4E^2 - 3M^2) - E is used.
+template <bool LEARNED>
+__device__ __forceinline__ unsigned invert_split(const Params& P, double gnn, const double (&qn)[NQ], double start,
+                                                 double& e, double& P0, float (&uo)[4], unsigned& iters,
+                                                 unsigned& fallbacks) {
+  const double E = qn[0] - qn[4];
+  const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
+  const double Pi = qn[14];
+  const double M2 = fma(gnn * Mn, Mn, fma(My, My, Mx * Mx));
+  const long long bE = obits(E);
+  unsigned st = 0;
+  if (!(bE > 0 && bE < 0x7ff0000000000000LL) || !(obits(M2) < obits(E * E))) {  // E > 0 finite, M^2 < E^2
+    st = ST_INVERSION;
+    e = (P.e_min > 0.0) ? P.e_min : 1e-30;
+    P0 = e * (1.0 / 3.0);
+  } else if (!P.eos_table) {
+    if (P.bulk_on && Pi != 0.0) {
+      st = ST_INVERSION;  // bulk pressure needs a non-conformal EOS
+      e = E;
+    } else {
+      const double M = sqrt(M2);  // cancellation-free form of sqrt(4E^2 - 3M^2) - E
+      e = 3.0 * (E - M) * (E + M) / (sqrt(fma(4.0 * E, E, -3.0 * M2)) + E);
+    }
+    P0 = e * (1.0 / 3.0);
+  } else if (LEARNED) {
+    st = rootfind_learned(P, E, E + Pi, M2, d2f_bits(M2), start, e, P0, iters, fallbacks);
+  } else {
+    st = rootfind_plain(P, E, E + Pi, M2, d2f_bits(M2), start, e, P0, iters);
+  }
+  if (st) {
+    uo[0] = 1.f;
+    uo[1] = uo[2] = uo[3] = 0.f;
+  } else {
+    // u^tau = sqrt((E + P)/(e + P)), u^i = M^i / ((e + P) u^tau), P = P0 + Pi, in single precision
+    const float Pt = d2f_bits(P0) + d2f_bits(Pi);
+    const float ePt = d2f_bits(e) + Pt, EPt = d2f_bits(E) + Pt;
+    const float ut = sqrtf(__fdividef(EPt, ePt));
+    const float w = __fdividef(1.f, ePt * ut);
+    uo[0] = ut;
+    uo[1] = d2f_bits(Mx) * w;
+    uo[2] = d2f_bits(My) * w;
+    uo[3] = d2f_bits(Mn) * w;
+  }
+  if (!isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3]) ||
+      !((obits(e) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL))
+    st |= ST_NONFINITE;
+  return st;
+}
+
+template <int STAGE>
+__device__ __forceinline__ float increment(const UpdIO& io, long long a) {
+  if constexpr (STAGE == 1) return __ldg(io.k1 + a);
+  else return 0.5f * (__ldg(io.k1 + a) + __ldg(io.k2 + a));
+}
+
+// One cell; all lanes of the warp call it together (the learned start is warp-wide).
+template <int STAGE, bool LEARNED>
+__device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, const UpdIO& io, int i, int j, int k,
+                                            double tau_out, const uint32_t* s_mlp, unsigned& st, unsigned& nit,
+                                            unsigned& nreg, unsigned& nfb) {
+  const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
+  const long long fs = L.fstride;
+  const long long c = L.idx(i + 2, j + 2, k + 2);
+  double qn[NQ];  // FP64 new state; components outside the inversion set are formed after it
+#pragma unroll
+  for (int n = 0; n < NQ; ++n) qn[n] = (n == 0) ? 1.0 : 0.0;  // a harmless rest state past the edge
+  if (valid) {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n)
+      if (inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
+  }
+
+  const double gnn = P.milne ? tau_out * tau_out : 1.0;
+  double start;
+  if constexpr (LEARNED) {
+    start = learned_start(P, gnn, qn, s_mlp);
+  } else {
+    start = valid ? to_f64<float>(__ldg(io.e_guess + c)) : 1.0;
+  }
+
+  if (!valid) return;
+  double e, P0;
+  float uo[4];
+  st |= invert_split<LEARNED>(P, gnn, qn, start, e, P0, uo, nit, nfb);
+
+  // the FP32 copy read by the next stencil (and the remaining FP64 components in stage 2)
+  float qr[NQ];
+  if constexpr (STAGE == 1) {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) qr[n] = __ldg(io.qf_n + n * fs + c) + __ldg(io.k1 + n * fs + c);
+  } else {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) {
+      if (!inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
+      qr[n] = from_f64<float>(qn[n]);
+    }
+  }
+  const float eR = from_f64<float>(e), P0R = from_f64<float>(P0);
+
+  // e) regulator (Eq. regPimunu), after the root-find, on pi only
+  if (P.regulate) {
+    const float go = P.milne ? from_f64<float>(tau_out * tau_out) : 1.f;
+    float pm[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        pm[a][b] = qr[pix(a, b)];
+        pm[b][a] = pm[a][b];
+      }
+    const float f = regulator_factor<float>(P, go, eR, P0R, uo, pm, qr[14]);
+    if (f < 0.999f) ++nreg;
+    if (f != 1.f) {
+      if constexpr (STAGE == 1) {
+#pragma unroll
+        for (int n = 4; n < 14; ++n) {  // f q* = q^n + (f k_1 + (f - 1) q^n)
+          const long long a = n * fs + c;
+          io.k1[a] = fmaf(f, io.k1[a], (f - 1.f) * __ldg(io.qf_n + a));
+          qr[n] *= f;
+        }
+      } else {
+        const double fd = to_f64<float>(f);
+#pragma unroll
+        for (int n = 4; n < 14; ++n) {
+          qn[n] *= fd;
+          qr[n] *= f;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < NQ; ++n)
+    if (!isfinite(qr[n])) st |= ST_NONFINITE;
+
+  // f) stores: q^{n+1} in FP64 at the cell (no kernel reads its ghosts), the FP32 copy, u, e, P
+  //    at the cell and its ghosts
+  if constexpr (STAGE == 2) {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) io.q[n * fs + c] = qn[n];
+  }
+  for_cell_and_ghosts(P, L, i + 2, j + 2, k + 2, [&](long long t) {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) io.qr_out[n * fs + t] = qr[n];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) io.u_out[m * fs + t] = uo[m];
+    io.e_out[t] = eR;
+    io.p_out[t] = P0R;
+  });
+}
+
+template <int STAGE, bool LEARNED>
+__global__ void __launch_bounds__(256, 3)
+    update_kernel(const Params P, const UpdIO io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
+                  int ntiles) {
+  unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
+  __shared__ uint32_t s_mlp[LEARNED ? PK_WORDS : 1];
+  if constexpr (LEARNED) {
+    mlp_load_shared(s_mlp, io.mlp_packed);
+    __syncthreads();
+  }
+  const double tau_out = io.d_tau[0] + P.dtau;
+  int t0, t1;
+  tile_range(ntiles, t0, t1);
+  for (int t = t0; t < t1; ++t) {
+    const Tile tl = tiles[t];
+    const Lattice L = lats[tl.event];
+    update_cell<STAGE, LEARNED>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z,
+                                tau_out, s_mlp, st, nit, nreg, nfb);
+  }
+  block_stats(io.status, nullptr, io.counters, st, 0.f, nit, nreg, nfb);
+}
+
+}  // namespace kt

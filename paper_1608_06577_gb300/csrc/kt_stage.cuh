@@ -191,131 +191,10 @@ __device__ __forceinline__ void conserved_fluxes(const Params& P, const Lattice&
   }
 }
 
-// 1/A to full double precision: a single-precision seed and two Newton-Raphson refinements
-__device__ __forceinline__ double rcp_fp64(double A) {
-  double r = f2d_bits(__frcp_rn(d2f_bits(A)));
-  r = fma(r, fma(-A, r, 1.0), r);
-  return fma(r, fma(-A, r, 1.0), r);
-}
-
 // ------------------------------------------------------------ d) inversion, FP64 (Sec. 2.4)
-// f(e) = e - E + M^2/(E + P0(e) + Pi) = 0 by Newton-Raphson inside the bracket [lo, E],
-// with bisection whenever a step leaves it; stop at |de| <= 2^-50 E (at most 100 steps).
-// The residual f and the iterate are FP64; the step length uses f' = 1 - M^2 c_s^2/A^2 in
-// single precision, which only perturbs the contraction rate, never the root.  u^mu is formed
-// in the stencil precision R.
-template <typename R>
-__device__ __forceinline__ unsigned invert_mixed(const Params& P, double tau, const double (&qn)[NQ], double guess,
-                                                 double& e, double& P0, R (&uo)[4], unsigned& iters) {
-  const double E = qn[0] - qn[4];
-  const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
-  const double Pi = qn[14];
-  const double gnn = P.milne ? tau * tau : 1.0;
-  const double M2 = fma(Mx, Mx, fma(My, My, gnn * Mn * Mn));
-  unsigned st = 0;
-  if (!(E > 0.0) || !isfinite(E) || !isfinite(M2) || !(M2 < E * E)) {
-    st = ST_INVERSION;
-    e = (P.e_min > 0.0) ? P.e_min : 1e-30;
-  } else if (!P.eos_table && (!P.bulk_on || Pi == 0.0)) {
-    double M = sqrt(M2);  // conformal closed form e = sqrt(4E^2 - 3M^2) - E, cancellation-free
-    e = 3.0 * (E - M) * (E + M) / (sqrt(fma(4.0 * E, E, -3.0 * M2)) + E);
-  } else {
-    double lo = (P.e_min > 0.0) ? P.e_min : 1e-300, hi = E;
-    e = (guess >= lo && guess <= hi) ? guess : hi;  // the cell's previous e, else E
-    const float M2f = d2f_bits(M2);
-    int it;
-    for (it = 0; it < 100; ++it) {
-      const int i = eos_interval<double>(P, P.seg_d, e);
-      const EosSeg<double>& s = P.seg_d[i];
-      const double t = (e - s.e0) * s.inv_de;
-      const double p0 = fma(t, fma(t, fma(t, s.cP3, s.cP2), s.mP), s.P0);
-      const EosSeg<float>& sf = P.seg_f[i];
-      const float tf = d2f_bits(t);
-      const float c2 = fmaf(tf, fmaf(tf, 3.f * sf.cP3, 2.f * sf.cP2), sf.mP) * sf.inv_de;
-      const double A = E + p0 + Pi;
-      const double rA = rcp_fp64(A);
-      const double f = (e - E) + M2 * rA;
-      if (f == 0.0) break;
-      if (f < 0.0) lo = e; else hi = e;
-      const float rAf = d2f_bits(rA);
-      const float fp = 1.f - M2f * rAf * rAf * c2;
-      double en = e - f * f2d_bits(__frcp_rn(fp));
-      if (!(en >= lo && en <= hi)) en = 0.5 * (lo + hi);
-      const double de = fabs(en - e);
-      e = en;
-      if (de <= ldexp(E, -50)) { ++it; break; }  // f is known to about one ulp of E
-    }
-    iters += (unsigned)it;
-    if (it >= 100) st |= ST_INVERSION;
-  }
-  if (e < P.e_min) e = P.e_min;
-  P0 = eos_P<double>(P, e);
-  if (st) {
-    uo[0] = R(1); uo[1] = uo[2] = uo[3] = R(0);
-  } else {
-    const double Pt = P0 + Pi;
-    const R ePt = from_f64<R>(e + Pt);
-    const R ut = sqrt(from_f64<R>(E + Pt) / ePt);
-    const R w = R(1) / (ePt * ut);
-    uo[0] = ut; uo[1] = from_f64<R>(Mx) * w; uo[2] = from_f64<R>(My) * w; uo[3] = from_f64<R>(Mn) * w;
-  }
-  if (!isfinite(e) || !isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3]))
-    st |= ST_NONFINITE;
-  return st;
-}
-
-// Learned start: from e_start (the network's prediction) at most two FP64 Newton steps; the
-// cell is accepted as soon as its residual |f(e)| <= 1e-10 E, else it falls back to the plain
-// root-find of invert_mixed, started from the last iterate.
-template <typename R>
-__device__ __forceinline__ unsigned invert_learned(const Params& P, double tau, const double (&qn)[NQ],
-                                                   double e_start, double& e, double& P0, R (&uo)[4],
-                                                   unsigned& iters, unsigned& fallbacks) {
-  const double E = qn[0] - qn[4];
-  const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
-  const double Pi = qn[14];
-  const double gnn = P.milne ? tau * tau : 1.0;
-  const double M2 = fma(Mx, Mx, fma(My, My, gnn * Mn * Mn));
-  const bool closed_form = !P.eos_table && (!P.bulk_on || Pi == 0.0);
-  if (!(E > 0.0) || !isfinite(E) || !isfinite(M2) || !(M2 < E * E) || closed_form)
-    return invert_mixed<R>(P, tau, qn, e_start, e, P0, uo, iters);
-  const double lo = (P.e_min > 0.0) ? P.e_min : 1e-300;
-  e = (e_start >= lo && e_start <= E) ? e_start : E;
-  const float M2f = d2f_bits(M2);
-  const double tol = 1e-10 * E;
-  bool ok = false;
-  double p0 = 0.0;
-  for (int kk = 0; kk < 3; ++kk) {
-    const int i = eos_interval<double>(P, P.seg_d, e);
-    const EosSeg<double>& s = P.seg_d[i];
-    const double t = (e - s.e0) * s.inv_de;
-    p0 = fma(t, fma(t, fma(t, s.cP3, s.cP2), s.mP), s.P0);
-    const double rA = rcp_fp64(E + p0 + Pi);
-    const double f = (e - E) + M2 * rA;
-    if (fabs(f) <= tol) { ok = true; break; }
-    if (kk == 2) break;
-    const EosSeg<float>& sf = P.seg_f[i];
-    const float tf = d2f_bits(t);
-    const float c2 = fmaf(tf, fmaf(tf, 3.f * sf.cP3, 2.f * sf.cP2), sf.mP) * sf.inv_de;
-    const float rAf = d2f_bits(rA);
-    e = fmin(fmax(e - f * f2d_bits(__frcp_rn(1.f - M2f * rAf * rAf * c2)), lo), E);
-    ++iters;
-  }
-  if (!ok) {
-    ++fallbacks;
-    return invert_mixed<R>(P, tau, qn, e, e, P0, uo, iters);
-  }
-  P0 = p0;
-  const double Pt = P0 + Pi;
-  const R ePt = from_f64<R>(e + Pt);
-  const R ut = sqrt(from_f64<R>(E + Pt) / ePt);
-  const R w = R(1) / (ePt * ut);
-  uo[0] = ut; uo[1] = from_f64<R>(Mx) * w; uo[2] = from_f64<R>(My) * w; uo[3] = from_f64<R>(Mn) * w;
-  unsigned st = 0;
-  if (!isfinite(e) || !isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3])) st |= ST_NONFINITE;
-  return st;
-}
-
+// f(e) = e - E + M^2/(E + P0(e) + Pi) = 0 by Newton-Raphson inside the bracket [e_min, E], with
+// bisection whenever a step leaves it; stop at |de| <= 2^-50 E (at most 100 steps).  With the
+// conformal EOS and no bulk pressure, the closed form.
 __device__ __forceinline__ unsigned invert_fp64(const Params& P, double tau, const double (&qn)[NQ], double guess,
                                                 double& e, double& P0, double (&uo)[4], unsigned& iters) {
   double E = qn[0] - qn[4];
@@ -372,7 +251,7 @@ template <typename R>
 __device__ __forceinline__ R regulator_factor(const Params& P, R gnn, R e, R P0, const R (&u)[4], const R (&pi)[4][4],
                                               R Pi) {
   const R glo[4] = {R(1), R(-1), R(-1), -gnn};
-  const R gup[4] = {R(1), R(-1), R(-1), R(-1) / gnn};
+  const R gup[4] = {R(1), R(-1), R(-1), -sdiv(R(1), gnn)};
   R PP = R(0);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -383,8 +262,8 @@ __device__ __forceinline__ R regulator_factor(const Params& P, R gnn, R e, R P0,
     }
   if (!(PP > R(0))) return R(1);
   R nPP = sqrt(PP);
-  R rho = nPP / (pr<R>(P).rho_max * sqrt(e * e + R(3) * P0 * P0));
-  R den = R(1) / (pr<R>(P).xi0_rho_max * nPP);
+  R rho = sdiv(nPP, pr<R>(P).rho_max * sqrt(e * e + R(3) * P0 * P0));
+  R den = sdiv(R(1), pr<R>(P).xi0_rho_max * nPP);
   R tr = pi[0][0] - pi[1][1] - pi[2][2] - gnn * pi[3][3];
   rho = fmax(rho, fabs(tr) * den);
 #pragma unroll
@@ -393,8 +272,8 @@ __device__ __forceinline__ R regulator_factor(const Params& P, R gnn, R e, R P0,
     if (l == 3 && P.milne) o *= sqrt(gnn);
     rho = fmax(rho, fabs(o) * den);
   }
-  if (rho < R(1e-4)) return R(1) - rho * rho / R(3);
-  return tanh(rho) / rho;
+  if (rho < R(1e-4)) return R(1) - rho * rho * R(1.0 / 3.0);
+  return sdiv(tanh(rho), rho);
 }
 
 // ---------------------------------------------------------------- f) stores with ghosts
@@ -419,12 +298,11 @@ __device__ __forceinline__ int ghost_source(int g, int n, int periodic) {
   return (g < 2) ? 2 : n + 1;
 }
 
-template <typename R>
-__device__ __forceinline__ void store_with_ghosts(const Params& P, const Lattice& L, const StageIO<R>& io, int i,
-                                                  int j, int k, const double (&qn)[NQ], const R (&qr)[NQ],
-                                                  const R (&uo)[4], R e, R P0) {
-  const long long fs = L.fstride;
-  store_cell<R>(io, fs, L.idx(i, j, k), qn, qr, uo, e, P0);
+// calls put(t) for the element index t of the padded cell (i, j, k) and of every ghost cell that
+// copies it (Eqs. ghostCells_1/2, or the periodic images)
+template <typename F>
+__device__ __forceinline__ void for_cell_and_ghosts(const Params& P, const Lattice& L, int i, int j, int k, F&& put) {
+  put(L.idx(i, j, k));
   const int nn[3] = {L.nx, L.ny, L.nz};
   const int pc[3] = {i, j, k};
 #pragma unroll
@@ -436,18 +314,195 @@ __device__ __forceinline__ void store_with_ghosts(const Params& P, const Lattice
     for (int g = 0; g < 4; ++g) {
       if (ghost_source(gs[g], n, P.periodic) != pc[ax]) continue;
       int ii = (ax == 0) ? gs[g] : i, jj = (ax == 1) ? gs[g] : j, kk = (ax == 2) ? gs[g] : k;
-      store_cell<R>(io, fs, L.idx(ii, jj, kk), qn, qr, uo, e, P0);
+      put(L.idx(ii, jj, kk));
     }
   }
 }
 
-// ---------------------------------------------------------------- one cell of a tile
-// All threads of a warp call this together (the learned start is a warp-wide MMA); cells past
-// the edge of the event (valid = false) compute nothing and store nothing.
-template <typename R, int STAGE, bool LEARNED>
+template <typename R>
+__device__ __forceinline__ void store_with_ghosts(const Params& P, const Lattice& L, const StageIO<R>& io, int i,
+                                                  int j, int k, const double (&qn)[NQ], const R (&qr)[NQ],
+                                                  const R (&uo)[4], R e, R P0) {
+  const long long fs = L.fstride;
+  for_cell_and_ghosts(P, L, i, j, k, [&](long long t) { store_cell<R>(io, fs, t, qn, qr, uo, e, P0); });
+}
+
+// ---------------------------------------------------------------- a) + b) for one cell
+// dq = C[q] of Eq. (semiDiscreteKT) at the cell c: -div H in x, y, eta plus the source vector
+// J = S + G (App. B), in the stencil precision R, evaluated at tau_src.
+template <typename R>
+__device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
+                                         double tau_src, R (&dq)[NQ], float& amax) {
+  const long long fs = L.fstride;
+  const R tau = from_f64<R>(tau_src);
+  const R gnn = P.milne ? tau * tau : R(1);
+  const R inv_gnn = P.milne ? sdiv(R(1), gnn) : R(1);
+
+#pragma unroll
+  for (int n = 0; n < NQ; ++n) dq[n] = R(0);
+  R du[4][4];
+  R dv = R(0);
+  {
+    const R sfac = P.milne ? tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
+    Faces<R> Fx, Fy, Fz;
+    face_setup<R, 0>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fx);
+    face_setup<R, 1>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fy);
+    face_setup<R, 2>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fz);
+    conserved_fluxes<R>(P, L, io, c, Fx, Fy, Fz, dq);
+  }
+
+  // ---- b) sources at the cell
+  R uc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    uc[m] = ld<R>(io.u_in + m * fs, c);
+    du[0][m] = (uc[m] - ld<R>(io.u_prev + m * fs, c)) * pr<R>(P).inv_dtau;  // backward difference
+  }
+  const R* q = io.qr_in;
+  R pi[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a; b < 4; ++b) {
+      pi[a][b] = ld<R>(q + pix(a, b) * fs, c);
+      pi[b][a] = pi[a][b];
+    }
+  const R Pic = ld<R>(q + 14 * fs, c);
+  const R ec = ld<R>(io.e_in, c), P0c = ld<R>(io.p_in, c);
+  const R Pt = P0c + Pic;
+  const R it = P.milne ? tau * inv_gnn : R(0);  // Gamma^eta_{tau eta} = 1/tau
+  const R tg = P.milne ? tau : R(0);         // Gamma^tau_{eta eta}
+
+  // geometric sources of the conservation laws, Eqs. (dT001)-(dT0i1)
+  {
+    R Tnn = (ec + Pt) * uc[3] * uc[3] + Pt * inv_gnn + pi[3][3];
+    dq[0] -= ld<R>(q, c) * it + tg * Tnn;
+    dq[1] -= ld<R>(q + fs, c) * it;
+    dq[2] -= ld<R>(q + 2 * fs, c) * it;
+    dq[3] -= R(3) * ld<R>(q + 3 * fs, c) * it;
+  }
+
+  if (P.shear_on || P.bulk_on) {
+    const R glo[4] = {R(1), R(-1), R(-1), -gnn};
+    const R gup[4] = {R(1), R(-1), R(-1), -inv_gnn};
+    // u^mu_{;alpha}, alpha = 0..3 (only Gamma^eta_{tau eta} = 1/tau, Gamma^tau_{eta eta} = tau)
+    R cov[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      cov[0][a] = du[a][0] + ((a == 3) ? tg * uc[3] : R(0));
+      cov[1][a] = du[a][1];
+      cov[2][a] = du[a][2];
+      cov[3][a] = du[a][3] + ((a == 0) ? it * uc[3] : ((a == 3) ? it * uc[0] : R(0)));
+    }
+    const R theta = cov[0][0] + cov[1][1] + cov[2][2] + cov[3][3];
+    const R theta3 = theta * R(1.0 / 3.0);
+    R Dup[4], Dlo[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      Dup[m] = uc[0] * cov[m][0] + uc[1] * cov[m][1] + uc[2] * cov[m][2] + uc[3] * cov[m][3];
+      Dlo[m] = glo[m] * Dup[m];
+    }
+    // nabla^a u^m = Delta^{a b} u^m_{;b} = g^{aa} u^m_{;a} - u^a D u^m
+    R nab[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) nab[a][m] = gup[a] * cov[m][a] - uc[a] * Dup[m];
+    R sig[4][4], om[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
+        sig[a][b] = R(0.5) * (nab[a][b] + nab[b][a]) - theta3 * Dab;
+        om[a][b] = R(0.5) * (nab[b][a] - nab[a][b]);  // App. A convention
+      }
+    R ps = R(0);  // pi^{mu nu} sigma_{mu nu}
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) ps += pi[a][b] * sig[a][b] * glo[a] * glo[b];
+    const R ps3 = ps * R(1.0 / 3.0);
+
+    // transport coefficients (Sec. 2.2) from T(e), ln(1/3 - c_s^2)(e)
+    R T, lnd;
+    eos_T_lnd<R>(P, ec, T, lnd);
+    const R iu0 = sdiv(R(1), uc[0]);
+
+    if (P.shear_on) {
+      R eta_tp = (ec + P0c) * R(0.2);
+      R es = eta_over_s<R>(P, T);
+      R rate_pi = (es > R(0)) ? sdiv(T, R(5) * es) : R(INFINITY);
+      rate_pi = fmin(rate_pi, pr<R>(P).rate_max);
+      const R tpp = pr<R>(P).tpp;
+      R av[4];  // pi^{mu lambda} D u_lambda
+#pragma unroll
+      for (int m = 0; m < 4; ++m) av[m] = pi[m][0] * Dlo[0] + pi[m][1] * Dlo[1] + pi[m][2] * Dlo[2] + pi[m][3] * Dlo[3];
+      // B^{mu nu} = pi^{mu l} g_ll omega^{nu l};  C^{mu nu} = pi^{mu l} g_ll sigma^{nu l}
+      R B[4][4], Cm[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          R sb = R(0), sc = R(0);
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            sb += pi[a][l] * glo[l] * om[b][l];
+            sc += pi[a][l] * glo[l] * sig[b][l];
+          }
+          B[a][b] = sb;
+          Cm[a][b] = sc;
+        }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a; b < 4; ++b) {
+          R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
+          R I1 = av[a] * uc[b] + av[b] * uc[a];
+          R I3 = B[a][b] + B[b][a];
+          R I4 = R(0.5) * (Cm[a][b] + Cm[b][a]) - Dab * ps3;
+          R Ipi = I1 + R(4.0 / 3.0) * theta * pi[a][b] - I3 + tpp * I4 - R(1.2) * Pic * sig[a][b];
+          R S = (R(2) * eta_tp * sig[a][b] - rate_pi * pi[a][b] - Ipi) * iu0 + pi[a][b] * dv;
+          // -G^{ab}/u^tau with G^{ab} = u^c Gamma^a_{cd} pi^{db} + (a <-> b)
+          R ha = (a == 0) ? tg * uc[3] * pi[3][b] : ((a == 3) ? it * (uc[0] * pi[3][b] + uc[3] * pi[0][b]) : R(0));
+          R hb = (b == 0) ? tg * uc[3] * pi[3][a] : ((b == 3) ? it * (uc[0] * pi[3][a] + uc[3] * pi[0][a]) : R(0));
+          dq[pix(a, b)] += S - (ha + hb) * iu0;
+        }
+    }
+    if (P.bulk_on) {
+      R lrate = R(2.70805020110221) + R(2) * lnd + log(T) - ln_zeta_over_s<R>(P, T);  // ln 15 + ...
+      R rate_Pi = fmin(exp(lrate), pr<R>(P).rate_max);
+      R d = exp(lnd);
+      R zt = R(15) * d * d * (ec + P0c);
+      R IPi = R(2.0 / 3.0) * Pic * theta - R(1.6) * d * ps;
+      dq[14] += (-zt * theta - rate_Pi * Pic - IPi) * iu0 + Pic * dv;
+    }
+  }
+}
+
+// The network's start for the root-find of the cell's new state qn (components 0-7 and 14 are
+// read): features in FP32, the warp-wide tensor-core inference, e = E e_conf/E exp(y/10).
+// All 32 lanes of the warp call it together.
+// E, M^2 in single precision from the FP64 components (they only feed the features).
+__device__ __forceinline__ double learned_start(const Params& P, double gnn, const double (&qn)[NQ],
+                                                const uint32_t* s_mlp) {
+  const float Ef = d2f_bits(qn[0]) - d2f_bits(qn[4]);
+  const float Mx = d2f_bits(qn[1]) - d2f_bits(qn[5]), My = d2f_bits(qn[2]) - d2f_bits(qn[6]),
+              Mn = d2f_bits(qn[3]) - d2f_bits(qn[7]);
+  const float M2f = fmaf(Mx, Mx, fmaf(My, My, d2f_bits(gnn) * Mn * Mn));
+  float x[MLP_IN], ecE;
+  mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_bits(qn[14]), x, ecE);
+  const float y = mlp_warp_infer(s_mlp, x);
+  return f2d_bits(Ef * ecE * __expf(0.1f * y));
+}
+
+// ---------------------------------------------------------------- one cell of a tile (FP64)
+// The whole stage for one cell in one thread; cells past the edge of the event (valid = false)
+// compute nothing and store nothing.
+template <typename R, int STAGE>
 __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, const StageIO<R>& io, int i, int j,
-                                           int k, const uint32_t* s_mlp, unsigned& st, unsigned& nit, unsigned& nreg,
-                                           unsigned& nfb, float& amax) {
+                                           int k, unsigned& st, unsigned& nit, unsigned& nreg, float& amax) {
+  static_assert(sizeof(R) == 8, "the fused stage is the FP64 path; mixed precision uses kt_split.cuh");
   const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
   const long long fs = L.fstride;
   const long long c = L.idx(i + 2, j + 2, k + 2);
@@ -459,149 +514,8 @@ __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, co
   for (int n = 0; n < NQ; ++n) qn[n] = (n == 0) ? 1.0 : 0.0;
 
   if (valid) {
-    const R tau = (R)tau_src;
-    const R gnn = P.milne ? tau * tau : R(1);
-
     R dq[NQ];
-#pragma unroll
-    for (int n = 0; n < NQ; ++n) dq[n] = R(0);
-    R du[4][4];
-    R dv = R(0);
-    {
-      const R inv_gnn = P.milne ? sdiv(R(1), gnn) : R(1);
-      const R sfac = P.milne ? tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
-      Faces<R> Fx, Fy, Fz;
-      face_setup<R, 0>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fx);
-      face_setup<R, 1>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fy);
-      face_setup<R, 2>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fz);
-      conserved_fluxes<R>(P, L, io, c, Fx, Fy, Fz, dq);
-    }
-
-    // ---- b) sources at the cell
-    R uc[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      uc[m] = ld<R>(io.u_in + m * fs, c);
-      du[0][m] = (uc[m] - ld<R>(io.u_prev + m * fs, c)) * pr<R>(P).inv_dtau;  // backward difference
-    }
-    const R* q = io.qr_in;
-    R pi[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a; b < 4; ++b) {
-        pi[a][b] = ld<R>(q + pix(a, b) * fs, c);
-        pi[b][a] = pi[a][b];
-      }
-    const R Pic = ld<R>(q + 14 * fs, c);
-    const R ec = ld<R>(io.e_in, c), P0c = ld<R>(io.p_in, c);
-    const R Pt = P0c + Pic;
-    const R it = P.milne ? R(1) / tau : R(0);  // Gamma^eta_{tau eta}
-    const R tg = P.milne ? tau : R(0);         // Gamma^tau_{eta eta}
-
-    // geometric sources of the conservation laws, Eqs. (dT001)-(dT0i1)
-    {
-      R Tnn = (ec + Pt) * uc[3] * uc[3] + Pt / gnn + pi[3][3];
-      dq[0] -= ld<R>(q, c) * it + tg * Tnn;
-      dq[1] -= ld<R>(q + fs, c) * it;
-      dq[2] -= ld<R>(q + 2 * fs, c) * it;
-      dq[3] -= R(3) * ld<R>(q + 3 * fs, c) * it;
-    }
-
-    if (P.shear_on || P.bulk_on) {
-      const R glo[4] = {R(1), R(-1), R(-1), -gnn};
-      const R gup[4] = {R(1), R(-1), R(-1), R(-1) / gnn};
-      // u^mu_{;alpha}, alpha = 0..3 (only Gamma^eta_{tau eta} = 1/tau, Gamma^tau_{eta eta} = tau)
-      R cov[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        cov[0][a] = du[a][0] + ((a == 3) ? tg * uc[3] : R(0));
-        cov[1][a] = du[a][1];
-        cov[2][a] = du[a][2];
-        cov[3][a] = du[a][3] + ((a == 0) ? it * uc[3] : ((a == 3) ? it * uc[0] : R(0)));
-      }
-      const R theta = cov[0][0] + cov[1][1] + cov[2][2] + cov[3][3];
-      R Dup[4], Dlo[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        Dup[m] = uc[0] * cov[m][0] + uc[1] * cov[m][1] + uc[2] * cov[m][2] + uc[3] * cov[m][3];
-        Dlo[m] = glo[m] * Dup[m];
-      }
-      // nabla^a u^m = Delta^{a b} u^m_{;b} = g^{aa} u^m_{;a} - u^a D u^m
-      R nab[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int m = 0; m < 4; ++m) nab[a][m] = gup[a] * cov[m][a] - uc[a] * Dup[m];
-      R sig[4][4], om[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
-          sig[a][b] = R(0.5) * (nab[a][b] + nab[b][a]) - theta * Dab / R(3);
-          om[a][b] = R(0.5) * (nab[b][a] - nab[a][b]);  // App. A convention
-        }
-      R ps = R(0);  // pi^{mu nu} sigma_{mu nu}
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) ps += pi[a][b] * sig[a][b] * glo[a] * glo[b];
-
-      // transport coefficients (Sec. 2.2) from T(e), ln(1/3 - c_s^2)(e)
-      R T, lnd;
-      eos_T_lnd<R>(P, ec, T, lnd);
-      const R iu0 = R(1) / uc[0];
-
-      if (P.shear_on) {
-        R eta_tp = (ec + P0c) * R(0.2);
-        R es = eta_over_s<R>(P, T);
-        R rate_pi = (es > R(0)) ? T / (R(5) * es) : R(INFINITY);
-        rate_pi = fmin(rate_pi, pr<R>(P).rate_max);
-        const R tpp = pr<R>(P).tpp;
-        R av[4];  // pi^{mu lambda} D u_lambda
-#pragma unroll
-        for (int m = 0; m < 4; ++m) av[m] = pi[m][0] * Dlo[0] + pi[m][1] * Dlo[1] + pi[m][2] * Dlo[2] + pi[m][3] * Dlo[3];
-        // B^{mu nu} = pi^{mu l} g_ll omega^{nu l};  C^{mu nu} = pi^{mu l} g_ll sigma^{nu l}
-        R B[4][4], Cm[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            R sb = R(0), sc = R(0);
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-              sb += pi[a][l] * glo[l] * om[b][l];
-              sc += pi[a][l] * glo[l] * sig[b][l];
-            }
-            B[a][b] = sb;
-            Cm[a][b] = sc;
-          }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = a; b < 4; ++b) {
-            R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
-            R I1 = av[a] * uc[b] + av[b] * uc[a];
-            R I3 = B[a][b] + B[b][a];
-            R I4 = R(0.5) * (Cm[a][b] + Cm[b][a]) - Dab * ps / R(3);
-            R Ipi = I1 + R(4.0 / 3.0) * theta * pi[a][b] - I3 + tpp * I4 - R(1.2) * Pic * sig[a][b];
-            R S = (R(2) * eta_tp * sig[a][b] - rate_pi * pi[a][b] - Ipi) * iu0 + pi[a][b] * dv;
-            // -G^{ab}/u^tau with G^{ab} = u^c Gamma^a_{cd} pi^{db} + (a <-> b)
-            R ha = (a == 0) ? tg * uc[3] * pi[3][b] : ((a == 3) ? it * (uc[0] * pi[3][b] + uc[3] * pi[0][b]) : R(0));
-            R hb = (b == 0) ? tg * uc[3] * pi[3][a] : ((b == 3) ? it * (uc[0] * pi[3][a] + uc[3] * pi[0][a]) : R(0));
-            dq[pix(a, b)] += S - (ha + hb) * iu0;
-          }
-      }
-      if (P.bulk_on) {
-        R lrate = R(2.70805020110221) + R(2) * lnd + log(T) - ln_zeta_over_s<R>(P, T);  // ln 15 + ...
-        R rate_Pi = fmin(exp(lrate), pr<R>(P).rate_max);
-        R d = exp(lnd);
-        R zt = R(15) * d * d * (ec + P0c);
-        R IPi = R(2.0 / 3.0) * Pic * theta - R(1.6) * d * ps;
-        dq[14] += (-zt * theta - rate_Pi * Pic - IPi) * iu0 + Pic * dv;
-      }
-    }
+    cell_rhs<R>(P, L, io, c, tau_src, dq, amax);
 
     // ---- c) Heun update in FP64 (Eqs. step1-finalStep)
 #pragma unroll
@@ -614,30 +528,12 @@ __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, co
     }
   }
 
-  // learned start of the root-find: one warp-wide tensor-core pass for 32 cells
-  double e_start = -1.0;
-  if constexpr (LEARNED) {
-    const float Ef = d2f_bits(qn[0] - qn[4]);
-    const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
-    const double gnn_o = P.milne ? tau_out * tau_out : 1.0;
-    const float M2f = d2f_bits(fma(Mx, Mx, fma(My, My, gnn_o * Mn * Mn)));
-    float x[MLP_IN], ecE;
-    mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_bits(qn[14]), x, ecE);
-    const float y = mlp_warp_infer(s_mlp, x);
-    e_start = f2d_bits(Ef * ecE * __expf(0.1f * y));
-  }
-
   if (valid) {
     // ---- d) inversion at tau^{n+1}
     double e, P0;
     R uo[4];
     const double guess = to_f64<R>(ld<R>(io.e_in, c));
-    if constexpr (sizeof(R) == 8)
-      st |= invert_fp64(P, tau_out, qn, guess, e, P0, uo, nit);
-    else if constexpr (LEARNED)
-      st |= invert_learned<R>(P, tau_out, qn, e_start, e, P0, uo, nit, nfb);
-    else
-      st |= invert_mixed<R>(P, tau_out, qn, guess, e, P0, uo, nit);
+    st |= invert_fp64(P, tau_out, qn, guess, e, P0, uo, nit);
 
     // the new state in the stencil precision (the copy the next stage's stencil reads)
     R qr[NQ];
@@ -676,29 +572,23 @@ __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, co
   }
 }
 
-// ---------------------------------------------------------------- the stage kernel
-// Persistent: every block walks the tile table with stride gridDim.x; a tile is one block-shaped
-// patch of one event, so one launch per Runge-Kutta stage advances every event of the context.
-template <typename R, int STAGE, bool LEARNED>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1)
-    stage_kernel(const Params P, const StageIO<R> io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
-                 int ntiles) {
-  unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
-  float amax = 0.f;
-  __shared__ uint32_t s_mlp[LEARNED ? PK_WORDS : 1];
-  if constexpr (LEARNED) {
-    mlp_load_shared(s_mlp, io.mlp_packed);
-    __syncthreads();
-  }
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile tl = tiles[t];
-    const Lattice L = lats[tl.event];
-    stage_cell<R, STAGE, LEARNED>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y,
-                                  tl.k0 + (int)threadIdx.z, s_mlp, st, nit, nreg, nfb, amax);
-  }
+// The contiguous run [t0, t1) of the tile table that this block processes.  Tiles are ordered
+// eta-fastest, so a block of a persistent grid walks up a column of tiles and the eta-neighbour
+// planes read by its stencil are mostly still in its SM's L1.
+__device__ __forceinline__ void tile_range(int ntiles, int& t0, int& t1) {
+  const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+  t0 = (int)blockIdx.x * per;
+  t1 = min(ntiles, t0 + per);
+}
 
-  // ---- statistics: warp shuffles, then one atomic per block
-  __shared__ unsigned s_st[8], s_max[8], s_it[8], s_reg[8], s_fb[8];
+// ---------------------------------------------------------------- per-launch statistics
+// status bits OR-ed, the largest local speed (float bits, all non-negative), and the Newton /
+// regulated / fallback counters: warp reductions, then one set of atomics per block.  Every
+// thread of the block calls this once, after its last cell.
+__device__ __forceinline__ void block_stats(unsigned* status, unsigned* max_speed_bits,
+                                            unsigned long long* counters, unsigned st, float amax, unsigned nit,
+                                            unsigned nreg, unsigned nfb) {
+  __shared__ unsigned s_st[32], s_max[32], s_it[32], s_reg[32], s_fb[32];
   const unsigned full = 0xffffffffu;
   unsigned w_st = __reduce_or_sync(full, st);
   unsigned w_max = __reduce_max_sync(full, __float_as_uint(amax));
@@ -716,12 +606,33 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1)
     for (int w = 0; w < nwarps; ++w) {
       a |= s_st[w]; b = max(b, s_max[w]); cI += s_it[w]; d += s_reg[w]; fb += s_fb[w];
     }
-    if (a) atomicOr(io.status, a);
-    atomicMax(io.max_speed_bits, b);
-    if (cI) atomicAdd(io.counters + 0, (unsigned long long)cI);
-    if (d) atomicAdd(io.counters + 1, (unsigned long long)d);
-    if (fb) atomicAdd(io.counters + 2, (unsigned long long)fb);
+    if (a) atomicOr(status, a);
+    if (max_speed_bits) atomicMax(max_speed_bits, b);
+    if (cI) atomicAdd(counters + 0, (unsigned long long)cI);
+    if (d) atomicAdd(counters + 1, (unsigned long long)d);
+    if (fb) atomicAdd(counters + 2, (unsigned long long)fb);
   }
+}
+
+// ---------------------------------------------------------------- the stage kernel
+// Persistent: every block walks its run of the tile table; a tile is one block-shaped patch of one
+// event, so one launch per Runge-Kutta stage advances every event of the context.
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(256, 1)
+    stage_kernel(const Params P, const StageIO<R> io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
+                 int ntiles) {
+  unsigned st = 0, nit = 0, nreg = 0;
+  float amax = 0.f;
+  int t0, t1;
+  tile_range(ntiles, t0, t1);
+  for (int t = t0; t < t1; ++t) {
+    const Tile tl = tiles[t];
+    const Lattice L = lats[tl.event];
+    stage_cell<R, STAGE>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z, st,
+                         nit, nreg, amax);
+  }
+
+  block_stats(io.status, io.max_speed_bits, io.counters, st, amax, nit, nreg, 0u);
 }
 
 }  // namespace kt
