@@ -40,7 +40,9 @@ enum {
   KT_ERR_EOS = -4,        /* EOS table not strictly increasing in e, or too short */
   KT_ERR_STATE = -5,      /* non-finite input state or T^{tau tau} <= |T^{tau i}| after set_state */
   KT_ERR_INVERSION = -6,  /* a cell's root-find (Eq. eInferred) failed during a step */
-  KT_ERR_NONFINITE = -7   /* a non-finite value appeared during a step */
+  KT_ERR_NONFINITE = -7,  /* a non-finite value appeared during a step */
+  KT_ERR_TIMEOUT = -8     /* a copy into shared memory did not complete within its bounded wait;
+                             the step's results are invalid */
 };
 
 enum { KT_MILNE = 0, KT_CARTESIAN = 1 };              /* coordinates (Cartesian: Sec. 5.1) */
@@ -105,7 +107,7 @@ typedef struct {
   long long steps;       /* steps taken since kt_set_state */
   float max_speed;       /* max local propagation speed a (Eq. ax) seen in the last step, times the
                             direction's metric factor (tau for eta): a CFL diagnostic */
-  unsigned int status;   /* OR of per-cell status bits of the last kt_step: 1 inversion, 2 non-finite */
+  unsigned int status;   /* OR of status bits of the last kt_step: 1 inversion, 2 non-finite, 4 copy timeout */
   long long newton_iters;/* total Newton iterations in the last kt_step (all cells, both stages) */
   long long fallbacks;   /* learned mode: cells that fell back to the plain root-find */
   long long regulated;   /* cells whose pi was scaled by a factor < 0.999 in the last kt_step */

@@ -56,6 +56,7 @@ def lib():
         L.ko_create.argtypes = [C.POINTER(_Params)]
         L.ko_free.argtypes = [C.c_void_p]
         L.ko_set_state.argtypes = [C.c_void_p, C.c_double, dp, dp, dp, dp, dp]
+        L.ko_set_state_q.argtypes = [C.c_void_p, C.c_double, dp, dp, dp, dp]
         L.ko_step.argtypes = [C.c_void_p, C.c_int]
         L.ko_get_state.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp]
         L.ko_rhs.argtypes = [C.c_void_p, dp]
@@ -132,6 +133,14 @@ class Oracle:
         e, u, pi, Pi, u_prev = map(conv, (e, u, pi, Pi, u_prev))
         self._state_keep = (e, u, pi, Pi, u_prev)
         return lib().ko_set_state(self.ctx, float(tau), _ptr(e), _ptr(u), _ptr(pi), _ptr(Pi), _ptr(u_prev))
+
+    def set_state_q(self, tau, q, e, u, u_prev=None):
+        """Restart from evolved variables: q [15, cells], e [cells], u [4, cells] (with u^tau),
+        u_prev [4, cells]."""
+        conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+        q, e, u, u_prev = map(conv, (q, e, u, u_prev))
+        self._state_keep = (q, e, u, u_prev)
+        return lib().ko_set_state_q(self.ctx, float(tau), _ptr(q), _ptr(e), _ptr(u), _ptr(u_prev))
 
     def step(self, n=1) -> int:
         return lib().ko_step(self.ctx, int(n))

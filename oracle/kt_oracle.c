@@ -735,6 +735,35 @@ int ko_set_state(ko_ctx* c, double tau, const double* e, const double* u, const 
   return st;
 }
 
+int ko_set_state_q(ko_ctx* c, double tau, const double* q, const double* e, const double* u,
+                   const double* u_prev) {
+  int nx = c->P.nx, ny = c->P.ny, nz = c->P.neta;
+  size_t ncp = (size_t)nx * ny * nz;
+  c->tau = tau;
+  int st = 0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t o = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * (size_t)k);
+        size_t idx = cidx(c, i + 2, j + 2, k + 2);
+        for (int n = 0; n < NQ; ++n) c->q[n][idx] = q[(size_t)n * ncp + o];
+        double P0, cs2, T, lnd;
+        eos_eval(c, e[o], &P0, &cs2, &T, &lnd);
+        c->e[idx] = e[o];
+        c->p[idx] = P0;
+        for (int m = 0; m < 4; ++m) {
+          c->u[m][idx] = u[(size_t)m * ncp + o];
+          c->up[m][idx] = u_prev ? u_prev[(size_t)m * ncp + o] : c->u[m][idx];
+        }
+        if (!isfinite(c->q[0][idx])) st |= KO_ST_NONFINITE;
+      }
+  for (int n = 0; n < NQ; ++n) fill_ghosts(c, c->q[n]);
+  for (int m = 0; m < 4; ++m) { fill_ghosts(c, c->u[m]); fill_ghosts(c, c->up[m]); }
+  fill_ghosts(c, c->e);
+  fill_ghosts(c, c->p);
+  return st;
+}
+
 int ko_get_state(const ko_ctx* c, double* tau, double* e, double* u, double* pi, double* Pi, double* q) {
   int nx = c->P.nx, ny = c->P.ny, nz = c->P.neta;
   size_t ncp = (size_t)nx * ny * nz;

@@ -53,6 +53,11 @@ void ko_free(ko_ctx* c);
  * (tt,tx,ty,tn,xx,xy,xn,yy,yn,nn), Pi = [cells]; any of u, pi, Pi, u_prev may be NULL. */
 int ko_set_state(ko_ctx* c, double tau, const double* e, const double* u, const double* pi,
                  const double* Pi, const double* u_prev);
+/* The state given directly as the evolved variables (to restart from another program's state):
+ * q = [15][cells] conserved variables, e = [cells] and u = [4][cells] (u^tau, u^x, u^y, u^eta) as
+ * produced by the last inversion, u_prev = [4][cells] (NULL = u).  P0 is evaluated from e. */
+int ko_set_state_q(ko_ctx* c, double tau, const double* q, const double* e, const double* u,
+                   const double* u_prev);
 int ko_step(ko_ctx* c, int nsteps);
 /* e = [cells], u = [4][cells], pi = [10][cells], Pi = [cells], q = [15][cells]; NULL skips */
 int ko_get_state(const ko_ctx* c, double* tau, double* e, double* u, double* pi, double* Pi,

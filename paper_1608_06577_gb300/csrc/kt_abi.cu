@@ -3,6 +3,8 @@
 // A context holds one or more events.  Every field array spans all events: component n of
 // event e starts at n * gs + base_e (gs = sum of the events' padded sizes), so one persistent
 // launch per Runge-Kutta stage can walk a table of (event, tile) work items.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,6 +65,7 @@ struct Ctx {
   uint32_t* d_mlp_packed = nullptr;
   Lattice* d_lat = nullptr;
   Tile* d_tiles = nullptr;
+  CUtensorMap* d_tmaps = nullptr;  // mixed precision: per event, the 4-d maps of qf (first nev) and qsf
   int max_tiles = 0;
   // work decomposition
   int shape = 0;
@@ -164,6 +167,7 @@ size_t state_bytes(const std::vector<Lattice>& lat, long long gs, size_t max_cel
   b += align_up(KT_MLP_PACKED_BYTES, 256);     // packed MLP weights
   b += align_up(lat.size() * sizeof(Lattice), 256);
   b += align_up((size_t)max_tiles * sizeof(Tile), 256);
+  if (mixed) b += align_up(2 * lat.size() * sizeof(CUtensorMap), 256);
   return b;
 }
 
@@ -395,7 +399,8 @@ template <int STAGE, bool LEARNED>
 void launch_split_stage(Ctx* c, const StageIO<float>& io, const UpdIO& uio) {
   const Shape& s = kShapes[c->shape];
   const dim3 blk(s.x, s.y, s.z);
-  rhs_kernel<STAGE><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k_buf(c, STAGE), c->d_lat, c->d_tiles, c->ntiles);
+  rhs_kernel<STAGE><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k_buf(c, STAGE), c->d_lat, c->d_tiles, c->ntiles,
+                                                        c->d_tmaps + (STAGE == 1 ? 0 : c->nev));
   update_kernel<STAGE, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
 }
 
@@ -414,13 +419,13 @@ void launch_step_stages(Ctx* c, cudaEvent_t* ev) {
     const dim3 blk(s.x, s.y, s.z);
     mark(c, ev, 0);
     rhs_kernel<1><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, make_io<float>(c, 1), k_buf(c, 1), c->d_lat, c->d_tiles,
-                                                      c->ntiles);
+                                                      c->ntiles, c->d_tmaps);
     mark(c, ev, 1);
     update_kernel<1, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, make_uio(c, 1), c->d_lat, c->d_tiles,
                                                                   c->ntiles);
     mark(c, ev, 2);
     rhs_kernel<2><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, make_io<float>(c, 2), k_buf(c, 2), c->d_lat, c->d_tiles,
-                                                      c->ntiles);
+                                                      c->ntiles, c->d_tmaps + c->nev);
     mark(c, ev, 3);
     update_kernel<2, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, make_uio(c, 2), c->d_lat, c->d_tiles,
                                                                   c->ntiles);
@@ -461,6 +466,40 @@ int occupancy_blocks(K kernel, const Shape& s) {
   return std::max(1, nb) * std::max(1, sms);
 }
 
+// The TMA descriptors of the FP32 copies of q read by the mixed-precision stencil: per event a
+// 4-d map (x: pitch, y: ny + 4, eta: neta + 4, component: 15) with the strides of the padded
+// lattice, and a box of the tile plus its two-cell halo, (bx + 4) x (by + 4) x (bz + 4) x 1.
+int encode_tensor_maps(Ctx* c) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(c, KT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const Shape& s = kShapes[c->shape];
+  if ((s.x + 4) * (s.y + 4) * (s.z + 4) > kBoxMax) return fail(c, KT_ERR_ARG, "tile box exceeds the staging buffer");
+  std::vector<CUtensorMap> maps(2 * c->nev);
+  for (int w = 0; w < 2; ++w)
+    for (int e = 0; e < c->nev; ++e) {
+      const Lattice& L = c->lat[e];
+      float* base = (w == 0 ? c->qf : c->qsf) + L.base;
+      cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)NQ};
+      cuuint64_t strides[3] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4, (cuuint64_t)c->gs * 4};
+      cuuint32_t box[4] = {(cuuint32_t)(s.x + 4), (cuuint32_t)(s.y + 4), (cuuint32_t)(s.z + 4), 1};
+      cuuint32_t estr[4] = {1, 1, 1, 1};
+      CUresult r = encode(&maps[w * c->nev + e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(c, KT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for event %d", (int)r, e);
+    }
+  CK(cudaMemcpyAsync(c->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return KT_OK;
+}
+
 int select_shape(Ctx* c, int cand) {
   const int shape = cand / 2, one_per_tile = cand % 2;
   std::vector<Tile> tiles;
@@ -470,6 +509,10 @@ int select_shape(Ctx* c, int cand) {
   CK(cudaStreamSynchronize(c->stream));
   c->shape = shape;
   c->ntiles = (int)tiles.size();
+  if (c->mixed) {
+    int rc = encode_tensor_maps(c);
+    if (rc != KT_OK) return rc;
+  }
   const Shape& sh = kShapes[shape];
   auto grid = [&](int cap) { return one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles)); };
   if (c->mixed) {
@@ -712,6 +755,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   c->d_lat = (Lattice*)carve(c->lat.size() * sizeof(Lattice));
   for (const auto& s : kShapes) c->max_tiles = std::max(c->max_tiles, tiles_for(c->lat, s));
   c->d_tiles = (Tile*)carve((size_t)c->max_tiles * sizeof(Tile));
+  if (c->mixed) c->d_tmaps = (CUtensorMap*)carve(2 * c->lat.size() * sizeof(CUtensorMap));
   P.seg_d = c->seg_d;
   P.seg_f = c->seg_f;
 
@@ -832,6 +876,7 @@ int finish_steps(Ctx* c, int n_steps) {
   c->last.newton_iters = (long long)cnt[0];
   c->last.regulated = (long long)cnt[1];
   c->last.fallbacks = (long long)cnt[2];
+  if (hst[0] & ST_TIMEOUT) return fail(c, KT_ERR_TIMEOUT, "kt_step: a shared-memory copy timed out");
   if (hst[0] & ST_NONFINITE) return fail(c, KT_ERR_NONFINITE, "kt_step: non-finite value");
   if (hst[0] & ST_INVERSION) return fail(c, KT_ERR_INVERSION, "kt_step: inversion failed in some cell");
   return KT_OK;

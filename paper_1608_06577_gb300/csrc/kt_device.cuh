@@ -17,7 +17,7 @@ __host__ __device__ __forceinline__ constexpr int pix(int a, int b) {
   return lo == 0 ? 4 + hi : (lo == 1 ? 7 + hi : (lo == 2 ? 9 + hi : 13));
 }
 
-enum : unsigned { ST_INVERSION = 1u, ST_NONFINITE = 2u };
+enum : unsigned { ST_INVERSION = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
 
 __device__ __forceinline__ double f2d_bits(float f);
 __device__ __forceinline__ float d2f_bits(double d);
@@ -152,7 +152,18 @@ __device__ __forceinline__ void eos_T_lnd(const Params& P, R e, R& T, R& lnd) {
     return;
   }
   const EosSeg<R>* seg = eos_table<R>(P);
-  const EosSeg<R>& s = seg[eos_interval<R>(P, seg, e)];
+  // FP64: the exact interval.  FP32 (the mixed-precision sources): the interval of the
+  // single-precision log guess alone; next to a node that may be the neighbouring interval,
+  // whose cubic matches value and slope at the node, so the difference stays far below FP32
+  // rounding, and the dependent table loads of the correction are saved.
+  int i;
+  if constexpr (sizeof(R) == 8) {
+    i = eos_interval<R>(P, seg, e);
+  } else {
+    const float g = (__logf(e) - P.lne0) * P.inv_h;
+    i = min((g > 0.f) ? (int)g : 0, P.eos_n - 2);
+  }
+  const EosSeg<R>& s = seg[i];
   R t = (e - s.e0) * s.inv_de;
   T = fma(t, fma(t, fma(t, s.cT3, s.cT2), s.mT), s.T0);
   lnd = fma(t, s.dl, s.l0);
@@ -170,10 +181,15 @@ __device__ __forceinline__ R limited_slope_d(R dl, R dr, R theta) {
   return (dl * dr > R(0)) ? copysign(mn, dl) : R(0);
 }
 
-// a / b in the stencil precision: IEEE division in FP64; in FP32 the two-ulp fast division
-// (the operands are velocities and u^tau >= 1, far from the range where it degrades)
+// a / b, exp, ln in the stencil precision: the correctly rounded library forms in FP64; in FP32
+// the fast hardware forms (a few ulp; division operands are velocities, u^tau >= 1 and
+// transport scales, far from the range where the fast division degrades)
 __device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sexp(double x) { return exp(x); }
+__device__ __forceinline__ float sexp(float x) { return __expf(x); }
+__device__ __forceinline__ double slog(double x) { return log(x); }
+__device__ __forceinline__ float slog(float x) { return __logf(x); }
 
 // eta/s(T) and ln(zeta/s)(T): const c0 or c0 exp(-((T - c1)/c2)^2)
 template <typename R>
@@ -181,7 +197,7 @@ __device__ __forceinline__ R eta_over_s(const Params& P, R T) {
   const PR<R>& p = pr<R>(P);
   if (P.eta.kind == 0) return p.eta_c0;
   R x = (T - p.eta_c1) * p.eta_inv_c2;
-  return p.eta_c0 * exp(-x * x);
+  return p.eta_c0 * sexp(-x * x);
 }
 
 template <typename R>

@@ -14,6 +14,7 @@
 // f k_1 + (f - 1) q^n.
 #pragma once
 #include "kt_stage.cuh"
+#include "kt_tma.cuh"
 
 namespace kt {
 
@@ -36,29 +37,88 @@ struct UpdIO {
 // inversion inputs of q: T^{tau mu} (0-3), pi^{tau mu} (4-7), Pi (14)
 __device__ __forceinline__ constexpr bool inversion_component(int n) { return n < 8 || n == 14; }
 
+// Shared-memory staging of the stencil: per tile and component, a box of (bx+4) x (by+4) x (bz+4)
+// FP32 values (the tile and its two-cell halo in x, y, eta) is copied by TMA from the event's
+// 4-d tensor map (x, y, eta, component), double-buffered so that the copy of component n+1
+// overlaps the fluxes of component n.  Parts of a box beyond the padded lattice are zero-filled
+// by TMA and read by no valid cell.
+constexpr int kBoxMax = 2176;               // floats per buffer: >= 36 * 12 * 5 and a multiple of 32
+constexpr unsigned kWaitPolls = 1u << 20;   // mbarrier polls before a wait gives up (far beyond any copy)
+
 template <int STAGE>
 __global__ void __launch_bounds__(256, 2)
     rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
-               const Tile* __restrict__ tiles, int ntiles) {
+               const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ tmaps) {
+  __shared__ alignas(128) float s_q[2][kBoxMax];
+  __shared__ alignas(8) uint64_t s_bar[2];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int bx = blockDim.x + 4, by = blockDim.y + 4, bz = blockDim.z + 4;
+  const unsigned box_bytes = 4u * bx * by * bz;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
   float amax = 0.f;
+  bool bad = false;
+  unsigned issued = 0, done = 0;  // TMA copies issued and waited for (the same in every thread)
   const double tau_n = io.d_tau[0];
-  const double tau_src = (STAGE == 1) ? tau_n : tau_n + P.dtau;
+  const CellGeom<float> G = cell_geom<float>(P, (STAGE == 1) ? tau_n : tau_n + P.dtau);
+  const float th = pr<float>(P).theta;
+  const int sy = bx, sz = bx * by;
+  const int own = ((int)threadIdx.z + 2) * sz + ((int)threadIdx.y + 2) * sy + (int)threadIdx.x + 2;
+  auto stage_box = [&](const CUtensorMap* map, const Tile& tl, int n) {  // thread 0 only
+    const unsigned b = issued & 1u;
+    fence_proxy_async_smem();  // earlier reads of this buffer before the async-proxy write
+    mbar_arrive_expect_tx(&s_bar[b], box_bytes);
+    tma_load_4d(s_q[b], map, tl.i0, tl.j0, tl.k0, n, &s_bar[b]);
+  };
+
   int t0, t1;
   tile_range(ntiles, t0, t1);
   for (int t = t0; t < t1; ++t) {
     const Tile tl = tiles[t];
     const Lattice L = lats[tl.event];
+    const CUtensorMap* map = tmaps + tl.event;
+    if (__syncthreads_or(bad)) { bad = true; break; }  // every thread is done with both buffers
+    if (tid == 0) {
+      fence_tensormap_acquire(map);
+      stage_box(map, tl, 0);
+    }
+    ++issued;
+
     const int i = tl.i0 + (int)threadIdx.x, j = tl.j0 + (int)threadIdx.y, k = tl.k0 + (int)threadIdx.z;
-    if (i < L.nx && j < L.ny && k < L.nz) {
-      const long long c = L.idx(i + 2, j + 2, k + 2);
-      float dq[NQ];
-      cell_rhs<float>(P, L, io, c, tau_src, dq, amax);
+    const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
+    const long long c = valid ? L.idx(i + 2, j + 2, k + 2) : 0;
+    float dq[NQ], du[4][4], dv = 0.f;
+    Faces<float> Fx, Fy, Fz;
+    if (valid) cell_faces<float>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+
+#pragma unroll 1
+    for (int n = 0; n < NQ; ++n) {
+      if (n + 1 < NQ) {
+        if (__syncthreads_or(bad)) { bad = true; break; }  // the other buffer is free again
+        if (tid == 0) stage_box(map, tl, n + 1);
+        ++issued;
+      }
+      const unsigned b = done & 1u;
+      if (!mbar_wait(&s_bar[b], (done >> 1) & 1u, kWaitPolls)) { bad = true; continue; }
+      ++done;
+      if (valid) component_rhs<float, true>(n, &s_q[b][own], 1, sy, sz, th, Fx, Fy, Fz, dq);
+    }
+    if (valid && !bad) {  // (a timed-out block leaves at the next tile's barrier)
+      cell_sources<float>(P, L, io, c, G, du, dv, dq);
       const float dt = pr<float>(P).dtau;
 #pragma unroll
       for (int n = 0; n < NQ; ++n) k_out[n * L.fstride + c] = dq[n] * dt;
     }
   }
-  block_stats(io.status, io.max_speed_bits, io.counters, 0u, amax, 0u, 0u, 0u);
+  if (bad) {  // a copy did not complete in time: let the ones in flight land before the block exits
+    for (; done < issued; ++done) mbar_wait(&s_bar[done & 1u], (done >> 1) & 1u, kWaitPolls);
+  }
+  block_stats(io.status, io.max_speed_bits, io.counters, bad ? ST_TIMEOUT : 0u, amax, 0u, 0u, 0u);
 }
 
 // ------------------------------------------------------------- d) the root-find (Sec. 2.4)

@@ -144,15 +144,17 @@ __device__ __forceinline__ void add_row(R (&dq)[NQ], int r, R v) {
   }
 }
 
-// one component along direction D: generalised-minmod reconstruction from the five-point
-// stencil p[-2s..2s] (a0 = p[0] given) and the flux difference -(H_R - H_L)/dx; a1, b1 return
-// the neighbours for the central differences of the S_c terms
-template <typename R, int D>
-__device__ __forceinline__ R component_flux(const R* p, R a0, R th, const Faces<R>& F, R& a1, R& b1) {
-  const int s = F.s;
-  const R a2 = ld<R>(p, -2 * s), b2 = ld<R>(p, 2 * s);
-  a1 = ld<R>(p, -s);
-  b1 = ld<R>(p, s);
+// one component along one direction: generalised-minmod reconstruction from the five-point
+// stencil p[-2s..2s] (a0 = p[0] given; global memory, or shared memory if SMEM) and the flux
+// difference -(H_R - H_L)/dx; a1, b1 return the neighbours for the central differences of S_c
+template <typename R, bool SMEM>
+__device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const Faces<R>& F, R& a1, R& b1) {
+  R a2, b2;
+  if constexpr (SMEM) {
+    a2 = p[-2 * s]; a1 = p[-s]; b1 = p[s]; b2 = p[2 * s];
+  } else {
+    a2 = ld<R>(p, -2 * s); a1 = ld<R>(p, -s); b1 = ld<R>(p, s); b2 = ld<R>(p, 2 * s);
+  }
   const R d0 = a1 - a2, d1 = a0 - a1, d2 = b1 - a0, d3 = b2 - b1;
   const R sm = limited_slope_d(d0, d1, th), s0 = limited_slope_d(d1, d2, th), sp = limited_slope_d(d2, d3, th);
   const R h = R(0.5);
@@ -160,9 +162,32 @@ __device__ __forceinline__ R component_flux(const R* p, R a0, R th, const Faces<
   return fma(F.wLp, qLp, fma(F.wLm, qLm, fma(F.wRp, qRp, F.wRm * qRm)));
 }
 
-// The 15 conserved components: -div H in x, y, eta and the remaining S_c terms
-// -d_d(-v^d pi^{tau nu} + pi^{d nu}) by central differences.  The component loop is not
-// unrolled: one compact body keeps the instruction stream of the whole kernel small.
+// Component n (warp-uniform) of the 15 conserved components, at a cell whose stencil starts at
+// p with strides sx, sy, sz: -div H in x, y, eta and the remaining S_c terms
+// -d_d(-v^d pi^{tau nu} + pi^{d nu}) by central differences, added to dq.
+template <typename R, bool SMEM>
+__device__ __forceinline__ void component_rhs(int n, const R* p, int sx, int sy, int sz, R th, const Faces<R>& Fx,
+                                              const Faces<R>& Fy, const Faces<R>& Fz, R (&dq)[NQ]) {
+  const R a0 = SMEM ? p[0] : ld<R>(p, 0);
+  R a1x, b1x, a1y, b1y, a1z, b1z;
+  R acc = component_flux<R, SMEM>(p, sx, a0, th, Fx, a1x, b1x);
+  acc += component_flux<R, SMEM>(p, sy, a0, th, Fy, a1y, b1y);
+  acc += component_flux<R, SMEM>(p, sz, a0, th, Fz, a1z, b1z);
+  add_row(dq, n, acc);
+  if (n >= 4 && n <= 13) {  // pi components
+    const int r0 = cross_row<0>(n, true);
+    if (r0 >= 0)
+      add_row(dq, r0, (Fx.vpl_h * b1x - Fx.vmi_h * a1x) + (Fy.vpl_h * b1y - Fy.vmi_h * a1y) +
+                          (Fz.vpl_h * b1z - Fz.vmi_h * a1z));
+    const int rx = cross_row<0>(n, false), ry = cross_row<1>(n, false), rz = cross_row<2>(n, false);
+    if (rx >= 0) add_row(dq, rx, -(b1x - a1x) * Fx.hinv);
+    if (ry >= 0) add_row(dq, ry, -(b1y - a1y) * Fy.hinv);
+    if (rz >= 0) add_row(dq, rz, -(b1z - a1z) * Fz.hinv);
+  }
+}
+
+// All 15 components from global memory.  The component loop is not unrolled: one compact body
+// keeps the instruction stream of the whole kernel small.
 template <typename R>
 __device__ __forceinline__ void conserved_fluxes(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                                  const Faces<R>& Fx, const Faces<R>& Fy, const Faces<R>& Fz,
@@ -171,24 +196,7 @@ __device__ __forceinline__ void conserved_fluxes(const Params& P, const Lattice&
   const R th = pr<R>(P).theta;
   const R* p = io.qr_in + c;
 #pragma unroll 1
-  for (int n = 0; n < NQ; ++n, p += fs) {
-    const R a0 = ld<R>(p, 0);
-    R a1x, b1x, a1y, b1y, a1z, b1z;
-    R acc = component_flux<R, 0>(p, a0, th, Fx, a1x, b1x);
-    acc += component_flux<R, 1>(p, a0, th, Fy, a1y, b1y);
-    acc += component_flux<R, 2>(p, a0, th, Fz, a1z, b1z);
-    add_row(dq, n, acc);
-    if (n >= 4 && n <= 13) {  // pi components
-      const int r0 = cross_row<0>(n, true);
-      if (r0 >= 0)
-        add_row(dq, r0, (Fx.vpl_h * b1x - Fx.vmi_h * a1x) + (Fy.vpl_h * b1y - Fy.vmi_h * a1y) +
-                            (Fz.vpl_h * b1z - Fz.vmi_h * a1z));
-      const int rx = cross_row<0>(n, false), ry = cross_row<1>(n, false), rz = cross_row<2>(n, false);
-      if (rx >= 0) add_row(dq, rx, -(b1x - a1x) * Fx.hinv);
-      if (ry >= 0) add_row(dq, ry, -(b1y - a1y) * Fy.hinv);
-      if (rz >= 0) add_row(dq, rz, -(b1z - a1z) * Fz.hinv);
-    }
-  }
+  for (int n = 0; n < NQ; ++n, p += fs) component_rhs<R, false>(n, p, Fx.s, Fy.s, Fz.s, th, Fx, Fy, Fz, dq);
 }
 
 // ------------------------------------------------------------ d) inversion, FP64 (Sec. 2.4)
@@ -329,28 +337,57 @@ __device__ __forceinline__ void store_with_ghosts(const Params& P, const Lattice
 
 // ---------------------------------------------------------------- a) + b) for one cell
 // dq = C[q] of Eq. (semiDiscreteKT) at the cell c: -div H in x, y, eta plus the source vector
-// J = S + G (App. B), in the stencil precision R, evaluated at tau_src.
+// J = S + G (App. B), in the stencil precision R, evaluated at tau.  In three parts: the cell's
+// face data (velocities, speeds, flux weights, d_d u^mu, d_i v^i, pressure part of S_c), the 15
+// components' fluxes (conserved_fluxes or a shared-memory loop), then the sources.
+template <typename R>
+struct CellGeom {
+  R tau, gnn, inv_gnn;
+};
+template <typename R>
+__device__ __forceinline__ CellGeom<R> cell_geom(const Params& P, double tau_src) {
+  CellGeom<R> g;
+  g.tau = from_f64<R>(tau_src);
+  g.gnn = P.milne ? g.tau * g.tau : R(1);
+  g.inv_gnn = P.milne ? sdiv(R(1), g.gnn) : R(1);
+  return g;
+}
+
+template <typename R>
+__device__ __forceinline__ void cell_faces(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
+                                           const CellGeom<R>& G, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax,
+                                           Faces<R>& Fx, Faces<R>& Fy, Faces<R>& Fz) {
+#pragma unroll
+  for (int n = 0; n < NQ; ++n) dq[n] = R(0);
+  dv = R(0);
+  const R sfac = P.milne ? G.tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
+  face_setup<R, 0>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fx);
+  face_setup<R, 1>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fy);
+  face_setup<R, 2>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fz);
+}
+
+template <typename R>
+__device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
+                                             const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ]);
+
 template <typename R>
 __device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                          double tau_src, R (&dq)[NQ], float& amax) {
-  const long long fs = L.fstride;
-  const R tau = from_f64<R>(tau_src);
-  const R gnn = P.milne ? tau * tau : R(1);
-  const R inv_gnn = P.milne ? sdiv(R(1), gnn) : R(1);
-
-#pragma unroll
-  for (int n = 0; n < NQ; ++n) dq[n] = R(0);
+  const CellGeom<R> G = cell_geom<R>(P, tau_src);
   R du[4][4];
-  R dv = R(0);
-  {
-    const R sfac = P.milne ? tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
-    Faces<R> Fx, Fy, Fz;
-    face_setup<R, 0>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fx);
-    face_setup<R, 1>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fy);
-    face_setup<R, 2>(P, L, io, c, inv_gnn, sfac, dq, du, dv, amax, Fz);
-    conserved_fluxes<R>(P, L, io, c, Fx, Fy, Fz, dq);
-  }
+  R dv;
+  Faces<R> Fx, Fy, Fz;
+  cell_faces<R>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+  conserved_fluxes<R>(P, L, io, c, Fx, Fy, Fz, dq);
+  cell_sources<R>(P, L, io, c, G, du, dv, dq);
+}
 
+// the source vector J = S + G of App. B at the cell, added to dq
+template <typename R>
+__device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
+                                             const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ]) {
+  const long long fs = L.fstride;
+  const R tau = G.tau, gnn = G.gnn, inv_gnn = G.inv_gnn;
   // ---- b) sources at the cell
   R uc[4];
 #pragma unroll
@@ -470,9 +507,9 @@ __device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, cons
         }
     }
     if (P.bulk_on) {
-      R lrate = R(2.70805020110221) + R(2) * lnd + log(T) - ln_zeta_over_s<R>(P, T);  // ln 15 + ...
-      R rate_Pi = fmin(exp(lrate), pr<R>(P).rate_max);
-      R d = exp(lnd);
+      R lrate = R(2.70805020110221) + R(2) * lnd + slog(T) - ln_zeta_over_s<R>(P, T);  // ln 15 + ...
+      R rate_Pi = fmin(sexp(lrate), pr<R>(P).rate_max);
+      R d = sexp(lnd);
       R zt = R(15) * d * d * (ec + P0c);
       R IPi = R(2.0 / 3.0) * Pic * theta - R(1.6) * d * ps;
       dq[14] += (-zt * theta - rate_Pi * Pic - IPi) * iu0 + Pic * dv;
