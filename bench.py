@@ -131,31 +131,19 @@ class ClockSampler:
 
 
 def dist_setup(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        backend = "nccl" if args.impl == "ours" else "gloo"
-        dist.init_process_group(backend=backend)
-    return world, rank, local
+    """One process per GPU under torchrun; NCCL for our arm, gloo for the CPU reference arm."""
+    from paper_1608_06577_gb300 import parallel
+    return parallel.init("nccl" if args.impl == "ours" else "gloo")
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_1608_06577_gb300 import parallel
+    parallel.barrier(world)
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    t = torch.tensor([x], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1608_06577_gb300 import parallel
+    return parallel.max_over_ranks(x, world)
 
 
 # ----------------------------------------------------------------------------- oracle timing

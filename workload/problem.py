@@ -217,16 +217,23 @@ def bjorken_problem(T0_gev=0.6, tau0=0.25, dtau=0.005, nsteps=100, eta_over_s=0.
     return p
 
 
+def batch_shapes(n_events=64, seed=1000, nx_choices=tuple(range(64, 161, 16)), neta_choices=(16, 32, 48, 64),
+                 hot_range=(20, 100)):
+    """The per-event draws of batch_problems without the fields: (nx = ny, neta, hotspots)."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(n_events):
+        n = nx_choices[int(rng.uniform() * len(nx_choices))]
+        nz = neta_choices[int(rng.uniform() * len(neta_choices))]
+        nhot = hot_range[0] + int(rng.uniform() * (hot_range[1] - hot_range[0] + 1))
+        out.append((n, nz, nhot))
+    return out
+
+
 def batch_problems(n_events=64, seed=1000, eta_over_s=0.08, nx_choices=tuple(range(64, 161, 16)),
                    neta_choices=(16, 32, 48, 64), hot_range=(20, 100), **kw):
     """Events with fluctuating initial conditions and uneven grids: per event nx = ny drawn
     uniformly from nx_choices, neta from neta_choices, the hotspot count uniformly in hot_range,
     hotspot seed = seed + event (all draws from SplitMix64(seed))."""
-    rng = SplitMix64(seed)
-    probs = []
-    for ev in range(n_events):
-        n = nx_choices[int(rng.uniform() * len(nx_choices))]
-        nz = neta_choices[int(rng.uniform() * len(neta_choices))]
-        nhot = hot_range[0] + int(rng.uniform() * (hot_range[1] - hot_range[0] + 1))
-        probs.append(hotspot_problem(nx=n, ny=n, neta=nz, nhot=nhot, seed=seed + ev, eta_over_s=eta_over_s, **kw))
-    return probs
+    return [hotspot_problem(nx=n, ny=n, neta=nz, nhot=nhot, seed=seed + ev, eta_over_s=eta_over_s, **kw)
+            for ev, (n, nz, nhot) in enumerate(batch_shapes(n_events, seed, nx_choices, neta_choices, hot_range))]
