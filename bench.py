@@ -33,14 +33,15 @@ UNIT = "cell updates/s"
 #   update 1: q (T, pi^{tau mu}, Pi) 72 + k1 60 + qf 60 + e 4 -> qsf 60 + u 16 + e, p 8
 #             + regulated k1 (pi) 40                                            = 320
 #   rhs 2:    qsf 60 + u 16 + u_prev 16 + e, p 8 -> k2 60                        = 160
-#   update 2: q 120 + k1 60 + k2 60 + e 4 -> q 120 + qf 60 + u 16 + e, p 8       = 448
-# = 1088 B (the learned start skips the 4-byte e reads: 1080 B).
-BYTES_PER_CELL = {"fp64": 856, "mixed": 1088, "learned": 1080}
+#   update 2: q 120 + k1 60 + k2 60 + qf (pi) 40 + e 4 -> q 120 + qf 60 + u 16 + e, p 8
+#                                                                               = 488
+# = 1128 B (the learned start skips the 4-byte e reads: 1120 B).
+BYTES_PER_CELL = {"fp64": 856, "mixed": 1128, "learned": 1120}
 # per launch slot of kt_time_kernels (bytes per cell); FP64: the fused stage kernels
 SLOT_BYTES = {
     "fp64": {"stage1_rhs": 368, "stage2_rhs": 488},
-    "mixed": {"stage1_rhs": 160, "stage1_update": 320, "stage2_rhs": 160, "stage2_update": 448},
-    "learned": {"stage1_rhs": 160, "stage1_update": 316, "stage2_rhs": 160, "stage2_update": 444},
+    "mixed": {"stage1_rhs": 160, "stage1_update": 320, "stage2_rhs": 160, "stage2_update": 488},
+    "learned": {"stage1_rhs": 160, "stage1_update": 316, "stage2_rhs": 160, "stage2_update": 484},
 }
 SLOT_KERNEL = {"stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel", "stage1_update": "update_kernel",
                "stage2_update": "update_kernel", "tau_advance": "advance_tau_kernel"}

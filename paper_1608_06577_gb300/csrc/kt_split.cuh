@@ -45,8 +45,10 @@ __device__ __forceinline__ constexpr bool inversion_component(int n) { return n 
 constexpr int kBoxMax = 2176;               // floats per buffer: >= 36 * 12 * 5 and a multiple of 32
 constexpr unsigned kWaitPolls = 1u << 20;   // mbarrier polls before a wait gives up (far beyond any copy)
 
+// Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM, 64 (update) 32 warps;
+// both measured faster than the occupancy the compiler picks unconstrained.
 template <int STAGE>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __maxnreg__(96)
     rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
                const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ tmaps) {
   __shared__ alignas(128) float s_q[2][kBoxMax];
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(256, 2)
     Faces<float> Fx, Fy, Fz;
     if (valid) cell_faces<float>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
 
-#pragma unroll 1
+#pragma unroll  // unrolled: the component index, the rows it feeds and every branch become constants
     for (int n = 0; n < NQ; ++n) {
       if (n + 1 < NQ) {
         if (__syncthreads_or(bad)) { bad = true; break; }  // the other buffer is free again
@@ -324,12 +326,11 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   if constexpr (STAGE == 1) {
 #pragma unroll
     for (int n = 0; n < NQ; ++n) qr[n] = __ldg(io.qf_n + n * fs + c) + __ldg(io.k1 + n * fs + c);
-  } else {
+  } else {  // pi components outside the inversion set: FP32 values for the regulator, FP64 below
 #pragma unroll
-    for (int n = 0; n < NQ; ++n) {
-      if (!inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
-      qr[n] = from_f64<float>(qn[n]);
-    }
+    for (int n = 0; n < NQ; ++n)
+      qr[n] = inversion_component(n) ? from_f64<float>(qn[n])
+                                     : __ldg(io.qf_n + n * fs + c) + increment<STAGE>(io, n * fs + c);
   }
   const float eR = from_f64<float>(e), P0R = from_f64<float>(P0);
 
@@ -354,14 +355,29 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
           io.k1[a] = fmaf(f, io.k1[a], (f - 1.f) * __ldg(io.qf_n + a));
           qr[n] *= f;
         }
-      } else {
-        const double fd = to_f64<float>(f);
+      } else {  // f q^{n+1} = q^n + (f dq + (f - 1) q^n), dq = (k_1 + k_2)/2: one FP64 add, no multiply
 #pragma unroll
-        for (int n = 4; n < 14; ++n) {
-          qn[n] *= fd;
-          qr[n] *= f;
+        for (int n = 4; n < 8; ++n) {
+          const long long a = n * fs + c;
+          qn[n] = __ldg(io.q + a) + to_f64<float>(fmaf(f, increment<STAGE>(io, a), (f - 1.f) * __ldg(io.qf_n + a)));
+          qr[n] = from_f64<float>(qn[n]);
         }
       }
+    }
+    if constexpr (STAGE == 2) {
+#pragma unroll
+      for (int n = 8; n < 14; ++n) {
+        const long long a = n * fs + c;
+        qn[n] = __ldg(io.q + a) + to_f64<float>(fmaf(f, increment<STAGE>(io, a), (f - 1.f) * __ldg(io.qf_n + a)));
+        qr[n] = from_f64<float>(qn[n]);
+      }
+    }
+  } else if constexpr (STAGE == 2) {
+#pragma unroll
+    for (int n = 8; n < 14; ++n) {
+      const long long a = n * fs + c;
+      qn[n] = __ldg(io.q + a) + to_f64<float>(increment<STAGE>(io, a));
+      qr[n] = from_f64<float>(qn[n]);
     }
   }
 #pragma unroll
@@ -385,7 +401,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
 }
 
 template <int STAGE, bool LEARNED>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __maxnreg__(64)
     update_kernel(const Params P, const UpdIO io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
                   int ntiles) {
   unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
