@@ -391,16 +391,33 @@ UpdIO make_uio(Ctx* c, int stage) {
 template <int STAGE>
 void launch_stage(Ctx* c, const StageIO<double>& io) {
   const Shape& s = kShapes[c->shape];
-  stage_kernel<double, STAGE><<<c->grid_blocks, dim3(s.x, s.y, s.z), 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles,
-                                                                                    c->ntiles);
+  const dim3 blk(s.x, s.y, s.z);
+  if (c->P.theta == 1.0)
+    stage_kernel<double, STAGE, true><<<c->grid_blocks, blk, 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles, c->ntiles);
+  else
+    stage_kernel<double, STAGE, false><<<c->grid_blocks, blk, 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles,
+                                                                             c->ntiles);
+}
+
+// the right-hand-side kernel of a stage, with the minmod specialised when theta = 1
+template <int STAGE>
+void launch_rhs(Ctx* c, const StageIO<float>& io) {
+  const Shape& s = kShapes[c->shape];
+  const dim3 blk(s.x, s.y, s.z);
+  const CUtensorMap* maps = c->d_tmaps + (STAGE == 1 ? 0 : c->nev);
+  if (c->P.theta == 1.0)
+    rhs_kernel<STAGE, true><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k_buf(c, STAGE), c->d_lat, c->d_tiles,
+                                                               c->ntiles, maps);
+  else
+    rhs_kernel<STAGE, false><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k_buf(c, STAGE), c->d_lat, c->d_tiles,
+                                                                c->ntiles, maps);
 }
 
 template <int STAGE, bool LEARNED>
 void launch_split_stage(Ctx* c, const StageIO<float>& io, const UpdIO& uio) {
   const Shape& s = kShapes[c->shape];
   const dim3 blk(s.x, s.y, s.z);
-  rhs_kernel<STAGE><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k_buf(c, STAGE), c->d_lat, c->d_tiles, c->ntiles,
-                                                        c->d_tmaps + (STAGE == 1 ? 0 : c->nev));
+  launch_rhs<STAGE>(c, io);
   update_kernel<STAGE, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
 }
 
@@ -418,14 +435,12 @@ void launch_step_stages(Ctx* c, cudaEvent_t* ev) {
     const Shape& s = kShapes[c->shape];
     const dim3 blk(s.x, s.y, s.z);
     mark(c, ev, 0);
-    rhs_kernel<1><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, make_io<float>(c, 1), k_buf(c, 1), c->d_lat, c->d_tiles,
-                                                      c->ntiles, c->d_tmaps);
+    launch_rhs<1>(c, make_io<float>(c, 1));
     mark(c, ev, 1);
     update_kernel<1, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, make_uio(c, 1), c->d_lat, c->d_tiles,
                                                                   c->ntiles);
     mark(c, ev, 2);
-    rhs_kernel<2><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, make_io<float>(c, 2), k_buf(c, 2), c->d_lat, c->d_tiles,
-                                                      c->ntiles, c->d_tmaps + c->nev);
+    launch_rhs<2>(c, make_io<float>(c, 2));
     mark(c, ev, 3);
     update_kernel<2, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, make_uio(c, 2), c->d_lat, c->d_tiles,
                                                                   c->ntiles);
@@ -516,12 +531,14 @@ int select_shape(Ctx* c, int cand) {
   const Shape& sh = kShapes[shape];
   auto grid = [&](int cap) { return one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles)); };
   if (c->mixed) {
-    c->grid_rhs = grid(occupancy_blocks(rhs_kernel<1>, sh));
+    c->grid_rhs = grid(c->P.theta == 1.0 ? occupancy_blocks(rhs_kernel<1, true>, sh)
+                                         : occupancy_blocks(rhs_kernel<1, false>, sh));
     c->grid_upd = grid(c->learned ? occupancy_blocks(update_kernel<1, true>, sh)
                                   : occupancy_blocks(update_kernel<1, false>, sh));
     c->grid_blocks = c->grid_rhs;
   } else {
-    c->grid_blocks = grid(occupancy_blocks(stage_kernel<double, 1>, sh));
+    c->grid_blocks = grid(c->P.theta == 1.0 ? occupancy_blocks(stage_kernel<double, 1, true>, sh)
+                                            : occupancy_blocks(stage_kernel<double, 1, false>, sh));
   }
   c->cand = cand;
   for (int p = 0; p < 3; ++p)

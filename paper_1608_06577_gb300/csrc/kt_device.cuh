@@ -174,10 +174,17 @@ __device__ __forceinline__ void eos_T_lnd(const Params& P, R e, R& T, R& lnd) {
 // exactly when dl and dr do, and then the result is that sign times the smallest magnitude.
 // This is the slope times the cell size.  (The product test loses slopes whose one-sided
 // differences multiply below the smallest subnormal, ~1e-45 in FP32 and ~1e-323 in FP64.)
-template <typename R>
+// TH1: theta = 1, where (|dl| + |dr|)/2 >= min(|dl|, |dr|) never decides (up to one ulp of the
+// rounded sum in FP32, the only precision that uses it).
+template <typename R, bool TH1 = false>
 __device__ __forceinline__ R limited_slope_d(R dl, R dr, R theta) {
-  R mn = fmin(theta * fabs(dl), theta * fabs(dr));
-  mn = fmin(mn, R(0.5) * fabs(dl + dr));
+  R mn;
+  if constexpr (TH1) {
+    mn = fmin(fabs(dl), fabs(dr));
+  } else {
+    mn = fmin(theta * fabs(dl), theta * fabs(dr));
+    mn = fmin(mn, R(0.5) * fabs(dl + dr));
+  }
   return (dl * dr > R(0)) ? copysign(mn, dl) : R(0);
 }
 

@@ -47,7 +47,7 @@ constexpr unsigned kWaitPolls = 1u << 20;   // mbarrier polls before a wait give
 
 // Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM, 64 (update) 32 warps;
 // both measured faster than the occupancy the compiler picks unconstrained.
-template <int STAGE>
+template <int STAGE, bool TH1>
 __global__ void __maxnreg__(96)
     rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
                const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ tmaps) {
@@ -96,7 +96,7 @@ __global__ void __maxnreg__(96)
     const long long c = valid ? L.idx(i + 2, j + 2, k + 2) : 0;
     float dq[NQ], du[4][4], dv = 0.f;
     Faces<float> Fx, Fy, Fz;
-    if (valid) cell_faces<float>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+    if (valid) cell_faces<float, TH1>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
 
 #pragma unroll  // unrolled: the component index, the rows it feeds and every branch become constants
     for (int n = 0; n < NQ; ++n) {
@@ -108,7 +108,7 @@ __global__ void __maxnreg__(96)
       const unsigned b = done & 1u;
       if (!mbar_wait(&s_bar[b], (done >> 1) & 1u, kWaitPolls)) { bad = true; continue; }
       ++done;
-      if (valid) component_rhs<float, true>(n, &s_q[b][own], 1, sy, sz, th, Fx, Fy, Fz, dq);
+      if (valid) component_rhs<float, true, TH1>(n, &s_q[b][own], 1, sy, sz, th, Fx, Fy, Fz, dq);
     }
     if (valid && !bad) {  // (a timed-out block leaves at the next tile's barrier)
       cell_sources<float>(P, L, io, c, G, du, dv, dq);
@@ -326,11 +326,12 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   if constexpr (STAGE == 1) {
 #pragma unroll
     for (int n = 0; n < NQ; ++n) qr[n] = __ldg(io.qf_n + n * fs + c) + __ldg(io.k1 + n * fs + c);
-  } else {  // pi components outside the inversion set: FP32 values for the regulator, FP64 below
+  } else {  // the pi components outside the inversion set are read once, here
 #pragma unroll
-    for (int n = 0; n < NQ; ++n)
-      qr[n] = inversion_component(n) ? from_f64<float>(qn[n])
-                                     : __ldg(io.qf_n + n * fs + c) + increment<STAGE>(io, n * fs + c);
+    for (int n = 0; n < NQ; ++n) {
+      if (!inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
+      qr[n] = from_f64<float>(qn[n]);
+    }
   }
   const float eR = from_f64<float>(e), P0R = from_f64<float>(P0);
 
@@ -355,29 +356,14 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
           io.k1[a] = fmaf(f, io.k1[a], (f - 1.f) * __ldg(io.qf_n + a));
           qr[n] *= f;
         }
-      } else {  // f q^{n+1} = q^n + (f dq + (f - 1) q^n), dq = (k_1 + k_2)/2: one FP64 add, no multiply
+      } else {  // rescale the FP64 state in registers (re-reading its inputs would miss L2)
+        const double fd = to_f64<float>(f);
 #pragma unroll
-        for (int n = 4; n < 8; ++n) {
-          const long long a = n * fs + c;
-          qn[n] = __ldg(io.q + a) + to_f64<float>(fmaf(f, increment<STAGE>(io, a), (f - 1.f) * __ldg(io.qf_n + a)));
-          qr[n] = from_f64<float>(qn[n]);
+        for (int n = 4; n < 14; ++n) {
+          qn[n] *= fd;
+          qr[n] *= f;
         }
       }
-    }
-    if constexpr (STAGE == 2) {
-#pragma unroll
-      for (int n = 8; n < 14; ++n) {
-        const long long a = n * fs + c;
-        qn[n] = __ldg(io.q + a) + to_f64<float>(fmaf(f, increment<STAGE>(io, a), (f - 1.f) * __ldg(io.qf_n + a)));
-        qr[n] = from_f64<float>(qn[n]);
-      }
-    }
-  } else if constexpr (STAGE == 2) {
-#pragma unroll
-    for (int n = 8; n < 14; ++n) {
-      const long long a = n * fs + c;
-      qn[n] = __ldg(io.q + a) + to_f64<float>(increment<STAGE>(io, a));
-      qr[n] = from_f64<float>(qn[n]);
     }
   }
 #pragma unroll

@@ -57,7 +57,7 @@ struct Faces {
 // (Sec. 3.1), the local speeds a = max(|v^p|, |v^m|) (Eq. ax), the central differences
 // d_d u^mu and d_d v^d, and the pressure part of S_c (App. B):
 // -d_d (v^d P delta^nu_tau - g^{d nu} P), P = P0 + Pi.
-template <typename R, int D>
+template <typename R, int D, bool TH1 = false>
 __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                            R inv_gnn, R sfac, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax,
                                            Faces<R>& F) {
@@ -79,8 +79,10 @@ __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, co
   const R up2t = ld<R>(u, c + 2 * s), up2d = ld<R>(u + (D + 1) * fs, c + 2 * s);
   R t0 = um1[0] - um2t, t1 = u0t - um1[0], t2 = up1[0] - u0t, t3 = up2t - up1[0];
   R d0 = um1[D + 1] - um2d, d1 = u0d - um1[D + 1], d2 = up1[D + 1] - u0d, d3 = up2d - up1[D + 1];
-  const R st_m = limited_slope_d(t0, t1, th), st_0 = limited_slope_d(t1, t2, th), st_p = limited_slope_d(t2, t3, th);
-  const R sd_m = limited_slope_d(d0, d1, th), sd_0 = limited_slope_d(d1, d2, th), sd_p = limited_slope_d(d2, d3, th);
+  const R st_m = limited_slope_d<R, TH1>(t0, t1, th), st_0 = limited_slope_d<R, TH1>(t1, t2, th),
+          st_p = limited_slope_d<R, TH1>(t2, t3, th);
+  const R sd_m = limited_slope_d<R, TH1>(d0, d1, th), sd_0 = limited_slope_d<R, TH1>(d1, d2, th),
+          sd_p = limited_slope_d<R, TH1>(d2, d3, th);
   const R h = R(0.5);
   const R vLm = sdiv(fma(h, sd_m, um1[D + 1]), fma(h, st_m, um1[0]));
   const R vLp = sdiv(fma(-h, sd_0, u0d), fma(-h, st_0, u0t));
@@ -147,7 +149,7 @@ __device__ __forceinline__ void add_row(R (&dq)[NQ], int r, R v) {
 // one component along one direction: generalised-minmod reconstruction from the five-point
 // stencil p[-2s..2s] (a0 = p[0] given; global memory, or shared memory if SMEM) and the flux
 // difference -(H_R - H_L)/dx; a1, b1 return the neighbours for the central differences of S_c
-template <typename R, bool SMEM>
+template <typename R, bool SMEM, bool TH1 = false>
 __device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const Faces<R>& F, R& a1, R& b1) {
   R a2, b2;
   if constexpr (SMEM) {
@@ -156,7 +158,8 @@ __device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const
     a2 = ld<R>(p, -2 * s); a1 = ld<R>(p, -s); b1 = ld<R>(p, s); b2 = ld<R>(p, 2 * s);
   }
   const R d0 = a1 - a2, d1 = a0 - a1, d2 = b1 - a0, d3 = b2 - b1;
-  const R sm = limited_slope_d(d0, d1, th), s0 = limited_slope_d(d1, d2, th), sp = limited_slope_d(d2, d3, th);
+  const R sm = limited_slope_d<R, TH1>(d0, d1, th), s0 = limited_slope_d<R, TH1>(d1, d2, th),
+          sp = limited_slope_d<R, TH1>(d2, d3, th);
   const R h = R(0.5);
   const R qLm = fma(h, sm, a1), qLp = fma(-h, s0, a0), qRm = fma(h, s0, a0), qRp = fma(-h, sp, b1);
   return fma(F.wLp, qLp, fma(F.wLm, qLm, fma(F.wRp, qRp, F.wRm * qRm)));
@@ -165,14 +168,14 @@ __device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const
 // Component n (warp-uniform) of the 15 conserved components, at a cell whose stencil starts at
 // p with strides sx, sy, sz: -div H in x, y, eta and the remaining S_c terms
 // -d_d(-v^d pi^{tau nu} + pi^{d nu}) by central differences, added to dq.
-template <typename R, bool SMEM>
+template <typename R, bool SMEM, bool TH1 = false>
 __device__ __forceinline__ void component_rhs(int n, const R* p, int sx, int sy, int sz, R th, const Faces<R>& Fx,
                                               const Faces<R>& Fy, const Faces<R>& Fz, R (&dq)[NQ]) {
   const R a0 = SMEM ? p[0] : ld<R>(p, 0);
   R a1x, b1x, a1y, b1y, a1z, b1z;
-  R acc = component_flux<R, SMEM>(p, sx, a0, th, Fx, a1x, b1x);
-  acc += component_flux<R, SMEM>(p, sy, a0, th, Fy, a1y, b1y);
-  acc += component_flux<R, SMEM>(p, sz, a0, th, Fz, a1z, b1z);
+  R acc = component_flux<R, SMEM, TH1>(p, sx, a0, th, Fx, a1x, b1x);
+  acc += component_flux<R, SMEM, TH1>(p, sy, a0, th, Fy, a1y, b1y);
+  acc += component_flux<R, SMEM, TH1>(p, sz, a0, th, Fz, a1z, b1z);
   add_row(dq, n, acc);
   if (n >= 4 && n <= 13) {  // pi components
     const int r0 = cross_row<0>(n, true);
@@ -188,7 +191,7 @@ __device__ __forceinline__ void component_rhs(int n, const R* p, int sx, int sy,
 
 // All 15 components from global memory.  The component loop is not unrolled: one compact body
 // keeps the instruction stream of the whole kernel small.
-template <typename R>
+template <typename R, bool TH1 = false>
 __device__ __forceinline__ void conserved_fluxes(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                                  const Faces<R>& Fx, const Faces<R>& Fy, const Faces<R>& Fz,
                                                  R (&dq)[NQ]) {
@@ -196,7 +199,7 @@ __device__ __forceinline__ void conserved_fluxes(const Params& P, const Lattice&
   const R th = pr<R>(P).theta;
   const R* p = io.qr_in + c;
 #pragma unroll 1
-  for (int n = 0; n < NQ; ++n, p += fs) component_rhs<R, false>(n, p, Fx.s, Fy.s, Fz.s, th, Fx, Fy, Fz, dq);
+  for (int n = 0; n < NQ; ++n, p += fs) component_rhs<R, false, TH1>(n, p, Fx.s, Fy.s, Fz.s, th, Fx, Fy, Fz, dq);
 }
 
 // ------------------------------------------------------------ d) inversion, FP64 (Sec. 2.4)
@@ -353,7 +356,7 @@ __device__ __forceinline__ CellGeom<R> cell_geom(const Params& P, double tau_src
   return g;
 }
 
-template <typename R>
+template <typename R, bool TH1 = false>
 __device__ __forceinline__ void cell_faces(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                            const CellGeom<R>& G, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax,
                                            Faces<R>& Fx, Faces<R>& Fy, Faces<R>& Fz) {
@@ -361,24 +364,24 @@ __device__ __forceinline__ void cell_faces(const Params& P, const Lattice& L, co
   for (int n = 0; n < NQ; ++n) dq[n] = R(0);
   dv = R(0);
   const R sfac = P.milne ? G.tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
-  face_setup<R, 0>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fx);
-  face_setup<R, 1>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fy);
-  face_setup<R, 2>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fz);
+  face_setup<R, 0, TH1>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fx);
+  face_setup<R, 1, TH1>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fy);
+  face_setup<R, 2, TH1>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fz);
 }
 
 template <typename R>
 __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                              const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ]);
 
-template <typename R>
+template <typename R, bool TH1 = false>
 __device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                          double tau_src, R (&dq)[NQ], float& amax) {
   const CellGeom<R> G = cell_geom<R>(P, tau_src);
   R du[4][4];
   R dv;
   Faces<R> Fx, Fy, Fz;
-  cell_faces<R>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
-  conserved_fluxes<R>(P, L, io, c, Fx, Fy, Fz, dq);
+  cell_faces<R, TH1>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+  conserved_fluxes<R, TH1>(P, L, io, c, Fx, Fy, Fz, dq);
   cell_sources<R>(P, L, io, c, G, du, dv, dq);
 }
 
@@ -536,7 +539,7 @@ __device__ __forceinline__ double learned_start(const Params& P, double gnn, con
 // ---------------------------------------------------------------- one cell of a tile (FP64)
 // The whole stage for one cell in one thread; cells past the edge of the event (valid = false)
 // compute nothing and store nothing.
-template <typename R, int STAGE>
+template <typename R, int STAGE, bool TH1>
 __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, const StageIO<R>& io, int i, int j,
                                            int k, unsigned& st, unsigned& nit, unsigned& nreg, float& amax) {
   static_assert(sizeof(R) == 8, "the fused stage is the FP64 path; mixed precision uses kt_split.cuh");
@@ -552,7 +555,7 @@ __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, co
 
   if (valid) {
     R dq[NQ];
-    cell_rhs<R>(P, L, io, c, tau_src, dq, amax);
+    cell_rhs<R, TH1>(P, L, io, c, tau_src, dq, amax);
 
     // ---- c) Heun update in FP64 (Eqs. step1-finalStep)
 #pragma unroll
@@ -654,7 +657,7 @@ __device__ __forceinline__ void block_stats(unsigned* status, unsigned* max_spee
 // ---------------------------------------------------------------- the stage kernel
 // Persistent: every block walks its run of the tile table; a tile is one block-shaped patch of one
 // event, so one launch per Runge-Kutta stage advances every event of the context.
-template <typename R, int STAGE>
+template <typename R, int STAGE, bool TH1>
 __global__ void __launch_bounds__(256, 1)
     stage_kernel(const Params P, const StageIO<R> io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
                  int ntiles) {
@@ -665,7 +668,7 @@ __global__ void __launch_bounds__(256, 1)
   for (int t = t0; t < t1; ++t) {
     const Tile tl = tiles[t];
     const Lattice L = lats[tl.event];
-    stage_cell<R, STAGE>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z, st,
+    stage_cell<R, STAGE, TH1>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z, st,
                          nit, nreg, amax);
   }
 
