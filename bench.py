@@ -64,6 +64,11 @@ def parse():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--iface", default="recon", choices=["recon", "invert"],
+                    help="face velocities: extrapolated u (default) or root-finds of the face states")
+    ap.add_argument("--eos", default="workload", choices=["workload", "lattice"],
+                    help="workload: c_s^2(T) table, eta/s 0.08, gaussian zeta/s; lattice: the paper's "
+                         "lattice EOS with its zeta/s parametrisation and eta/s 0.2")
     return ap.parse_args()
 
 
@@ -233,7 +238,13 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     n = args.n
-    prob = hotspot_problem(nx=n, ny=n, neta=n, seed=1 + rank)
+    if args.eos == "lattice":
+        from workload.eos import lattice_table
+        prob = hotspot_problem(nx=n, ny=n, neta=n, seed=1 + rank, eta_over_s=0.2, zeta="paper",
+                               eos_table=lattice_table())
+    else:
+        prob = hotspot_problem(nx=n, ny=n, neta=n, seed=1 + rank)
+    prob.iface = args.iface
     cells = prob.ncells
     hbm_peak, peak_kind = measured_peaks()
 
@@ -335,10 +346,13 @@ def run_ours(args, world, rank, local):
         line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": main["steps"],
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f32+f64", "data": "synthetic",
-                "config": {"workload": f"hotspots {n}x{n}x{n} Milne, nonconformal EOS, eta/s 0.08, "
-                                       f"zeta/s gaussian, dtau 0.005 fm", "global_batch": world, "seq_len": None,
+                "config": {"workload": (f"hotspots {n}x{n}x{n} Milne, nonconformal EOS, eta/s 0.08, "
+                                        f"zeta/s gaussian, dtau 0.005 fm") if args.eos == "workload" else
+                                       (f"hotspots {n}x{n}x{n} Milne, lattice EOS (Sec. 2.3), eta/s 0.2, "
+                                        f"zeta/s of Eq. (zetas), dtau 0.005 fm"),
+                           "global_batch": world, "seq_len": None,
                            "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)",
-                           "mode": args.mode},
+                           "mode": args.mode, "iface": args.iface, "eos": args.eos},
                 "modes": {m: {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
                               "newton_iters_per_cell_stage": r["stats"]["newton_iters"] / ncs(r),
                               "fallbacks_per_cell_stage": r["stats"]["fallbacks"] / ncs(r)}

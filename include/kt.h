@@ -49,8 +49,9 @@ enum { KT_MILNE = 0, KT_CARTESIAN = 1 };              /* coordinates (Cartesian:
 enum { KT_BC_COPY = 0, KT_BC_PERIODIC = 1 };          /* ghost cells: Eqs. ghostCells_1/2 or periodic */
 enum { KT_FP64 = 0, KT_MIXED = 1 };                   /* precision mode */
 enum { KT_INV_PLAIN = 0, KT_INV_LEARNED = 1 };        /* inversion start: previous e, or MLP */
+enum { KT_IFACE_RECON = 0, KT_IFACE_INVERT = 1 };     /* face velocities (see kt_options.iface) */
 enum { KT_EOS_CONFORMAL = 0, KT_EOS_TABLE = 1 };
-enum { KT_COEF_CONST = 0, KT_COEF_GAUSS = 1 };
+enum { KT_COEF_CONST = 0, KT_COEF_GAUSS = 1, KT_COEF_PAPER_ZETA = 2 };
 
 typedef struct {
   int nx, ny, neta; /* physical cells per axis, each >= 1 */
@@ -70,7 +71,10 @@ typedef struct {
 } kt_eos;
 
 /* Specific viscosity eta/s or zeta/s as a function of T (fm^-1):
- * KT_COEF_CONST: c0;  KT_COEF_GAUSS: c0 exp(-((T - c1)/c2)^2).
+ * KT_COEF_CONST: c0;  KT_COEF_GAUSS: c0 exp(-((T - c1)/c2)^2);
+ * KT_COEF_PAPER_ZETA: c0 times the zeta/s parametrisation of Sec. 2.2, Eq. (zetas), with
+ *   x = T/T_c, T_c = c1 (the paper uses 200 MeV): a quadratic for 0.995 <= x <= 1.05 and
+ *   exponential tails above (-> 0.001) and below (-> 0.03).
  * KT_COEF_CONST with c0 = 0 switches the channel off (pi == 0 or Pi == 0). */
 typedef struct {
   int kind;
@@ -96,6 +100,12 @@ typedef struct {
   int autotune;          /* 1 (default): the first kt_step times the candidate tile shapes and grid
                             sizes (side-effect-free first-stage launches) and keeps the fastest;
                             0: 32 x 4 x 2 tiles on a persistent grid */
+  int iface;             /* velocities v^+- at the cell faces (Sec. 3.1).  KT_IFACE_RECON (default):
+                            u^mu extrapolated to the faces with the same generalised minmod as q.
+                            KT_IFACE_INVERT: the extrapolated conserved states q^+- themselves are
+                            inverted (Eq. eInferred), 12 root-finds per cell and stage, each started
+                            from the e of the cell the state was extrapolated from; a state with no
+                            root gets v = 0.  FP64 root-finds in KT_FP64, FP32 in KT_MIXED. */
 } kt_options;
 
 /* Learned inversion start: an MLP 6 -> 32 -> 32 -> 1 with ReLU; weights row-major

@@ -57,6 +57,7 @@ def lib():
         L.ko_free.argtypes = [C.c_void_p]
         L.ko_set_state.argtypes = [C.c_void_p, C.c_double, dp, dp, dp, dp, dp]
         L.ko_set_state_q.argtypes = [C.c_void_p, C.c_double, dp, dp, dp, dp]
+        L.ko_coefficients.argtypes = [C.c_void_p, C.c_double, dp]
         L.ko_step.argtypes = [C.c_void_p, C.c_int]
         L.ko_get_state.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp]
         L.ko_rhs.argtypes = [C.c_void_p, dp]
@@ -79,7 +80,7 @@ def _ptr(a):
 
 
 def _kind(k):
-    return {"const": 0, "gauss": 1}[k]
+    return {"const": 0, "gauss": 1, "paper": 2}[k]
 
 
 class Oracle:
@@ -156,6 +157,12 @@ class Oracle:
         out = np.empty((15, self.prob.ncells))
         lib().ko_rhs(self.ctx, _ptr(out))
         return out
+
+    def coefficients(self, T):
+        """(eta/s, zeta/s) at temperature T (fm^-1)."""
+        out = np.empty(2)
+        lib().ko_coefficients(self.ctx, float(T), _ptr(out))
+        return out[0], out[1]
 
     # single-formula entry points
     def eos(self, e):

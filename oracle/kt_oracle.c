@@ -132,16 +132,32 @@ typedef struct {
   double lam_Pipi;       /* lambda_{Pi pi}/tau_Pi = 8/5 (1/3 - cs2) */
 } transport_t;
 
+/* zeta/s of Sec. 2.2, Eq. (zetas), as a function of x = T/T_c: a quadratic around T_c joined to
+ * two exponential tails; the printed domain of the quadratic, "0.995 T_c >= T >= 1.05 T_c", is read
+ * as 0.995 T_c <= T <= 1.05 T_c (the other two branches cover T > 1.05 T_c and T < 0.995 T_c) */
+static double zeta_over_s_paper(double x) {
+  if (x > 1.05) return 0.9 * exp(-(x - 1.0) / 0.025) + 0.25 * exp(-(x - 1.0) / 0.13) + 0.001;
+  if (x < 0.995) return 0.9 * exp((x - 1.0) / 0.0025) + 0.22 * exp((x - 1.0) / 0.022) + 0.03;
+  return -13.45 + 27.55 * x - 13.77 * x * x;
+}
+
 static double coef_value(int kind, const double* cc, double T) {
   if (kind == KO_COEF_CONST) return cc[0];
+  if (kind == KO_COEF_PAPER_ZETA) return cc[0] * zeta_over_s_paper(T / cc[1]);
   double x = (T - cc[1]) / cc[2];
   return cc[0] * exp(-x * x);
 }
 
 static double coef_log(int kind, const double* cc, double T) {
   if (kind == KO_COEF_CONST) return log(cc[0]);
+  if (kind == KO_COEF_PAPER_ZETA) return log(coef_value(kind, cc, T));
   double x = (T - cc[1]) / cc[2];
   return log(cc[0]) - x * x;
+}
+
+void ko_coefficients(const ko_ctx* c, double T, double* out) {
+  out[0] = coef_value(c->P.eta_kind, c->P.eta_c, T);
+  out[1] = coef_value(c->P.zeta_kind, c->P.zeta_c, T);
 }
 
 static void transport(const ko_ctx* c, double e, double P0, double T, double lnd, transport_t* tr) {

@@ -19,7 +19,7 @@ extern "C" {
 enum { KO_MILNE = 0, KO_CARTESIAN = 1 };
 enum { KO_BC_COPY = 0, KO_BC_PERIODIC = 1 };
 enum { KO_EOS_CONFORMAL = 0, KO_EOS_TABLE = 1 };
-enum { KO_COEF_CONST = 0, KO_COEF_GAUSS = 1 };
+enum { KO_COEF_CONST = 0, KO_COEF_GAUSS = 1, KO_COEF_PAPER_ZETA = 2 };
 enum { KO_IFACE_RECON = 0, KO_IFACE_INVERT = 1 };
 
 /* status bits OR-ed over all cells of a step */
@@ -36,7 +36,7 @@ typedef struct {
   int eos_n;                 /* table: nodes uniform in ln e */
   const double *eos_e, *eos_p, *eos_cs2, *eos_T, *eos_lndelta; /* lndelta = ln(1/3 - cs2) */
   int eta_kind;  double eta_c[3];   /* eta/s(T): c0 or c0*exp(-((T-c1)/c2)^2), T in fm^-1 */
-  int zeta_kind; double zeta_c[3];  /* zeta/s(T), same forms */
+  int zeta_kind; double zeta_c[3];  /* zeta/s(T), same forms, or c0 times Eq. (zetas) with T_c = c1 */
   int tau_pipi_on;           /* 1: tau_pipi/tau_pi = 10/7; 0: tau_pipi = 0 */
   int regulate;              /* 1: apply Eq. (regPimunu) after each inversion */
   double rho_max, xi0;
@@ -65,6 +65,8 @@ int ko_get_state(const ko_ctx* c, double* tau, double* e, double* u, double* pi,
 /* C[q] of Eq. (semiDiscreteKT) for the current state at the current tau (no update). */
 int ko_rhs(ko_ctx* c, double* out /* [15][cells] */);
 int ko_set_threads(int n);
+/* eta/s and zeta/s at temperature T (fm^-1): out[0] = eta/s, out[1] = zeta/s */
+void ko_coefficients(const ko_ctx* c, double T, double* out);
 
 /* ---- single-formula entry points used by the oracle's own pin tests ---- */
 double ko_minmod3(double x, double y, double z);

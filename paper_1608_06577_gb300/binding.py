@@ -46,7 +46,8 @@ class Options(C.Structure):
                 ("inversion", C.c_int), ("tau_pipi_on", C.c_int), ("regulate", C.c_int), ("rho_max", C.c_double),
                 ("xi0", C.c_double), ("e_min", C.c_double), ("tau_relax_min", C.c_double),
                 ("stream", C.c_void_p), ("arena", C.c_void_p), ("arena_bytes", C.c_size_t),
-                ("mlp_weights", C.POINTER(C.c_float)), ("use_graph", C.c_int), ("autotune", C.c_int)]
+                ("mlp_weights", C.POINTER(C.c_float)), ("use_graph", C.c_int), ("autotune", C.c_int),
+                ("iface", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -96,7 +97,7 @@ def _dptr(a):
 
 
 def _coef(t):
-    kind = {"const": 0, "gauss": 1}[t[0]]
+    kind = {"const": 0, "gauss": 1, "paper": 2}[t[0]]
     return Coef(kind, float(t[1]), float(t[2]), float(t[3]))
 
 
@@ -126,6 +127,7 @@ class KT:
         o.inversion = inversion
         o.tau_pipi_on = int(bool(prob.tau_pipi_on))
         o.regulate = int(bool(prob.regulate))
+        o.iface = 1 if getattr(prob, "iface", "recon") == "invert" else 0
         o.rho_max, o.xi0 = prob.rho_max, prob.xi0
         o.e_min, o.tau_relax_min = prob.e_min, prob.tau_relax_min
         o.use_graph = int(bool(use_graph))

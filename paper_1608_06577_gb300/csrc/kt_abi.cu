@@ -194,8 +194,9 @@ void fill_pr(PR<R>& o, const Params& P) {
   o.xi0_rho_max = (R)(P.xi0 * P.rho_max);
   o.eos_a = (R)P.eos_a;
   o.eta_c0 = (R)P.eta.c0; o.eta_c1 = (R)P.eta.c1; o.eta_inv_c2 = (R)(1.0 / P.eta.c2); o.eta_ln_c0 = (R)P.eta.ln_c0;
+  o.eta_inv_c1 = (R)(1.0 / P.eta.c1);
   o.zeta_c0 = (R)P.zeta.c0; o.zeta_c1 = (R)P.zeta.c1; o.zeta_inv_c2 = (R)(1.0 / P.zeta.c2);
-  o.zeta_ln_c0 = (R)P.zeta.ln_c0;
+  o.zeta_ln_c0 = (R)P.zeta.ln_c0; o.zeta_inv_c1 = (R)(1.0 / P.zeta.c1);
 }
 
 // Per-interval cubic coefficients of the table EOS (see kt_eos in kt.h).
@@ -392,11 +393,15 @@ template <int STAGE>
 void launch_stage(Ctx* c, const StageIO<double>& io) {
   const Shape& s = kShapes[c->shape];
   const dim3 blk(s.x, s.y, s.z);
-  if (c->P.theta == 1.0)
-    stage_kernel<double, STAGE, true><<<c->grid_blocks, blk, 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles, c->ntiles);
+  const bool t1 = (c->P.theta == 1.0), inv = c->P.iface_invert;
+  if (t1 && !inv)
+    stage_kernel<double, STAGE, true, false><<<c->grid_blocks, blk, 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles, c->ntiles);
+  else if (!inv)
+    stage_kernel<double, STAGE, false, false><<<c->grid_blocks, blk, 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles, c->ntiles);
+  else if (t1)
+    stage_kernel<double, STAGE, true, true><<<c->grid_blocks, blk, 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles, c->ntiles);
   else
-    stage_kernel<double, STAGE, false><<<c->grid_blocks, blk, 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles,
-                                                                             c->ntiles);
+    stage_kernel<double, STAGE, false, true><<<c->grid_blocks, blk, 0, c->stream>>>(c->P, io, c->d_lat, c->d_tiles, c->ntiles);
 }
 
 // the right-hand-side kernel of a stage, with the minmod specialised when theta = 1
@@ -405,12 +410,16 @@ void launch_rhs(Ctx* c, const StageIO<float>& io) {
   const Shape& s = kShapes[c->shape];
   const dim3 blk(s.x, s.y, s.z);
   const CUtensorMap* maps = c->d_tmaps + (STAGE == 1 ? 0 : c->nev);
-  if (c->P.theta == 1.0)
-    rhs_kernel<STAGE, true><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k_buf(c, STAGE), c->d_lat, c->d_tiles,
-                                                               c->ntiles, maps);
+  float* k = k_buf(c, STAGE);
+  const bool t1 = (c->P.theta == 1.0), inv = c->P.iface_invert;
+  if (t1 && !inv)
+    rhs_kernel<STAGE, true, false><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
+  else if (!inv)
+    rhs_kernel<STAGE, false, false><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
+  else if (t1)
+    rhs_kernel<STAGE, true, true><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
   else
-    rhs_kernel<STAGE, false><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k_buf(c, STAGE), c->d_lat, c->d_tiles,
-                                                                c->ntiles, maps);
+    rhs_kernel<STAGE, false, true><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
 }
 
 template <int STAGE, bool LEARNED>
@@ -531,14 +540,12 @@ int select_shape(Ctx* c, int cand) {
   const Shape& sh = kShapes[shape];
   auto grid = [&](int cap) { return one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles)); };
   if (c->mixed) {
-    c->grid_rhs = grid(c->P.theta == 1.0 ? occupancy_blocks(rhs_kernel<1, true>, sh)
-                                         : occupancy_blocks(rhs_kernel<1, false>, sh));
+    c->grid_rhs = grid(occupancy_blocks(rhs_kernel<1, true, false>, sh));  // the same register cap for all
     c->grid_upd = grid(c->learned ? occupancy_blocks(update_kernel<1, true>, sh)
                                   : occupancy_blocks(update_kernel<1, false>, sh));
     c->grid_blocks = c->grid_rhs;
   } else {
-    c->grid_blocks = grid(c->P.theta == 1.0 ? occupancy_blocks(stage_kernel<double, 1, true>, sh)
-                                            : occupancy_blocks(stage_kernel<double, 1, false>, sh));
+    c->grid_blocks = grid(occupancy_blocks(stage_kernel<double, 1, true, false>, sh));  // same launch bounds
   }
   c->cand = cand;
   for (int p = 0; p < 3; ++p)
@@ -635,6 +642,7 @@ int kt_options_default(kt_options* o) {
   o->tau_relax_min = 0.0;
   o->use_graph = 1;
   o->autotune = 1;
+  o->iface = KT_IFACE_RECON;
   return KT_OK;
 }
 
@@ -690,6 +698,12 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   P.periodic = (o.bc == KT_BC_PERIODIC);
   coef_from(P.eta, eta_over_s);
   coef_from(P.zeta, zeta_over_s);
+  for (const Coef* k : {&P.eta, &P.zeta}) {
+    const bool ok = (k->kind == KT_COEF_CONST && k->c0 >= 0.0) ||
+                    (k->kind == KT_COEF_GAUSS && k->c0 >= 0.0 && k->c2 > 0.0) ||
+                    (k->kind == KT_COEF_PAPER_ZETA && k->c0 >= 0.0 && k->c1 > 0.0);
+    if (!ok) return bail(KT_ERR_ARG);
+  }
   P.eos_table = (eos->kind == KT_EOS_TABLE);
   P.eos_a = eos->a;
   if (eos->kind == KT_EOS_TABLE) {
@@ -709,6 +723,8 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   P.bulk_on = !(P.zeta.kind == KT_COEF_CONST && P.zeta.c0 == 0.0) && P.eos_table;
   P.tpp = o.tau_pipi_on ? 10.0 / 7.0 : 0.0;
   P.regulate = o.regulate;
+  if (o.iface != KT_IFACE_RECON && o.iface != KT_IFACE_INVERT) return bail(KT_ERR_ARG);
+  P.iface_invert = (o.iface == KT_IFACE_INVERT);
   P.rho_max = o.rho_max;
   P.xi0 = o.xi0;
   P.e_min = o.e_min;

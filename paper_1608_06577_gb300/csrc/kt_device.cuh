@@ -69,8 +69,8 @@ struct PR {
   R tpp;               // tau_pipi/tau_pi
   R rho_max, xi0_rho_max;
   R eos_a;
-  R eta_c0, eta_c1, eta_inv_c2, eta_ln_c0;
-  R zeta_c0, zeta_c1, zeta_inv_c2, zeta_ln_c0;
+  R eta_c0, eta_c1, eta_inv_c2, eta_ln_c0, eta_inv_c1;
+  R zeta_c0, zeta_c1, zeta_inv_c2, zeta_ln_c0, zeta_inv_c1;
 };
 
 struct Params {
@@ -88,6 +88,7 @@ struct Params {
   int shear_on, bulk_on;
   double tpp;         // tau_pipi / tau_pi (10/7 or 0)
   int regulate;
+  int iface_invert;   // face velocities from root-finds of the extrapolated states (KT_IFACE_INVERT)
   double rho_max, xi0;
   double e_min;
   double rate_max;    // 1 / tau_relax_min (or +inf)
@@ -198,11 +199,21 @@ __device__ __forceinline__ float sexp(float x) { return __expf(x); }
 __device__ __forceinline__ double slog(double x) { return log(x); }
 __device__ __forceinline__ float slog(float x) { return __logf(x); }
 
-// eta/s(T) and ln(zeta/s)(T): const c0 or c0 exp(-((T - c1)/c2)^2)
+// zeta/s of Sec. 2.2, Eq. (zetas), at x = T/T_c (the quadratic on 0.995 <= x <= 1.05)
+template <typename R>
+__device__ __forceinline__ R zeta_over_s_paper(R x) {
+  const R y = x - R(1);
+  if (x > R(1.05)) return R(0.9) * sexp(-y * R(1.0 / 0.025)) + R(0.25) * sexp(-y * R(1.0 / 0.13)) + R(0.001);
+  if (x < R(0.995)) return R(0.9) * sexp(y * R(1.0 / 0.0025)) + R(0.22) * sexp(y * R(1.0 / 0.022)) + R(0.03);
+  return R(-13.45) + R(27.55) * x - R(13.77) * x * x;
+}
+
+// eta/s(T) and ln(zeta/s)(T): const c0, c0 exp(-((T - c1)/c2)^2), or c0 times Eq. (zetas)
 template <typename R>
 __device__ __forceinline__ R eta_over_s(const Params& P, R T) {
   const PR<R>& p = pr<R>(P);
   if (P.eta.kind == 0) return p.eta_c0;
+  if (P.eta.kind == 2) return p.eta_c0 * zeta_over_s_paper<R>(T * p.eta_inv_c1);
   R x = (T - p.eta_c1) * p.eta_inv_c2;
   return p.eta_c0 * sexp(-x * x);
 }
@@ -211,6 +222,7 @@ template <typename R>
 __device__ __forceinline__ R ln_zeta_over_s(const Params& P, R T) {
   const PR<R>& p = pr<R>(P);
   if (P.zeta.kind == 0) return p.zeta_ln_c0;
+  if (P.zeta.kind == 2) return slog(p.zeta_c0 * zeta_over_s_paper<R>(T * p.zeta_inv_c1));
   R x = (T - p.zeta_c1) * p.zeta_inv_c2;
   return p.zeta_ln_c0 - x * x;
 }

@@ -47,7 +47,7 @@ constexpr unsigned kWaitPolls = 1u << 20;   // mbarrier polls before a wait give
 
 // Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM, 64 (update) 32 warps;
 // both measured faster than the occupancy the compiler picks unconstrained.
-template <int STAGE, bool TH1>
+template <int STAGE, bool TH1, bool IFACE>
 __global__ void __maxnreg__(96)
     rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
                const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ tmaps) {
@@ -96,7 +96,7 @@ __global__ void __maxnreg__(96)
     const long long c = valid ? L.idx(i + 2, j + 2, k + 2) : 0;
     float dq[NQ], du[4][4], dv = 0.f;
     Faces<float> Fx, Fy, Fz;
-    if (valid) cell_faces<float, TH1>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+    if (valid) cell_faces<float, TH1, IFACE>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
 
 #pragma unroll  // unrolled: the component index, the rows it feeds and every branch become constants
     for (int n = 0; n < NQ; ++n) {

@@ -53,11 +53,88 @@ struct Faces {
   int s;                 // element stride of direction d
 };
 
+// Root-find of one extrapolated face state (KT_IFACE_INVERT): f(e) = e - E + M^2/A = 0 with
+// A = E + P0(e) + Pi, safeguarded Newton in the stencil precision inside [e_min, E] from `guess`;
+// returns A at the root (v^d = M^d / A), or false if the state has none (E <= 0, M^2 >= E^2, no
+// convergence in 100 steps).  FP64: stop at |de| <= 2^-50 E as the cell root-find; FP32: 2^-21 E.
+template <typename R>
+__device__ __forceinline__ bool face_root(const Params& P, R E, R M2, R Pi, R guess, R& A) {
+  if (!(E > R(0)) || !(M2 < E * E) || !isfinite(E) || !isfinite(M2)) return false;
+  if (!P.eos_table && (!P.bulk_on || Pi == R(0))) {
+    const R M = sqrt(M2);  // conformal closed form, cancellation-free
+    const R e = R(3) * (E - M) * (E + M) / (sqrt(fma(R(4) * E, E, R(-3) * M2)) + E);
+    A = E + e * R(1.0 / 3.0) + Pi;
+    return true;
+  }
+  R lo = (P.e_min > 0.0) ? R(P.e_min) : R(sizeof(R) == 8 ? 1e-300 : 1e-30), hi = E;
+  R e = (guess >= lo && guess <= hi) ? guess : hi;
+  const R stop = E * R(sizeof(R) == 8 ? 0x1p-50 : 0x1p-21);
+  for (int it = 0; it < 100; ++it) {
+    R p0, c2;
+    eos_P_cs2<R>(P, e, p0, c2);
+    A = E + p0 + Pi;
+    const R f = e - E + M2 / A;
+    if (f == R(0)) return true;
+    if (f < R(0)) lo = e; else hi = e;
+    R en = e - f / (R(1) - M2 * c2 / (A * A));
+    if (!(en >= lo && en <= hi)) en = R(0.5) * (lo + hi);
+    const R de = fabs(en - e);
+    e = en;
+    if (de <= stop) {
+      if (e < R(P.e_min)) e = R(P.e_min);
+      A = E + eos_P<R>(P, e) + Pi;
+      return true;
+    }
+  }
+  return false;
+}
+
+// KT_IFACE_INVERT (literal reading of Sec. 3.1): the four extrapolated states along D -- left face
+// m (from cell i-1) and p (from cell i), right face m (from cell i) and p (from cell i+1) -- of the
+// components the root-find reads (T^{tau mu}, pi^{tau mu}, Pi), each inverted from the e of the cell
+// it was extrapolated from; v^d = M^d / (E + P0 + Pi) at the root, 0 for a state without one.
+template <typename R, int D, bool TH1>
+__device__ __forceinline__ void face_velocities_inverted(const Params& P, const Lattice& L, const StageIO<R>& io,
+                                                         long long c, int s, R th, R gnn, R& vLm, R& vLp, R& vRm,
+                                                         R& vRp) {
+  const long long fs = L.fstride;
+  const R h = R(0.5);
+  R E4[4] = {R(0), R(0), R(0), R(0)}, M4[3][4] = {}, Pi4[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int n = (k < 8) ? k : 14;
+    const R* p = io.qr_in + n * fs;
+    const R a2 = ld<R>(p, c - 2 * s), a1 = ld<R>(p, c - s), a0 = ld<R>(p, c), b1 = ld<R>(p, c + s),
+            b2 = ld<R>(p, c + 2 * s);
+    const R d0 = a1 - a2, d1 = a0 - a1, d2 = b1 - a0, d3 = b2 - b1;
+    const R sm = limited_slope_d<R, TH1>(d0, d1, th), s0 = limited_slope_d<R, TH1>(d1, d2, th),
+            sp = limited_slope_d<R, TH1>(d2, d3, th);
+    const R x[4] = {fma(h, sm, a1), fma(-h, s0, a0), fma(h, s0, a0), fma(-h, sp, b1)};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (n == 0) E4[j] += x[j];
+      else if (n == 4) E4[j] -= x[j];
+      else if (n < 4) M4[n - 1][j] += x[j];
+      else if (n < 8) M4[n - 5][j] -= x[j];
+      else Pi4[j] = x[j];
+    }
+  }
+  const R g[4] = {ld<R>(io.e_in, c - s), ld<R>(io.e_in, c), ld<R>(io.e_in, c), ld<R>(io.e_in, c + s)};
+  R v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const R M2 = fma(M4[0][j], M4[0][j], fma(M4[1][j], M4[1][j], gnn * M4[2][j] * M4[2][j]));
+    R A;
+    v[j] = face_root<R>(P, E4[j], M2, Pi4[j], g[j], A) ? M4[D][j] / A : R(0);
+  }
+  vLm = v[0]; vLp = v[1]; vRm = v[2]; vRp = v[3];
+}
+
 // Velocity part of direction D: limited face states of u^tau and u^d and their ratio v^d
 // (Sec. 3.1), the local speeds a = max(|v^p|, |v^m|) (Eq. ax), the central differences
 // d_d u^mu and d_d v^d, and the pressure part of S_c (App. B):
 // -d_d (v^d P delta^nu_tau - g^{d nu} P), P = P0 + Pi.
-template <typename R, int D, bool TH1 = false>
+template <typename R, int D, bool TH1 = false, bool IFACE = false>
 __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                            R inv_gnn, R sfac, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax,
                                            Faces<R>& F) {
@@ -74,20 +151,25 @@ __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, co
     um1[m] = ld<R>(u + m * fs, c - s);
     up1[m] = ld<R>(u + m * fs, c + s);
   }
-  const R u0t = ld<R>(u, c), u0d = ld<R>(u + (D + 1) * fs, c);
-  const R um2t = ld<R>(u, c - 2 * s), um2d = ld<R>(u + (D + 1) * fs, c - 2 * s);
-  const R up2t = ld<R>(u, c + 2 * s), up2d = ld<R>(u + (D + 1) * fs, c + 2 * s);
-  R t0 = um1[0] - um2t, t1 = u0t - um1[0], t2 = up1[0] - u0t, t3 = up2t - up1[0];
-  R d0 = um1[D + 1] - um2d, d1 = u0d - um1[D + 1], d2 = up1[D + 1] - u0d, d3 = up2d - up1[D + 1];
-  const R st_m = limited_slope_d<R, TH1>(t0, t1, th), st_0 = limited_slope_d<R, TH1>(t1, t2, th),
-          st_p = limited_slope_d<R, TH1>(t2, t3, th);
-  const R sd_m = limited_slope_d<R, TH1>(d0, d1, th), sd_0 = limited_slope_d<R, TH1>(d1, d2, th),
-          sd_p = limited_slope_d<R, TH1>(d2, d3, th);
-  const R h = R(0.5);
-  const R vLm = sdiv(fma(h, sd_m, um1[D + 1]), fma(h, st_m, um1[0]));
-  const R vLp = sdiv(fma(-h, sd_0, u0d), fma(-h, st_0, u0t));
-  const R vRm = sdiv(fma(h, sd_0, u0d), fma(h, st_0, u0t));
-  const R vRp = sdiv(fma(-h, sd_p, up1[D + 1]), fma(-h, st_p, up1[0]));
+  R vLm, vLp, vRm, vRp;
+  if constexpr (IFACE) {
+    face_velocities_inverted<R, D, TH1>(P, L, io, c, s, th, sfac * sfac, vLm, vLp, vRm, vRp);
+  } else {
+    const R u0t = ld<R>(u, c), u0d = ld<R>(u + (D + 1) * fs, c);
+    const R um2t = ld<R>(u, c - 2 * s), um2d = ld<R>(u + (D + 1) * fs, c - 2 * s);
+    const R up2t = ld<R>(u, c + 2 * s), up2d = ld<R>(u + (D + 1) * fs, c + 2 * s);
+    R t0 = um1[0] - um2t, t1 = u0t - um1[0], t2 = up1[0] - u0t, t3 = up2t - up1[0];
+    R d0 = um1[D + 1] - um2d, d1 = u0d - um1[D + 1], d2 = up1[D + 1] - u0d, d3 = up2d - up1[D + 1];
+    const R st_m = limited_slope_d<R, TH1>(t0, t1, th), st_0 = limited_slope_d<R, TH1>(t1, t2, th),
+            st_p = limited_slope_d<R, TH1>(t2, t3, th);
+    const R sd_m = limited_slope_d<R, TH1>(d0, d1, th), sd_0 = limited_slope_d<R, TH1>(d1, d2, th),
+            sd_p = limited_slope_d<R, TH1>(d2, d3, th);
+    const R h = R(0.5);
+    vLm = sdiv(fma(h, sd_m, um1[D + 1]), fma(h, st_m, um1[0]));
+    vLp = sdiv(fma(-h, sd_0, u0d), fma(-h, st_0, u0t));
+    vRm = sdiv(fma(h, sd_0, u0d), fma(h, st_0, u0t));
+    vRp = sdiv(fma(-h, sd_p, up1[D + 1]), fma(-h, st_p, up1[0]));
+  }
   const R aL = fmax(fabs(vLp), fabs(vLm));
   const R aR = fmax(fabs(vRp), fabs(vRm));
   amax = fmaxf(amax, (float)((D == 2) ? aR * sfac : aR));
@@ -356,7 +438,7 @@ __device__ __forceinline__ CellGeom<R> cell_geom(const Params& P, double tau_src
   return g;
 }
 
-template <typename R, bool TH1 = false>
+template <typename R, bool TH1 = false, bool IFACE = false>
 __device__ __forceinline__ void cell_faces(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                            const CellGeom<R>& G, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax,
                                            Faces<R>& Fx, Faces<R>& Fy, Faces<R>& Fz) {
@@ -364,23 +446,23 @@ __device__ __forceinline__ void cell_faces(const Params& P, const Lattice& L, co
   for (int n = 0; n < NQ; ++n) dq[n] = R(0);
   dv = R(0);
   const R sfac = P.milne ? G.tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
-  face_setup<R, 0, TH1>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fx);
-  face_setup<R, 1, TH1>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fy);
-  face_setup<R, 2, TH1>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fz);
+  face_setup<R, 0, TH1, IFACE>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fx);
+  face_setup<R, 1, TH1, IFACE>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fy);
+  face_setup<R, 2, TH1, IFACE>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fz);
 }
 
 template <typename R>
 __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                              const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ]);
 
-template <typename R, bool TH1 = false>
+template <typename R, bool TH1 = false, bool IFACE = false>
 __device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                          double tau_src, R (&dq)[NQ], float& amax) {
   const CellGeom<R> G = cell_geom<R>(P, tau_src);
   R du[4][4];
   R dv;
   Faces<R> Fx, Fy, Fz;
-  cell_faces<R, TH1>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+  cell_faces<R, TH1, IFACE>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
   conserved_fluxes<R, TH1>(P, L, io, c, Fx, Fy, Fz, dq);
   cell_sources<R>(P, L, io, c, G, du, dv, dq);
 }
@@ -539,7 +621,7 @@ __device__ __forceinline__ double learned_start(const Params& P, double gnn, con
 // ---------------------------------------------------------------- one cell of a tile (FP64)
 // The whole stage for one cell in one thread; cells past the edge of the event (valid = false)
 // compute nothing and store nothing.
-template <typename R, int STAGE, bool TH1>
+template <typename R, int STAGE, bool TH1, bool IFACE>
 __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, const StageIO<R>& io, int i, int j,
                                            int k, unsigned& st, unsigned& nit, unsigned& nreg, float& amax) {
   static_assert(sizeof(R) == 8, "the fused stage is the FP64 path; mixed precision uses kt_split.cuh");
@@ -555,7 +637,7 @@ __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, co
 
   if (valid) {
     R dq[NQ];
-    cell_rhs<R, TH1>(P, L, io, c, tau_src, dq, amax);
+    cell_rhs<R, TH1, IFACE>(P, L, io, c, tau_src, dq, amax);
 
     // ---- c) Heun update in FP64 (Eqs. step1-finalStep)
 #pragma unroll
@@ -657,7 +739,7 @@ __device__ __forceinline__ void block_stats(unsigned* status, unsigned* max_spee
 // ---------------------------------------------------------------- the stage kernel
 // Persistent: every block walks its run of the tile table; a tile is one block-shaped patch of one
 // event, so one launch per Runge-Kutta stage advances every event of the context.
-template <typename R, int STAGE, bool TH1>
+template <typename R, int STAGE, bool TH1, bool IFACE>
 __global__ void __launch_bounds__(256, 1)
     stage_kernel(const Params P, const StageIO<R> io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
                  int ntiles) {
@@ -668,7 +750,7 @@ __global__ void __launch_bounds__(256, 1)
   for (int t = t0; t < t1; ++t) {
     const Tile tl = tiles[t];
     const Lattice L = lats[tl.event];
-    stage_cell<R, STAGE, TH1>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z, st,
+    stage_cell<R, STAGE, TH1, IFACE>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z, st,
                          nit, nreg, amax);
   }
 

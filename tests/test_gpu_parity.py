@@ -187,3 +187,55 @@ def test_mixed_mode_error_after_100_steps(baseline_eos):
     print("mixed mode after 100 steps: max rel err e", rel_e, {k: f"{v:.2e}" for k, v in errs.items()})
     assert rel_e < 1e-4
     assert errs["e[0]"] < 1e-4 and errs["q[0]"] < 1e-4
+
+
+@pytest.mark.parametrize("shape", [(20, 18, 10), (33, 9, 7)])
+def test_face_inversion_fp64_parity(shape, baseline_eos):
+    """KT_IFACE_INVERT (face velocities from root-finds of the extrapolated states, the literal
+    reading of Sec. 3.1) against the oracle with the same option: 1e-12 per field after 10 steps."""
+    from dataclasses import replace
+    nx, ny, nz = shape
+    p = replace(hotspot_problem(nx=nx, ny=ny, neta=nz, nhot=6, seed=9, r_max=1.0, eos_table=baseline_eos),
+                iface="invert")
+    g, r, _ = run_pair(p, 10)
+    assert_parity(g, r)
+
+
+def test_face_inversion_mixed_error(baseline_eos):
+    """Mixed precision with FP32 face root-finds against the FP64 oracle (same option): pointwise
+    relative error in e <= 1e-4 after 40 steps; and the option changes the result (it is not the
+    default reconstruction)."""
+    from dataclasses import replace
+    p = replace(hotspot_problem(nx=28, ny=24, neta=12, nhot=8, seed=6, r_max=1.0, eos_table=baseline_eos),
+                iface="invert")
+    g, r, _ = run_pair(p, 40, precision=1)
+    rel_e = np.max(np.abs(g["e"] / r["e"] - 1))
+    print("face inversion, mixed, 40 steps: max rel err e", rel_e)
+    assert rel_e < 1e-4
+    g2, _, _ = run_pair(replace(p, iface="recon"), 40, precision=1)
+    assert np.max(np.abs(g2["e"] / g["e"] - 1)) > 1e-8
+
+
+def test_lattice_eos_and_paper_zeta_fp64_parity():
+    """The lattice EOS of Sec. 2.3 with zeta/s of Eq. (zetas) (T_c = 200 MeV): hotspots and the
+    nonconformal Bjorken setup of Sec. 5.5, FP64 against the oracle to 1e-12 per field."""
+    from workload.eos import lattice_table
+    p = hotspot_problem(nx=22, ny=20, neta=8, nhot=6, seed=8, r_max=1.0, eta_over_s=0.2, zeta="paper",
+                        eos_table=lattice_table())
+    g, r, _ = run_pair(p, 10)
+    assert_parity(g, r)
+    b = bjorken_problem(T0_gev=0.6, tau0=0.25, dtau=0.004, nsteps=10, eos="lattice", zeta="paper", eta_over_s=0.2)
+    g, r, _ = run_pair(b, 10)
+    assert_parity(g, r)
+    assert r["Pi"][0] > 0
+
+
+def test_lattice_eos_mixed_error():
+    """The same hotspots in mixed precision: pointwise relative error in e <= 1e-4 after 40 steps."""
+    from workload.eos import lattice_table
+    p = hotspot_problem(nx=22, ny=20, neta=8, nhot=6, seed=8, r_max=1.0, eta_over_s=0.2, zeta="paper",
+                        eos_table=lattice_table())
+    g, r, _ = run_pair(p, 40, precision=1)
+    rel_e = np.max(np.abs(g["e"] / r["e"] - 1))
+    print("lattice EOS, mixed, 40 steps: max rel err e", rel_e)
+    assert rel_e < 1e-4

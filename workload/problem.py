@@ -120,10 +120,11 @@ def hotspot_problem(nx=128, ny=128, neta=128, dx=0.1, deta=0.1, tau0=0.5, dtau=0
                     e_floor_gev=1e-4, eos_table=None) -> Problem:
     """The 128^3 nonconformal viscous workload: tabulated EOS with c_s^2(T) = 1/3 - 0.2
     exp(-((T-0.17)/0.05)^2), eta/s = 0.08, zeta/s = 0.1 exp(-((T-0.17)/0.03)^2), hotspot e,
-    u at rest, pi = Pi = 0."""
+    u at rest, pi = Pi = 0.  zeta: True / "gauss" (that zeta/s), "paper" (Eq. zetas) or False;
+    eos_table: another table (e.g. the lattice EOS of Sec. 2.3)."""
     from .eos import baseline_table
     tab = eos_table if eos_table is not None else baseline_table()
-    zs = ("gauss", 0.1, 0.17 / HBARC, 0.03 / HBARC) if zeta else ("const", 0.0, 0.0, 1.0)
+    zs = zeta_coef(zeta)
     p = Problem(name=f"hotspots_{nx}x{ny}x{neta}_s{seed}", nx=nx, ny=ny, neta=neta, dx=dx, dy=dx,
                 deta=deta, dtau=dtau, tau0=tau0, nsteps=nsteps, coords="milne", bc="copy",
                 theta=theta, eos=tab, eta_over_s=("const", eta_over_s, 0.0, 1.0), zeta_over_s=zs,
@@ -178,15 +179,31 @@ def cylinder_problem(n=60, dx=0.2, dt=None, t_end=1.0, R=1.0, e_in_gev=0.0246, e
 
 
 # ----------------------------------------------------------------------------------- Bjorken
+ZETA_PAPER_TC_GEV = 0.2  # T_c of the zeta/s parametrisation of Sec. 2.2 (Eq. zetas)
+
+
+def zeta_coef(kind):
+    """zeta/s inputs: "gauss" = 0.1 exp(-((T - 0.17 GeV)/0.03 GeV)^2) (the 128^3 workload),
+    "paper" = Eq. (zetas) with T_c = 200 MeV and normalisation 1, None/False = off."""
+    if kind in (True, "gauss"):
+        return ("gauss", 0.1, 0.17 / HBARC, 0.03 / HBARC)
+    if kind == "paper":
+        return ("paper", 1.0, ZETA_PAPER_TC_GEV / HBARC, 1.0)
+    return ("const", 0.0, 0.0, 1.0)
+
+
 def bjorken_problem(T0_gev=0.6, tau0=0.25, dtau=0.005, nsteps=100, eta_over_s=0.2, eos="conformal",
                     zeta=False, n=4, pi_ns=True, tau_pipi_on=True) -> Problem:
-    """Transversely homogeneous, boost-invariant flow (Secs. 5.4-5.5) on a small uniform grid."""
-    from .eos import A_SB, baseline_table
+    """Transversely homogeneous, boost-invariant flow (Secs. 5.4-5.5) on a small uniform grid.
+    eos: "conformal", "table" (the 128^3 workload's c_s^2(T)) or "lattice" (Sec. 2.3)."""
+    from .eos import A_SB, baseline_table, lattice_table
     if eos == "conformal":
         eosv = conformal_eos()
+    elif eos == "lattice":
+        eosv = lattice_table()
     else:
         eosv = baseline_table()
-    zs = ("gauss", 0.1, 0.17 / HBARC, 0.03 / HBARC) if zeta else ("const", 0.0, 0.0, 1.0)
+    zs = zeta_coef(zeta)
     p = Problem(name="bjorken", nx=n, ny=n, neta=n, dx=0.1, dy=0.1, deta=0.1, dtau=dtau, tau0=tau0,
                 nsteps=nsteps, coords="milne", bc="copy", theta=1.0, eos=eosv,
                 eta_over_s=("const", eta_over_s, 0.0, 1.0), zeta_over_s=zs, tau_pipi_on=tau_pipi_on,
