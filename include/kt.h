@@ -160,6 +160,22 @@ int kt_step(kt_ctx* ctx, int n_steps);
 int kt_get_state(kt_ctx* ctx, double* tau, double* e, double* u, double* pi, double* Pi, double* q,
                  int on_device);
 
+/* Validity diagnostics of Sec. 7 (Eqs. inverseReynoldsNumbers, inverseReynoldsNumbers2) at the
+ * current state of an event, out = [7][cells] (layout as kt_get_state; host pointer, or device
+ * pointer if on_device):
+ *   0  Kn_theta_pi = tau_pi theta          1  Kn_theta_Pi = tau_Pi theta
+ *   2  R_pi^-1 = sqrt(pi^{mu nu} pi_{mu nu}) / P0      3  R_Pi^-1 = |Pi| / P0
+ *   4  (R_pi^(2))^-1 = sqrt(J^{mu nu} J_{mu nu}) / (2 eta sqrt(sigma^{mu nu} sigma_{mu nu}))
+ *   5  (R_Pi^(2))^-1 = |J| / (zeta |theta|)
+ *   6  the regulation factor tanh(rho)/rho of Eq. (regPimunu) applied to pi in the last step
+ *      (1 before the first step or with the regulator off)
+ * with J^{mu nu}, J the second-order terms of Eq. (14_moment_terms) (no diffusion), the
+ * unfloored relaxation times tau_pi = 5 (eta/s)/T and tau_Pi = (zeta/s)/(15 (1/3 - c_s^2)^2 T),
+ * and the time derivative of u taken backward over the last step, as in the first stage.  A
+ * quantity whose channel is off, or whose denominator vanishes, is 0.  Computed by one extra
+ * kernel over the event (stencil precision of the context). */
+int kt_get_diagnostics(kt_ctx* ctx, int event, double* out, int on_device);
+
 int kt_get_stats(kt_ctx* ctx, kt_stats* stats);
 const char* kt_last_error(const kt_ctx* ctx);
 void kt_free(kt_ctx* ctx);

@@ -58,6 +58,7 @@ def lib():
         L.ko_set_state.argtypes = [C.c_void_p, C.c_double, dp, dp, dp, dp, dp]
         L.ko_set_state_q.argtypes = [C.c_void_p, C.c_double, dp, dp, dp, dp]
         L.ko_coefficients.argtypes = [C.c_void_p, C.c_double, dp]
+        L.ko_diagnostics.argtypes = [C.c_void_p, dp]
         L.ko_step.argtypes = [C.c_void_p, C.c_int]
         L.ko_get_state.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp]
         L.ko_rhs.argtypes = [C.c_void_p, dp]
@@ -157,6 +158,14 @@ class Oracle:
         out = np.empty((15, self.prob.ncells))
         lib().ko_rhs(self.ctx, _ptr(out))
         return out
+
+    DIAGNOSTICS = ("Kn_theta_pi", "Kn_theta_Pi", "Rinv_pi", "Rinv_Pi", "R2inv_pi", "R2inv_Pi", "regulation")
+
+    def diagnostics(self):
+        """The validity diagnostics of Sec. 7 at the current state, as a dict of [cells] arrays."""
+        out = np.empty((7, self.prob.ncells))
+        lib().ko_diagnostics(self.ctx, _ptr(out))
+        return dict(zip(self.DIAGNOSTICS, out))
 
     def coefficients(self, T):
         """(eta/s, zeta/s) at temperature T (fm^-1)."""

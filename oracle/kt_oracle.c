@@ -58,6 +58,7 @@ struct ko_ctx {
   /* u^n, u^*, u^{n-1}, u^{n+1} */
   double *u[4], *us[4], *up[4], *un[4];
   double *e, *p, *es, *ps;
+  double *reg; /* regulation factor applied to pi^{n+1} in the last step (1 before any step) */
 };
 
 /* ------------------------------------------------------------------ geometry (Sec. 2.4) */
@@ -616,7 +617,7 @@ static int for_all_cells_stage(ko_ctx* c, const fields_t* F, double* const* upre
 }
 
 /* set inferred variables, then regulate pi, then ghosts (steps 2-4 and 8 of Sec. 4.3) */
-static int infer_regulate_ghost(ko_ctx* c, double** q, double tau, double** u, double* e, double* p) {
+static int infer_regulate_ghost(ko_ctx* c, double** q, double tau, double** u, double* e, double* p, double* reg) {
   int nx = c->P.nx, ny = c->P.ny, nz = c->P.neta;
   int st_all = 0;
   geom_t g;
@@ -640,6 +641,7 @@ static int infer_regulate_ghost(ko_ctx* c, double** q, double tau, double** u, d
           double f = regulator_factor(&g, c->P.coords == KO_MILNE, tau, o[0], o[1], &o[2], pi, qc[14],
                                       c->P.rho_max, c->P.xi0);
           for (int n = 4; n < 14; ++n) q[n][idx] = f * qc[n];
+          if (reg) reg[idx] = f;
         }
       }
   for (int n = 0; n < NQ; ++n) fill_ghosts(c, q[n]);
@@ -659,14 +661,14 @@ int ko_step(ko_ctx* c, int nsteps) {
     for (int m = 0; m < 4; ++m) F.u[m] = c->u[m];
     for_all_cells_stage(c, &F, c->up, tau_n, c->qs, NULL);
     /* 2.-4. e^*, p^*, u^* from q^* at tau^{n+1}; regulate; ghosts */
-    st |= infer_regulate_ghost(c, c->qs, tau_1, c->us, c->es, c->ps);
+    st |= infer_regulate_ghost(c, c->qs, tau_1, c->us, c->es, c->ps, NULL);
     /* 5.-6. Q = (q^n + E[q^*; e^*, p^*, u^*, u^n])/2, sources at tau^{n+1} */
     fields_t S = {{0}, {0}, c->es, c->ps};
     for (int n = 0; n < NQ; ++n) S.q[n] = c->qs[n];
     for (int m = 0; m < 4; ++m) S.u[m] = c->us[m];
     for_all_cells_stage(c, &S, c->u, tau_1, c->Q, c->q);
     /* 8. e, p, u^{n+1} from Q; regulate; ghosts */
-    st |= infer_regulate_ghost(c, c->Q, tau_1, c->un, c->e, c->p);
+    st |= infer_regulate_ghost(c, c->Q, tau_1, c->un, c->e, c->p, c->reg);
     /* 7. and 9. u^{n-1} <- u^n, u^n <- u^{n+1}, q <-> Q */
     for (int m = 0; m < 4; ++m) {
       double* t = c->up[m];
@@ -698,6 +700,79 @@ int ko_rhs(ko_ctx* c, double* out) {
         cell_rhs(c, &F, c->up, c->tau, cidx(c, i, j, k), C);
         size_t o = (size_t)(i - 2) + (size_t)nx * ((size_t)(j - 2) + (size_t)ny * (size_t)(k - 2));
         for (int n = 0; n < NQ; ++n) out[(size_t)n * ncp + o] = C[n];
+      }
+  return 0;
+}
+
+/* Validity diagnostics of Sec. 7 at the current state (tau^n, with the backward time derivative
+ * u^n - u^{n-1} as in the first stage): Knudsen numbers tau_pi theta and tau_Pi theta (unfloored
+ * relaxation times), first-order inverse Reynolds numbers sqrt(pi^{mu nu} pi_{mu nu})/P0 and
+ * |Pi|/P0 (Eq. inverseReynoldsNumbers), second-order ones sqrt(J^{mu nu} J_{mu nu}) /
+ * (2 eta sqrt(sigma^{mu nu} sigma_{mu nu})) and |J| / (zeta |theta|) (Eq. inverseReynoldsNumbers2)
+ * with J^{mu nu}, J of Eq. (14_moment_terms) without diffusion, and the regulation factor of the
+ * last step.  A quantity whose channel is off (or whose denominator vanishes) is 0. */
+static void cell_diagnostics(const ko_ctx* c, const fields_t* F, double* const* uprev, double tau, size_t idx,
+                             double out[6]) {
+  geom_t g;
+  geom_at(c, tau, &g);
+  size_t str[3] = {1, (size_t)c->NX, (size_t)c->NX * (size_t)c->NY};
+  double Dd[3] = {c->P.dx, c->P.dy, c->P.deta};
+  double u[4];
+  for (int m = 0; m < 4; ++m) u[m] = F->u[m][idx];
+  double e = F->e[idx], P0 = F->p[idx], Pi = F->q[14][idx];
+  double P0x, cs2, T, lnd;
+  eos_eval(c, e, &P0x, &cs2, &T, &lnd);
+  transport_t tr;
+  transport(c, e, P0, T, lnd, &tr);
+  double pi[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) pi[a][b] = F->q[PIX[a][b]][idx];
+  double du[4][4];
+  for (int m = 0; m < 4; ++m) du[0][m] = (u[m] - uprev[m][idx]) / c->P.dtau;
+  for (int d = 0; d < 3; ++d)
+    for (int m = 0; m < 4; ++m) du[d + 1][m] = (F->u[m][idx + str[d]] - F->u[m][idx - str[d]]) / (2.0 * Dd[d]);
+  tens_t t;
+  tensor_terms(&g, u, du, pi, &t);
+  double tpp = c->P.tau_pipi_on ? 10.0 / 7.0 : 0.0;
+  double pp = 0.0, ss = 0.0, xx = 0.0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      double w = g.glo[a] * g.glo[b];
+      /* J^{ab}/tau_pi = 2 pi_l^<a omega^b>l - (4/3) pi theta - (tau_pipi/tau_pi) pi^l<a sigma_l^b>
+       *               + (6/5) Pi sigma, with I3, I4 of App. A */
+      double X = t.I3[a][b] - (4.0 / 3.0) * t.theta * pi[a][b] - tpp * t.I4[a][b] + 1.2 * Pi * t.sigma[a][b];
+      pp += pi[a][b] * pi[a][b] * w;
+      ss += t.sigma[a][b] * t.sigma[a][b] * w;
+      xx += X * X * w;
+    }
+  double es = coef_value(c->P.eta_kind, c->P.eta_c, T);
+  double tau_pi = tr.shear_on ? 5.0 * es / T : 0.0;
+  double tau_Pi = tr.bulk_on ? exp(-(log(15.0) + 2.0 * lnd + log(T) - coef_log(c->P.zeta_kind, c->P.zeta_c, T)))
+                             : 0.0;
+  out[0] = tau_pi * t.theta;
+  out[1] = tau_Pi * t.theta;
+  out[2] = sqrt(pp) / P0;
+  out[3] = fabs(Pi) / P0;
+  out[4] = (tr.shear_on && ss > 0.0) ? sqrt(xx) / (2.0 * tr.eta_over_taupi * sqrt(ss)) : 0.0;
+  double J = (2.0 / 3.0) * Pi * t.theta - tr.lam_Pipi * t.pisig; /* -J / tau_Pi */
+  out[5] = (tr.bulk_on && t.theta != 0.0) ? fabs(J) / (tr.zeta_over_tauPi * fabs(t.theta)) : 0.0;
+}
+
+int ko_diagnostics(const ko_ctx* c, double* out) {
+  fields_t F = {{0}, {0}, c->e, c->p};
+  for (int n = 0; n < NQ; ++n) F.q[n] = c->q[n];
+  for (int m = 0; m < 4; ++m) F.u[m] = c->u[m];
+  int nx = c->P.nx, ny = c->P.ny, nz = c->P.neta;
+  size_t ncp = (size_t)nx * ny * nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t o = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * (size_t)k);
+        size_t idx = cidx(c, i + 2, j + 2, k + 2);
+        double d[6];
+        cell_diagnostics(c, &F, c->up, c->tau, idx, d);
+        for (int m = 0; m < 6; ++m) out[(size_t)m * ncp + o] = d[m];
+        out[6 * ncp + o] = c->reg[idx];
       }
   return 0;
 }
@@ -734,6 +809,7 @@ int ko_set_state(ko_ctx* c, double tau, const double* e, const double* u, const 
         c->q[14][idx] = Pic;
         c->e[idx] = ec;
         c->p[idx] = P0;
+        c->reg[idx] = 1.0;
         for (int m = 0; m < 4; ++m) c->u[m][idx] = uu[m];
         if (u_prev) {
           double px = u_prev[o], py = u_prev[ncp + o], pn = u_prev[2 * ncp + o];
@@ -767,6 +843,7 @@ int ko_set_state_q(ko_ctx* c, double tau, const double* q, const double* e, cons
         eos_eval(c, e[o], &P0, &cs2, &T, &lnd);
         c->e[idx] = e[o];
         c->p[idx] = P0;
+        c->reg[idx] = 1.0;
         for (int m = 0; m < 4; ++m) {
           c->u[m][idx] = u[(size_t)m * ncp + o];
           c->up[m][idx] = u_prev ? u_prev[(size_t)m * ncp + o] : c->u[m][idx];
@@ -823,9 +900,11 @@ ko_ctx* ko_create(const ko_params* prm) {
     c->u[m] = zalloc(c->ncell); c->us[m] = zalloc(c->ncell); c->up[m] = zalloc(c->ncell); c->un[m] = zalloc(c->ncell);
   }
   c->e = zalloc(c->ncell); c->p = zalloc(c->ncell); c->es = zalloc(c->ncell); c->ps = zalloc(c->ncell);
+  c->reg = zalloc(c->ncell);
   /* unused ghost corners keep a harmless rest state */
   for (size_t i = 0; i < c->ncell; ++i) {
     c->u[0][i] = c->us[0][i] = c->up[0][i] = c->un[0][i] = 1.0;
+    c->reg[i] = 1.0;
   }
   return c;
 }
@@ -836,6 +915,7 @@ void ko_free(ko_ctx* c) {
   for (int n = 0; n < NQ; ++n) { free(c->q[n]); free(c->qs[n]); free(c->Q[n]); }
   for (int m = 0; m < 4; ++m) { free(c->u[m]); free(c->us[m]); free(c->up[m]); free(c->un[m]); }
   free(c->e); free(c->p); free(c->es); free(c->ps);
+  free(c->reg);
   free(c);
 }
 

@@ -65,6 +65,10 @@ int ko_get_state(const ko_ctx* c, double* tau, double* e, double* u, double* pi,
 /* C[q] of Eq. (semiDiscreteKT) for the current state at the current tau (no update). */
 int ko_rhs(ko_ctx* c, double* out /* [15][cells] */);
 int ko_set_threads(int n);
+/* Validity diagnostics of Sec. 7 at the current state, out = [7][cells]: tau_pi theta,
+ * tau_Pi theta, sqrt(pi.pi)/P0, |Pi|/P0, the second-order inverse Reynolds numbers of shear and
+ * bulk (Eq. inverseReynoldsNumbers2), and the regulation factor of the last step. */
+int ko_diagnostics(const ko_ctx* c, double* out);
 /* eta/s and zeta/s at temperature T (fm^-1): out[0] = eta/s, out[1] = zeta/s */
 void ko_coefficients(const ko_ctx* c, double T, double* out);
 

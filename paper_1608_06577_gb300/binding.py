@@ -88,6 +88,7 @@ def load_library():
     L.kt_get_state_event.argtypes = [vp, C.c_int, dp, vp, vp, vp, vp, vp, C.c_int]
     L.kt_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int)]
     L.kt_time_kernels.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int)]
+    L.kt_get_diagnostics.argtypes = [vp, C.c_int, vp, C.c_int]
     _LIB = L
     return L
 
@@ -247,6 +248,13 @@ class KT:
         return {"block": tuple(blk), "grid_blocks": grid.value, "candidate_ms": list(ms)[:n.value]}
 
     KERNEL_SLOTS = ("stage1_rhs", "stage1_update", "stage2_rhs", "stage2_update", "tau_advance")
+    DIAGNOSTICS = ("Kn_theta_pi", "Kn_theta_Pi", "Rinv_pi", "Rinv_Pi", "R2inv_pi", "R2inv_Pi", "regulation")
+
+    def diagnostics(self, event=0) -> dict:
+        """The validity diagnostics of Sec. 7 at the current state (kt_get_diagnostics)."""
+        out = np.empty((7, self.ncells_ev[event]))
+        self._check(self.L.kt_get_diagnostics(self.ctx, int(event), _dptr(out), 0), "kt_get_diagnostics")
+        return dict(zip(self.DIAGNOSTICS, out))
 
     def time_kernels(self, n_steps: int) -> dict:
         """Advances n_steps steps launch by launch with CUDA events between the launches

@@ -66,6 +66,7 @@ struct Ctx {
   Lattice* d_lat = nullptr;
   Tile* d_tiles = nullptr;
   CUtensorMap* d_tmaps = nullptr;  // mixed precision: per event, the 4-d maps of qf (first nev) and qsf
+  float* reg = nullptr;            // regulation factor of the last step, per cell (diagnostics)
   int max_tiles = 0;
   // work decomposition
   int shape = 0;
@@ -168,6 +169,7 @@ size_t state_bytes(const std::vector<Lattice>& lat, long long gs, size_t max_cel
   b += align_up(lat.size() * sizeof(Lattice), 256);
   b += align_up((size_t)max_tiles * sizeof(Tile), 256);
   if (mixed) b += align_up(2 * lat.size() * sizeof(CUtensorMap), 256);
+  b += align_up(fs * 4, 256);                  // regulation factors
   return b;
 }
 
@@ -231,7 +233,7 @@ __device__ __forceinline__ double gnn_at(const Params& P, double tau) { return P
 template <typename R>
 __global__ void set_state_kernel(const Params P, const Lattice L, const double* __restrict__ in, int has_u, int has_pi,
                                  int has_Pi, int has_up, double tau, double* q, float* qf, R* U, R* Up, R* E, R* Pb,
-                                 unsigned* status) {
+                                 float* reg, unsigned* status) {
   long long ncp = (long long)L.nx * L.ny * L.nz;
   long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= ncp) return;
@@ -271,6 +273,7 @@ __global__ void set_state_kernel(const Params P, const Lattice L, const double* 
   const long long fs = L.fstride;
   const int pc[3] = {i + 2, j + 2, k + 2};
   const int nn[3] = {L.nx, L.ny, L.nz};
+  reg[L.idx(pc[0], pc[1], pc[2])] = 1.f;  // no regulation recorded yet
   for (int t = -1; t < 12; ++t) {
     int ii = pc[0], jj = pc[1], kk = pc[2];
     if (t >= 0) {
@@ -300,6 +303,27 @@ __global__ void gather_kernel(const Lattice L, const S* __restrict__ f, double* 
 }
 
 __global__ void advance_tau_kernel(double* tau, double dtau) { tau[0] += dtau; }
+
+// validity diagnostics of Sec. 7 at the current state of one event (kt_get_diagnostics): the
+// stage-1 right-hand side's kinematics and coefficients, evaluated per physical cell into the
+// packed output [7][cells], the last column the recorded regulation factor
+template <typename R>
+__global__ void diag_kernel(const Params P, const Lattice L, const StageIO<R> io, double tau, const float* reg,
+                            double* out) {
+  const long long ncp = (long long)L.nx * L.ny * L.nz;
+  const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= ncp) return;
+  const int i = (int)(o % L.nx), j = (int)((o / L.nx) % L.ny), k = (int)(o / ((long long)L.nx * L.ny));
+  const long long c = L.idx(i + 2, j + 2, k + 2);
+  const CellGeom<R> G = cell_geom<R>(P, tau);
+  R dq[NQ], du[4][4], dv, dg[6];
+  float amax = 0.f;
+  Faces<R> Fx, Fy, Fz;
+  cell_faces<R>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+  cell_sources<R, true>(P, L, io, c, G, du, dv, dq, dg);
+  for (int m = 0; m < 6; ++m) out[m * ncp + o] = to_f64<R>(dg[m]);
+  out[6 * ncp + o] = f2d_bits(reg[c]);
+}
 
 // training samples of the learned start: features as the stage kernel forms them, the exact
 // FP64 root and the target 10 ln(e / e_conf)
@@ -363,6 +387,7 @@ StageIO<R> make_io(Ctx* c, int stage) {
   io.max_speed_bits = c->d_stat + 1;
   io.counters = (unsigned long long*)(c->d_stat + 4);
   io.mlp_packed = c->learned ? c->d_mlp_packed : nullptr;
+  io.reg_out = (stage == 2) ? c->reg : nullptr;
   return io;
 }
 
@@ -386,6 +411,7 @@ UpdIO make_uio(Ctx* c, int stage) {
   u.status = c->d_stat;
   u.counters = (unsigned long long*)(c->d_stat + 4);
   u.mlp_packed = c->learned ? c->d_mlp_packed : nullptr;
+  u.reg_out = io.reg_out;
   return u;
 }
 
@@ -789,6 +815,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   for (const auto& s : kShapes) c->max_tiles = std::max(c->max_tiles, tiles_for(c->lat, s));
   c->d_tiles = (Tile*)carve((size_t)c->max_tiles * sizeof(Tile));
   if (c->mixed) c->d_tmaps = (CUtensorMap*)carve(2 * c->lat.size() * sizeof(CUtensorMap));
+  c->reg = (float*)carve(fs * 4);
   P.seg_d = c->seg_d;
   P.seg_f = c->seg_f;
 
@@ -856,12 +883,12 @@ int kt_set_state_event(kt_ctx* c, int event, double tau, const double* e, const 
     set_state_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, L, s, u != nullptr, pi != nullptr, Pi != nullptr,
                                                        u_prev != nullptr, tau, c->q, c->qf, (float*)c->U[c->cur],
                                                        (float*)c->U[c->prev], (float*)c->E[0], (float*)c->Pb[0],
-                                                       c->d_stat);
+                                                       c->reg, c->d_stat);
   else
     set_state_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, L, s, u != nullptr, pi != nullptr, Pi != nullptr,
                                                         u_prev != nullptr, tau, c->q, nullptr, (double*)c->U[c->cur],
                                                         (double*)c->U[c->prev], (double*)c->E[0], (double*)c->Pb[0],
-                                                        c->d_stat);
+                                                        c->reg, c->d_stat);
   CK(cudaGetLastError());
   unsigned st = 0;
   CK(cudaMemcpyAsync(&st, c->d_stat, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1003,6 +1030,27 @@ int kt_get_state_event(kt_ctx* c, int event, double* tau, double* e, double* u, 
 
 int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, double* Pi, double* q, int on_device) {
   return kt_get_state_event(c, 0, tau, e, u, pi, Pi, q, on_device);
+}
+
+int kt_get_diagnostics(kt_ctx* c, int event, double* out, int on_device) {
+  if (!c || !out) return KT_ERR_ARG;
+  if (event < 0 || event >= c->nev) return fail(c, KT_ERR_ARG, "kt_get_diagnostics: bad event");
+  if (!c->ev_set[event]) return fail(c, KT_ERR_ARG, "kt_get_diagnostics: event %d has no state", event);
+  const Lattice& L = c->lat[event];
+  const size_t ncp = (size_t)L.nx * L.ny * L.nz;
+  const int nb = (int)((ncp + 255) / 256);
+  if (c->mixed) {
+    StageIO<float> io = make_io<float>(c, 1);
+    diag_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, L, io, c->tau, c->reg, c->stage);
+  } else {
+    StageIO<double> io = make_io<double>(c, 1);
+    diag_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, L, io, c->tau, c->reg, c->stage);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, c->stage, 7 * ncp * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return KT_OK;
 }
 
 int kt_mlp_features(kt_ctx* c, long long n, const long long* cells, float* x, float* y, double* e_exact) {

@@ -32,6 +32,7 @@ struct UpdIO {
   unsigned* status;
   unsigned long long* counters;
   const uint32_t* mlp_packed;
+  float* reg_out;           // stage 2: the regulation factor applied at each cell, or null
 };
 
 // inversion inputs of q: T^{tau mu} (0-3), pi^{tau mu} (4-7), Pi (14)
@@ -348,6 +349,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
       }
     const float f = regulator_factor<float>(P, go, eR, P0R, uo, pm, qr[14]);
     if (f < 0.999f) ++nreg;
+    if (STAGE == 2 && io.reg_out) io.reg_out[c] = f;
     if (f != 1.f) {
       if constexpr (STAGE == 1) {
 #pragma unroll

@@ -37,6 +37,7 @@ struct StageIO {
   unsigned* max_speed_bits;
   unsigned long long* counters;  // [0] Newton iterations, [1] regulated cells, [2] fallbacks
   const uint32_t* mlp_packed;  // learned start: packed weights (see kt_mlp.cuh), or null
+  float* reg_out;        // stage 2: the regulation factor applied to pi^{n+1} at each cell, or null
 };
 
 // ------------------------------------------------------------------ a) the stencil
@@ -451,9 +452,10 @@ __device__ __forceinline__ void cell_faces(const Params& P, const Lattice& L, co
   face_setup<R, 2, TH1, IFACE>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fz);
 }
 
-template <typename R>
+template <typename R, bool DIAG = false>
 __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
-                                             const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ]);
+                                             const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ],
+                                             R* dg = nullptr);
 
 template <typename R, bool TH1 = false, bool IFACE = false>
 __device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
@@ -467,10 +469,18 @@ __device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, cons
   cell_sources<R>(P, L, io, c, G, du, dv, dq);
 }
 
-// the source vector J = S + G of App. B at the cell, added to dq
-template <typename R>
+// The source vector J = S + G of App. B at the cell, added to dq.  DIAG: also the validity
+// diagnostics of Sec. 7 into dg[0..5]: tau_pi theta, tau_Pi theta (unfloored relaxation times),
+// sqrt(pi.pi)/P0, |Pi|/P0, sqrt(J^{mu nu} J_{mu nu})/(2 eta sqrt(sigma.sigma)) and |J|/(zeta
+// |theta|) with J^{mu nu}, J the second-order terms of Eq. (14_moment_terms) (no diffusion); a
+// quantity whose channel is off, or whose denominator vanishes, is 0.
+template <typename R, bool DIAG>
 __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
-                                             const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ]) {
+                                             const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ], R* dg) {
+  if constexpr (DIAG) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dg[k] = R(0);
+  }
   const long long fs = L.fstride;
   const R tau = G.tau, gnn = G.gnn, inv_gnn = G.inv_gnn;
   // ---- b) sources at the cell
@@ -557,6 +567,7 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
       R rate_pi = (es > R(0)) ? sdiv(T, R(5) * es) : R(INFINITY);
       rate_pi = fmin(rate_pi, pr<R>(P).rate_max);
       const R tpp = pr<R>(P).tpp;
+      R xs = R(0);  // sigma.sigma (diagnostics)
       R av[4];  // pi^{mu lambda} D u_lambda
 #pragma unroll
       for (int m = 0; m < 4; ++m) av[m] = pi[m][0] * Dlo[0] + pi[m][1] * Dlo[1] + pi[m][2] * Dlo[2] + pi[m][3] * Dlo[3];
@@ -585,11 +596,23 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
           R I4 = R(0.5) * (Cm[a][b] + Cm[b][a]) - Dab * ps3;
           R Ipi = I1 + R(4.0 / 3.0) * theta * pi[a][b] - I3 + tpp * I4 - R(1.2) * Pic * sig[a][b];
           R S = (R(2) * eta_tp * sig[a][b] - rate_pi * pi[a][b] - Ipi) * iu0 + pi[a][b] * dv;
+          if constexpr (DIAG) {  // sums over the full tensor: off-diagonal pairs count twice
+            const R w = glo[a] * glo[b] * ((a == b) ? R(1) : R(2));
+            const R X = Ipi - I1;  // -J^{ab}/tau_pi
+            dg[2] += pi[a][b] * pi[a][b] * w;
+            dg[4] += X * X * w;
+            xs += sig[a][b] * sig[a][b] * w;
+          }
           // -G^{ab}/u^tau with G^{ab} = u^c Gamma^a_{cd} pi^{db} + (a <-> b)
           R ha = (a == 0) ? tg * uc[3] * pi[3][b] : ((a == 3) ? it * (uc[0] * pi[3][b] + uc[3] * pi[0][b]) : R(0));
           R hb = (b == 0) ? tg * uc[3] * pi[3][a] : ((b == 3) ? it * (uc[0] * pi[3][a] + uc[3] * pi[0][a]) : R(0));
           dq[pix(a, b)] += S - (ha + hb) * iu0;
         }
+      if constexpr (DIAG) {
+        dg[0] = sdiv(R(5) * es, T) * theta;
+        dg[4] = (xs > R(0)) ? sdiv(sqrt(dg[4]), R(2) * eta_tp * sqrt(xs)) : R(0);
+        (void)xs;
+      }
     }
     if (P.bulk_on) {
       R lrate = R(2.70805020110221) + R(2) * lnd + slog(T) - ln_zeta_over_s<R>(P, T);  // ln 15 + ...
@@ -598,6 +621,14 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
       R zt = R(15) * d * d * (ec + P0c);
       R IPi = R(2.0 / 3.0) * Pic * theta - R(1.6) * d * ps;
       dq[14] += (-zt * theta - rate_Pi * Pic - IPi) * iu0 + Pic * dv;
+      if constexpr (DIAG) {
+        dg[1] = sexp(-lrate) * theta;
+        dg[5] = (theta != R(0)) ? sdiv(fabs(IPi), zt * fabs(theta)) : R(0);
+      }
+    }
+    if constexpr (DIAG) {
+      dg[2] = sdiv(sqrt(dg[2]), P0c);
+      dg[3] = sdiv(fabs(Pic), P0c);
     }
   }
 }
@@ -676,6 +707,7 @@ __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, co
         }
       const R f = regulator_factor<R>(P, go, eR, P0R, uo, pm, qr[14]);
       if (f < R(0.999)) ++nreg;
+      if (STAGE == 2 && io.reg_out) io.reg_out[c] = (float)f;
       if (f != R(1)) {
         const double fd = to_f64<R>(f);
 #pragma unroll

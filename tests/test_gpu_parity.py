@@ -239,3 +239,26 @@ def test_lattice_eos_mixed_error():
     rel_e = np.max(np.abs(g["e"] / r["e"] - 1))
     print("lattice EOS, mixed, 40 steps: max rel err e", rel_e)
     assert rel_e < 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_diagnostics_parity(precision, baseline_eos):
+    """kt_get_diagnostics (validity diagnostics of Sec. 7) against the oracle after 6 steps on a
+    hotspot grid: FP64 to 1e-11 of each diagnostic's max (the regulation factor is stored in FP32,
+    so to 1e-7), mixed precision to 1e-4."""
+    from paper_1608_06577_gb300 import KT
+    p = hotspot_problem(nx=22, ny=18, neta=8, nhot=6, seed=10, r_max=1.0, eos_table=baseline_eos)
+    kt = KT(p, precision=precision)
+    kt.set_problem_state()
+    kt.step(6)
+    g = kt.diagnostics()
+    o = oracle.Oracle(p)
+    assert o.step(6) == 0
+    r = o.diagnostics()
+    tol = 1e-11 if precision == 0 else 1e-4
+    for k in r:
+        scale = max(np.max(np.abs(r[k])), 1e-300)
+        err = np.max(np.abs(g[k] - r[k])) / scale
+        t = max(tol, 1e-7) if k == "regulation" else tol
+        assert err <= t, (k, err)
+    assert np.min(g["regulation"]) < 1.0

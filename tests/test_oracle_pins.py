@@ -557,3 +557,62 @@ def test_nonconformal_bjorken_lattice_eos_e5():
     assert o.step(50) == 0
     s = o.get_state()
     assert s["Pi"][0] > 1e-4 * s["e"][0]
+
+
+# ------------------------------------------------------------- validity diagnostics (Sec. 7)
+def test_diagnostics_bjorken_closed_forms():
+    """Conformal Bjorken flow with pi at its Navier-Stokes value (tau_pipi = 0): theta = 1/tau,
+    so Kn = tau_pi/tau = 5 (eta/s)/(T tau); sqrt(pi.pi) = sqrt(3/2) 4 eta/(3 tau); and with
+    pi = 2 eta sigma the second-order terms reduce to J = -delta_pipi theta pi = -(4/3) tau_pi
+    theta pi, so (R_pi^(2))^-1 = (4/3) Kn.  The bulk diagnostics vanish without bulk viscosity and
+    no step has regulated anything."""
+    es, tau0 = 0.2, 0.25
+    p = bjorken_problem(T0_gev=0.6, tau0=tau0, eta_over_s=es, tau_pipi_on=False)
+    o = oracle.Oracle(p)
+    d = o.diagnostics()
+    e = p.e[0]
+    P, _, T = o.eos(e)
+    eta = es * (e + P) / T
+    assert np.allclose(d["Kn_theta_pi"], 5 * es / (T * tau0), rtol=1e-12)
+    assert np.allclose(d["Rinv_pi"], math.sqrt(1.5) * 4 * eta / (3 * tau0) / P, rtol=1e-12)
+    assert np.allclose(d["R2inv_pi"], 4 / 3 * 5 * es / (T * tau0), rtol=1e-12)
+    for k in ("Kn_theta_Pi", "Rinv_Pi", "R2inv_Pi"):
+        assert np.all(d[k] == 0.0)
+    assert np.all(d["regulation"] == 1.0)
+
+
+def test_diagnostics_bulk_closed_forms():
+    """Nonconformal Bjorken with the lattice EOS and zeta/s of Eq. (zetas), Pi = 0 and pi at
+    Navier-Stokes: tau_Pi theta = (zeta/s)/(15 (1/3 - c_s^2)^2 T tau), and with Pi = 0 the bulk
+    second-order term is lambda_Pipi pi.sigma = 1.6 (1/3 - c_s^2) tau_Pi 2 eta sigma.sigma with
+    sigma.sigma = 2/(3 tau^2) in Bjorken flow.  (The tables interpolate ln(1/3 - c_s^2) linearly,
+    while 1/3 - c_s^2 here comes from the derivative of the P interpolant: 1e-5 apart.)"""
+    es, tau0 = 0.2, 0.25
+    p = bjorken_problem(T0_gev=0.6, tau0=tau0, eta_over_s=es, eos="lattice", zeta="paper")
+    o = oracle.Oracle(p)
+    d = o.diagnostics()
+    e = p.e[0]
+    P, cs2, T = o.eos(e)
+    delta = 1.0 / 3.0 - cs2
+    zs = o.coefficients(T)[1]
+    eta = es * (e + P) / T
+    theta = 1 / tau0
+    assert np.allclose(d["Kn_theta_Pi"], zs / (15 * delta ** 2 * T) * theta, rtol=1e-4)
+    expect = 1.6 * delta * 2 * eta * (2 / (3 * tau0 ** 2)) / (15 * delta ** 2 * (e + P) * theta)
+    assert np.allclose(d["R2inv_Pi"], expect, rtol=1e-4)
+    assert np.all(d["Rinv_Pi"] == 0.0)
+
+
+def test_diagnostics_regulation_record(baseline_eos):
+    """The recorded regulation factor lies in (0, 1], is below 1 somewhere on a hotspot grid
+    after a few steps, and stays 1 with the regulator switched off."""
+    from workload.problem import hotspot_problem
+    p = hotspot_problem(nx=16, ny=14, neta=6, nhot=4, seed=5, r_max=0.6, eos_table=baseline_eos)
+    o = oracle.Oracle(p)
+    assert o.step(4) == 0
+    r = o.diagnostics()["regulation"]
+    assert np.all(r > 0) and np.all(r <= 1) and np.min(r) < 1 - 1e-4
+    p.regulate = False
+    o = oracle.Oracle(p)
+    assert o.step(4) == 0
+    assert np.all(o.diagnostics()["regulation"] == 1.0)
