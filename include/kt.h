@@ -176,6 +176,13 @@ int kt_get_state(kt_ctx* ctx, double* tau, double* e, double* u, double* pi, dou
  * kernel over the event (stencil precision of the context). */
 int kt_get_diagnostics(kt_ctx* ctx, int event, double* out, int on_device);
 
+/* Self-test of failure detection (the paper has no counterpart): one block waits, with at most
+ * `polls` polls, on an mbarrier that nothing arms -- the bounded wait the stage kernels use for
+ * their shared-memory copies -- and reports the timeout through the status word instead of
+ * hanging.  Returns KT_ERR_TIMEOUT (the expected outcome), KT_ERR_ARG for polls = 0, or a CUDA
+ * error.  The context stays usable. */
+int kt_selftest_wait(kt_ctx* ctx, unsigned polls);
+
 int kt_get_stats(kt_ctx* ctx, kt_stats* stats);
 const char* kt_last_error(const kt_ctx* ctx);
 void kt_free(kt_ctx* ctx);

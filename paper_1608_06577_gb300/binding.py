@@ -15,7 +15,7 @@ _LIB = None
 
 KT_OK = 0
 ERRORS = {-1: "KT_ERR_ARG", -2: "KT_ERR_CUDA", -3: "KT_ERR_OOM", -4: "KT_ERR_EOS", -5: "KT_ERR_STATE",
-          -6: "KT_ERR_INVERSION", -7: "KT_ERR_NONFINITE"}
+          -6: "KT_ERR_INVERSION", -7: "KT_ERR_NONFINITE", -8: "KT_ERR_TIMEOUT"}
 KT_FP64, KT_MIXED = 0, 1
 KT_INV_PLAIN, KT_INV_LEARNED = 0, 1
 MLP_NPARAM = 32 * 6 + 32 + 32 * 32 + 32 + 32 + 1
@@ -89,6 +89,7 @@ def load_library():
     L.kt_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int)]
     L.kt_time_kernels.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int)]
     L.kt_get_diagnostics.argtypes = [vp, C.c_int, vp, C.c_int]
+    L.kt_selftest_wait.argtypes = [vp, C.c_uint]
     _LIB = L
     return L
 
@@ -212,12 +213,21 @@ class KT:
             self._check(rc, "kt_step")
         return rc
 
-    def get_state(self, fields=("e", "u", "pi", "Pi", "q"), event=0):
+    def get_state(self, fields=("e", "u", "pi", "Pi", "q"), event=0, out=None):
+        """Host copies of the fields; `out` may hold preallocated float64 arrays (e.g. views of
+        pinned memory) for some of them."""
         N = self.ncells_ev[event]
+        given = out or {}
         out = {}
         shapes = {"e": (N,), "u": (4, N), "pi": (10, N), "Pi": (N,), "q": (15, N)}
         for f in ("e", "u", "pi", "Pi", "q"):
-            out[f] = np.empty(shapes[f]) if f in fields else None
+            if f in fields and f in given:
+                a = given[f]
+                if a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != shapes[f]:
+                    raise ValueError(f"out[{f!r}] must be a C-contiguous float64 array of shape {shapes[f]}")
+                out[f] = a
+            else:
+                out[f] = np.empty(shapes[f]) if f in fields else None
         tau = C.c_double()
         rc = self.L.kt_get_state_event(self.ctx, int(event), C.byref(tau),
                                        *[_dptr(out[f]) for f in ("e", "u", "pi", "Pi", "q")], 0)

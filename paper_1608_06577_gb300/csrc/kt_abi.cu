@@ -304,6 +304,20 @@ __global__ void gather_kernel(const Lattice L, const S* __restrict__ f, double* 
 
 __global__ void advance_tau_kernel(double* tau, double dtau) { tau[0] += dtau; }
 
+// Self-test of the bounded waits: every thread waits on an mbarrier that nothing arms, with the
+// given poll limit, exactly as the stage kernels wait for their TMA copies; the block records
+// ST_TIMEOUT and returns.
+__global__ void wait_selftest_kernel(unsigned polls, unsigned* status) {
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    kt::mbar_init(&bar, 1);
+    kt::fence_barrier_init();
+  }
+  __syncthreads();
+  const bool ok = kt::mbar_wait(&bar, 0u, polls);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
 // validity diagnostics of Sec. 7 at the current state of one event (kt_get_diagnostics): the
 // stage-1 right-hand side's kinematics and coefficients, evaluated per physical cell into the
 // packed output [7][cells], the last column the recorded regulation factor
@@ -1030,6 +1044,18 @@ int kt_get_state_event(kt_ctx* c, int event, double* tau, double* e, double* u, 
 
 int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, double* Pi, double* q, int on_device) {
   return kt_get_state_event(c, 0, tau, e, u, pi, Pi, q, on_device);
+}
+
+int kt_selftest_wait(kt_ctx* c, unsigned polls) {
+  if (!c || polls == 0) return KT_ERR_ARG;
+  CK(cudaMemsetAsync(c->d_stat, 0, 4, c->stream));
+  wait_selftest_kernel<<<1, 128, 0, c->stream>>>(polls, c->d_stat);
+  CK(cudaGetLastError());
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, c->d_stat, 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st & ST_TIMEOUT) return fail(c, KT_ERR_TIMEOUT, "kt_selftest_wait: the wait gave up after %u polls", polls);
+  return KT_OK;
 }
 
 int kt_get_diagnostics(kt_ctx* c, int event, double* out, int on_device) {

@@ -11,7 +11,8 @@
 // summed in FP64 onto q^n.  q* itself is never stored in FP64: the root-find of stage 1 forms the
 // components it needs (T^{tau mu}, pi^{tau mu}, Pi) in FP64, the stage-2 stencil reads the FP32
 // copy of q*, and the regulator's rescaling q* -> f q* of the pi components is carried in k_1 as
-// f k_1 + (f - 1) q^n.
+// f k_1 + (f - 1) q^n.  (Forming (k_1 + k_2)/2 in the stage-2 rhs kernel instead was measured
+// slower: the read of k_1 at the end of that kernel costs more than it saves in the update.)
 #pragma once
 #include "kt_stage.cuh"
 #include "kt_tma.cuh"
@@ -46,8 +47,9 @@ __device__ __forceinline__ constexpr bool inversion_component(int n) { return n 
 constexpr int kBoxMax = 2176;               // floats per buffer: >= 36 * 12 * 5 and a multiple of 32
 constexpr unsigned kWaitPolls = 1u << 20;   // mbarrier polls before a wait gives up (far beyond any copy)
 
-// Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM, 64 (update) 32 warps;
-// both measured faster than the occupancy the compiler picks unconstrained.
+// Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM; 64 (stage-1 update) 32
+// warps; 96 for the stage-2 update, which holds all 15 FP64 components; each measured faster than
+// the compiler's unconstrained choice.
 template <int STAGE, bool TH1, bool IFACE>
 __global__ void __maxnreg__(96)
     rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
@@ -286,6 +288,7 @@ __device__ __forceinline__ unsigned invert_split(const Params& P, double gnn, co
   return st;
 }
 
+// the increment added to q^n in FP64: k_1 (stage 1) or (k_1 + k_2)/2 (stage 2)
 template <int STAGE>
 __device__ __forceinline__ float increment(const UpdIO& io, long long a) {
   if constexpr (STAGE == 1) return __ldg(io.k1 + a);
@@ -389,7 +392,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
 }
 
 template <int STAGE, bool LEARNED>
-__global__ void __maxnreg__(64)
+__global__ void __maxnreg__(STAGE == 1 ? 64 : 96)
     update_kernel(const Params P, const UpdIO io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
                   int ntiles) {
   unsigned st = 0, nit = 0, nreg = 0, nfb = 0;

@@ -262,3 +262,22 @@ def test_diagnostics_parity(precision, baseline_eos):
         t = max(tol, 1e-7) if k == "regulation" else tol
         assert err <= t, (k, err)
     assert np.min(g["regulation"]) < 1.0
+
+
+def test_bounded_wait_times_out_and_context_survives(baseline_eos):
+    """Failure detection without a GPU fault: a wait on an mbarrier that nothing arms gives up
+    after its poll limit and the host sees KT_ERR_TIMEOUT; the same context then steps normally
+    and still matches the oracle."""
+    from paper_1608_06577_gb300 import KT
+    from paper_1608_06577_gb300.binding import ERRORS
+    p = hotspot_problem(nx=20, ny=16, neta=6, nhot=4, seed=2, r_max=0.8, eos_table=baseline_eos)
+    kt = KT(p, precision=1)
+    kt.set_problem_state()
+    rc = kt.L.kt_selftest_wait(kt.ctx, 1000)
+    assert rc == -8, ERRORS.get(rc, rc)  # KT_ERR_TIMEOUT
+    assert b"gave up" in kt.L.kt_last_error(kt.ctx)
+    kt.step(5)
+    assert kt.stats()["status"] == 0
+    o = oracle.Oracle(p)
+    assert o.step(5) == 0
+    assert np.max(np.abs(kt.get_state()["e"] / o.get_state()["e"] - 1)) < 1e-4
