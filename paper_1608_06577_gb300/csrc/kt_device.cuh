@@ -115,10 +115,18 @@ __device__ __forceinline__ int eos_interval(const Params& P, const EosSeg<R>* se
   float g = (__logf(ef) - P.lne0) * P.inv_h;
   int i = (g > 0.f) ? (int)g : 0;  // NaN compares false -> 0
   i = min(i, n1);
-  #pragma unroll 1
-  for (int it = 0; it < 64 && i > 0 && e < seg[i].e0; ++it) --i;
-  #pragma unroll 1
-  for (int it = 0; it < 64 && i < n1 && e >= seg[i + 1].e0; ++it) ++i;
+  if constexpr (sizeof(R) == 8) {  // nodes are positive: compare bit patterns (e <= 0 orders below all)
+    const long long b = __double_as_longlong(e);
+#pragma unroll 1
+    for (int it = 0; it < 64 && i > 0 && b < __double_as_longlong(seg[i].e0); ++it) --i;
+#pragma unroll 1
+    for (int it = 0; it < 64 && i < n1 && b >= __double_as_longlong(seg[i + 1].e0); ++it) ++i;
+  } else {
+#pragma unroll 1
+    for (int it = 0; it < 64 && i > 0 && e < seg[i].e0; ++it) --i;
+#pragma unroll 1
+    for (int it = 0; it < 64 && i < n1 && e >= seg[i + 1].e0; ++it) ++i;
+  }
   return i;
 }
 
@@ -173,20 +181,50 @@ __device__ __forceinline__ void eos_T_lnd(const Params& P, R e, R& T, R& lnd) {
 // Generalised minmod of (theta dl, (dl + dr)/2, theta dr), Sec. 3.1, with sgn(0) = 0, from the
 // one-sided differences dl = q_i - q_{i-1}, dr = q_{i+1} - q_i: the three arguments share a sign
 // exactly when dl and dr do, and then the result is that sign times the smallest magnitude.
-// This is the slope times the cell size.  (The product test loses slopes whose one-sided
-// differences multiply below the smallest subnormal, ~1e-45 in FP32 and ~1e-323 in FP64.)
-// TH1: theta = 1, where (|dl| + |dr|)/2 >= min(|dl|, |dr|) never decides (up to one ulp of the
-// rounded sum in FP32, the only precision that uses it).
+// This is the slope times the cell size.
+// FP64: the signs and magnitudes are compared as integers (the magnitudes of doubles order like
+// their bit patterns), so only the theta branch does FP64 arithmetic.  FP32 with theta = 1: the
+// median of (dl, dr, 0) by four min/max instructions.  (FP32 theta != 1 tests the sign by the
+// product, which loses slopes whose one-sided differences multiply below ~1e-45.)
+// TH1: theta = 1, where (|dl| + |dr|)/2 >= min(|dl|, |dr|) never decides.
 template <typename R, bool TH1 = false>
 __device__ __forceinline__ R limited_slope_d(R dl, R dr, R theta) {
-  R mn;
-  if constexpr (TH1) {
-    mn = fmin(fabs(dl), fabs(dr));
+  if constexpr (sizeof(R) == 8) {
+    const long long bl = __double_as_longlong(dl), br = __double_as_longlong(dr);
+    const long long ml = bl & 0x7fffffffffffffffLL, mr = br & 0x7fffffffffffffffLL;
+    R m = (ml < mr) ? dl : dr;  // the smaller magnitude (0 if either is 0), with the shared sign
+    if constexpr (!TH1) {
+      const R m1 = theta * m, m2 = R(0.5) * (dl + dr);
+      m = ((__double_as_longlong(m1) & 0x7fffffffffffffffLL) < (__double_as_longlong(m2) & 0x7fffffffffffffffLL))
+              ? m1 : m2;
+    }
+    return ((bl ^ br) >= 0) ? m : R(0);
+  } else if constexpr (TH1) {
+    return fmaxf(fminf(dl, dr), fminf(fmaxf(dl, dr), 0.f));
   } else {
-    mn = fmin(theta * fabs(dl), theta * fabs(dr));
+    R mn = fmin(theta * fabs(dl), theta * fabs(dr));
     mn = fmin(mn, R(0.5) * fabs(dl + dr));
+    return (dl * dr > R(0)) ? copysign(mn, dl) : R(0);
   }
-  return (dl * dr > R(0)) ? copysign(mn, dl) : R(0);
+}
+
+// a / b for b > 0 (face velocities: b is an extrapolated u^tau >= 1).  FP32: the fast hardware
+// division.  FP64, for b within [2^-125, 2^125): Newton-Raphson for 1/b from a single-precision
+// seed (b's leading 20 mantissa bits, approximate reciprocal: relative error ~2^-20), one step
+// r <- r + r (1 - b r) (~2^-40), then the quotient corrected once, q <- q + r (a - b q), which
+// leaves about one ulp; five FP64 instructions.  Other b take the IEEE division.
+__device__ __forceinline__ float vdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double vdiv(double a, double b) {
+  const unsigned hi = (unsigned)__double2hiint(b);
+  if ((hi >> 20) - 898u > 249u) return a / b;  // also b <= 0, NaN, infinity
+  const float bf = __uint_as_float((hi - 0x38000000u) << 3);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(bf));
+  const unsigned rb = __float_as_uint(rf);
+  const double r0 = __hiloint2double((int)((rb >> 3) + 0x38000000u), (int)(rb << 29));
+  const double r1 = fma(r0, fma(-b, r0, 1.0), r0);
+  const double q0 = a * r1;
+  return fma(r1, fma(-b, q0, a), q0);
 }
 
 // a / b, exp, ln in the stencil precision: the correctly rounded library forms in FP64; in FP32
@@ -259,6 +297,8 @@ __device__ __forceinline__ float d2f_bits(double d) {
 template <typename R> __device__ __forceinline__ double to_f64(R x);
 template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }
 template <> __device__ __forceinline__ double to_f64<float>(float x) { return f2d_bits(x); }
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(double x) { return d2f_bits(x); }
 template <typename R> __device__ __forceinline__ R from_f64(double x);
 template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_bits(x); }

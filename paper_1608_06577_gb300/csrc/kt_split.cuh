@@ -126,94 +126,6 @@ __global__ void __maxnreg__(96)
   block_stats(io.status, io.max_speed_bits, io.counters, bad ? ST_TIMEOUT : 0u, amax, 0u, 0u, 0u);
 }
 
-// ------------------------------------------------------------- d) the root-find (Sec. 2.4)
-// Positive doubles are ordered like their bit patterns read as integers, so the brackets and
-// tolerances below are compared with integer instructions and the slow FP64 pipe only does
-// arithmetic.
-__device__ __forceinline__ long long obits(double x) { return __double_as_longlong(x); }
-__device__ __forceinline__ long long abits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
-__device__ __forceinline__ double clamp_pos(double x, double lo, double hi) {  // lo, hi > 0; NaN -> hi
-  return (obits(x) < obits(lo)) ? lo : ((obits(x) <= obits(hi)) ? x : hi);
-}
-
-// interval of e > 0 in the FP64 table: the rule of eos_interval with integer comparisons
-__device__ __forceinline__ int eos_interval_pos(const Params& P, double e) {
-  const EosSeg<double>* seg = P.seg_d;
-  const int n1 = P.eos_n - 2;
-  const float g = (__logf(d2f_bits(e)) - P.lne0) * P.inv_h;
-  int i = (g > 0.f) ? (int)g : 0;  // NaN compares false -> 0
-  i = min(i, n1);
-  const long long b = obits(e);
-#pragma unroll 1
-  for (int it = 0; it < 64 && i > 0 && b < obits(seg[i].e0); ++it) --i;
-#pragma unroll 1
-  for (int it = 0; it < 64 && i < n1 && b >= obits(seg[i + 1].e0); ++it) ++i;
-  return i;
-}
-
-// The residual in product form g(e) = (e - E) A(e) + M^2 = f(e) A(e), A = E + P0(e) + Pi > 0:
-// the root and the sign of f(e) = e - E + M^2 / A of Eq. (eInferred), without a reciprocal.
-// Also A, P0(e) and, in single precision, A f'(e) = A - M^2 c_s^2 / A: the Newton step on f,
-// e - f/f' = e - g/(A f'), then needs the FP64 product of g with a single-precision factor
-// (which only sets the step length; f is nearly linear in e where M is small, g is not).
-struct Resid {
-  double g, A, p0;
-  float gp;
-};
-__device__ __forceinline__ Resid residual(const Params& P, double e, double E, double EPi, double M2, float M2f) {
-  const int i = eos_interval_pos(P, e);
-  const EosSeg<double>& s = P.seg_d[i];
-  const double d = e - s.e0;
-  Resid r;
-  r.p0 = fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
-  r.A = EPi + r.p0;
-  const double em = e - E;
-  r.g = fma(em, r.A, M2);
-  const EosSeg<float>& sf = P.seg_f[i];
-  const float df = d2f_bits(d);
-  const float c2 = fmaf(df, fmaf(df, 3.f * sf.a3, 2.f * sf.a2), sf.a1);
-  const float Af = d2f_bits(r.A);
-  r.gp = Af - __fdividef(M2f * c2, Af);
-  return r;
-}
-
-// one Newton step on f: e - g / (A f')
-__device__ __forceinline__ double newton_step(double e, const Resid& r) {
-  return fma(-r.g, f2d_bits(__frcp_rn(r.gp)), e);
-}
-
-// P0(e) on the FP64 table
-__device__ __forceinline__ double eos_P_pos(const Params& P, double e) {
-  const EosSeg<double>& s = P.seg_d[eos_interval_pos(P, e)];
-  const double d = e - s.e0;
-  return fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
-}
-
-// Plain root-find: safeguarded Newton inside the bracket [e_min, E] (a step that leaves it
-// bisects), from `start` if it lies inside, else from E; stop at |de| <= 2^-50 E (g is known to
-// about one ulp of E A), at most 100 steps.  Table EOS only.
-__device__ __forceinline__ unsigned rootfind_plain(const Params& P, double E, double EPi, double M2, float M2f,
-                                                   double start, double& e, double& P0, unsigned& iters) {
-  double lo = (P.e_min > 0.0) ? P.e_min : 1e-300, hi = E;
-  e = (obits(start) >= obits(lo) && obits(start) <= obits(hi)) ? start : hi;
-  const long long stop = obits(E * 0x1p-50);
-  int it;
-  for (it = 0; it < 100; ++it) {
-    const Resid r = residual(P, e, E, EPi, M2, M2f);
-    if (abits(r.g) == 0) break;
-    if (obits(r.g) < 0) lo = e; else hi = e;
-    double en = newton_step(e, r);
-    if (!(obits(en) >= obits(lo) && obits(en) <= obits(hi))) en = 0.5 * (lo + hi);
-    const double de = en - e;
-    e = en;
-    if (abits(de) <= stop) { ++it; break; }
-  }
-  iters += (unsigned)it;
-  if (obits(e) < obits(P.e_min)) e = P.e_min;
-  P0 = eos_P_pos(P, e);
-  return (it >= 100) ? ST_INVERSION : 0u;
-}
-
 // Learned start: from e_start at most two Newton steps; the root is accepted as soon as
 // |f(e)| <= 1e-10 E, i.e. |g| <= 1e-10 E A; otherwise the plain root-find continues from the
 // last iterate and the cell counts as a fallback.

@@ -44,11 +44,14 @@ struct StageIO {
 // Per direction d the cell has two faces, L = i-1/2 and R = i+1/2, each with a left (m) and a
 // right (p) state.  With F = v q the central-upwind flux of Eq. (Hflux) is linear in the face
 // states, H = (v^p - a)/2 q^p + (v^m + a)/2 q^m, so the velocities and speeds of a face are
-// folded once into four weights per direction (times 1/dx, the R-face weights negated) and
-// every component then costs its reconstruction and four multiply-adds.
+// folded once into four weights per direction (times 1/dx, the R-face weights negated),
+//   -(H_R - H_L)/dx = wLp q_L^p + wLm q_L^m + wRp q_R^p + wRm q_R^m,
+// and, with the face states q_L^m = q_{i-1} + s_{i-1}/2, q_L^p = q_i - s_i/2, q_R^m = q_i + s_i/2,
+// q_R^p = q_{i+1} - s_{i+1}/2, every component costs its three slopes and seven multiply-adds:
+//   (wLp + wRm) q_i + wLm q_{i-1} + wRp q_{i+1} + (wLm s_{i-1} + (wRm - wLp) s_i - wRp s_{i+1})/2.
 template <typename R>
 struct Faces {
-  R wLp, wLm, wRp, wRm;  // -(H_R - H_L)/dx = wLp q_L^p + wLm q_L^m + wRp q_R^p + wRm q_R^m
+  R c0, wLm, wRp, dW;    // c0 = wLp + wRm, dW = wRm - wLp
   R vpl_h, vmi_h;        // v^d at i+1 and i-1, times 1/(2 dx)
   R hinv;                // 1/(2 dx)
   int s;                 // element stride of direction d
@@ -166,22 +169,23 @@ __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, co
     const R sd_m = limited_slope_d<R, TH1>(d0, d1, th), sd_0 = limited_slope_d<R, TH1>(d1, d2, th),
             sd_p = limited_slope_d<R, TH1>(d2, d3, th);
     const R h = R(0.5);
-    vLm = sdiv(fma(h, sd_m, um1[D + 1]), fma(h, st_m, um1[0]));
-    vLp = sdiv(fma(-h, sd_0, u0d), fma(-h, st_0, u0t));
-    vRm = sdiv(fma(h, sd_0, u0d), fma(h, st_0, u0t));
-    vRp = sdiv(fma(-h, sd_p, up1[D + 1]), fma(-h, st_p, up1[0]));
+    vLm = vdiv(fma(h, sd_m, um1[D + 1]), fma(h, st_m, um1[0]));
+    vLp = vdiv(fma(-h, sd_0, u0d), fma(-h, st_0, u0t));
+    vRm = vdiv(fma(h, sd_0, u0d), fma(h, st_0, u0t));
+    vRp = vdiv(fma(-h, sd_p, up1[D + 1]), fma(-h, st_p, up1[0]));
   }
   const R aL = fmax(fabs(vLp), fabs(vLm));
   const R aR = fmax(fabs(vRp), fabs(vRm));
-  amax = fmaxf(amax, (float)((D == 2) ? aR * sfac : aR));
-  F.wLp = (vLp - aL) * hinv;
+  amax = fmaxf(amax, to_f32((D == 2) ? aR * sfac : aR));
+  const R wLp = (vLp - aL) * hinv, wRm = -(vRm + aR) * hinv;
+  F.c0 = wLp + wRm;
+  F.dW = wRm - wLp;
   F.wLm = (vLm + aL) * hinv;
   F.wRp = (aR - vRp) * hinv;
-  F.wRm = -(vRm + aR) * hinv;
 
 #pragma unroll
   for (int m = 0; m < 4; ++m) du[D + 1][m] = (up1[m] - um1[m]) * hinv;
-  const R vpl = sdiv(up1[D + 1], up1[0]), vmi = sdiv(um1[D + 1], um1[0]);
+  const R vpl = vdiv(up1[D + 1], up1[0]), vmi = vdiv(um1[D + 1], um1[0]);
   dv += (vpl - vmi) * hinv;
   F.vpl_h = vpl * hinv;
   F.vmi_h = vmi * hinv;
@@ -231,9 +235,10 @@ __device__ __forceinline__ void add_row(R (&dq)[NQ], int r, R v) {
 
 // one component along one direction: generalised-minmod reconstruction from the five-point
 // stencil p[-2s..2s] (a0 = p[0] given; global memory, or shared memory if SMEM) and the flux
-// difference -(H_R - H_L)/dx; a1, b1 return the neighbours for the central differences of S_c
+// difference -(H_R - H_L)/dx, added to acc; a1, b1 return the neighbours for the central
+// differences of S_c
 template <typename R, bool SMEM, bool TH1 = false>
-__device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const Faces<R>& F, R& a1, R& b1) {
+__device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const Faces<R>& F, R& a1, R& b1, R acc) {
   R a2, b2;
   if constexpr (SMEM) {
     a2 = p[-2 * s]; a1 = p[-s]; b1 = p[s]; b2 = p[2 * s];
@@ -243,9 +248,11 @@ __device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const
   const R d0 = a1 - a2, d1 = a0 - a1, d2 = b1 - a0, d3 = b2 - b1;
   const R sm = limited_slope_d<R, TH1>(d0, d1, th), s0 = limited_slope_d<R, TH1>(d1, d2, th),
           sp = limited_slope_d<R, TH1>(d2, d3, th);
-  const R h = R(0.5);
-  const R qLm = fma(h, sm, a1), qLp = fma(-h, s0, a0), qRm = fma(h, s0, a0), qRp = fma(-h, sp, b1);
-  return fma(F.wLp, qLp, fma(F.wLm, qLm, fma(F.wRp, qRp, F.wRm * qRm)));
+  const R slopes = fma(F.wLm, sm, fma(F.dW, s0, -F.wRp * sp));
+  acc = fma(F.c0, a0, acc);
+  acc = fma(F.wLm, a1, acc);
+  acc = fma(F.wRp, b1, acc);
+  return fma(R(0.5), slopes, acc);
 }
 
 // Component n (warp-uniform) of the 15 conserved components, at a cell whose stencil starts at
@@ -256,9 +263,9 @@ __device__ __forceinline__ void component_rhs(int n, const R* p, int sx, int sy,
                                               const Faces<R>& Fy, const Faces<R>& Fz, R (&dq)[NQ]) {
   const R a0 = SMEM ? p[0] : ld<R>(p, 0);
   R a1x, b1x, a1y, b1y, a1z, b1z;
-  R acc = component_flux<R, SMEM, TH1>(p, sx, a0, th, Fx, a1x, b1x);
-  acc += component_flux<R, SMEM, TH1>(p, sy, a0, th, Fy, a1y, b1y);
-  acc += component_flux<R, SMEM, TH1>(p, sz, a0, th, Fz, a1z, b1z);
+  R acc = component_flux<R, SMEM, TH1>(p, sx, a0, th, Fx, a1x, b1x, R(0));
+  acc = component_flux<R, SMEM, TH1>(p, sy, a0, th, Fy, a1y, b1y, acc);
+  acc = component_flux<R, SMEM, TH1>(p, sz, a0, th, Fz, a1z, b1z, acc);
   add_row(dq, n, acc);
   if (n >= 4 && n <= 13) {  // pi components
     const int r0 = cross_row<0>(n, true);
@@ -285,54 +292,124 @@ __device__ __forceinline__ void conserved_fluxes(const Params& P, const Lattice&
   for (int n = 0; n < NQ; ++n, p += fs) component_rhs<R, false, TH1>(n, p, Fx.s, Fy.s, Fz.s, th, Fx, Fy, Fz, dq);
 }
 
+// ------------------------------------------------------------- d) the root-find (Sec. 2.4)
+// Positive doubles are ordered like their bit patterns read as integers, so the brackets and
+// tolerances below are compared with integer instructions and the slow FP64 pipe only does
+// arithmetic.
+__device__ __forceinline__ long long obits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long abits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+__device__ __forceinline__ double clamp_pos(double x, double lo, double hi) {  // lo, hi > 0; NaN -> hi
+  return (obits(x) < obits(lo)) ? lo : ((obits(x) <= obits(hi)) ? x : hi);
+}
+
+// interval of e > 0 in the FP64 table: the rule of eos_interval with integer comparisons
+__device__ __forceinline__ int eos_interval_pos(const Params& P, double e) {
+  const EosSeg<double>* seg = P.seg_d;
+  const int n1 = P.eos_n - 2;
+  const float g = (__logf(d2f_bits(e)) - P.lne0) * P.inv_h;
+  int i = (g > 0.f) ? (int)g : 0;  // NaN compares false -> 0
+  i = min(i, n1);
+  const long long b = obits(e);
+#pragma unroll 1
+  for (int it = 0; it < 64 && i > 0 && b < obits(seg[i].e0); ++it) --i;
+#pragma unroll 1
+  for (int it = 0; it < 64 && i < n1 && b >= obits(seg[i + 1].e0); ++it) ++i;
+  return i;
+}
+
+// The residual in product form g(e) = (e - E) A(e) + M^2 = f(e) A(e), A = E + P0(e) + Pi > 0:
+// the root and the sign of f(e) = e - E + M^2 / A of Eq. (eInferred), without a reciprocal.
+// Also A, P0(e) and, in single precision, A f'(e) = A - M^2 c_s^2 / A: the Newton step on f,
+// e - f/f' = e - g/(A f'), then needs the FP64 product of g with a single-precision factor
+// (which only sets the step length; f is nearly linear in e where M is small, g is not).
+struct Resid {
+  double g, A, p0;
+  float gp;
+};
+__device__ __forceinline__ Resid residual(const Params& P, double e, double E, double EPi, double M2, float M2f) {
+  const int i = eos_interval_pos(P, e);
+  const EosSeg<double>& s = P.seg_d[i];
+  const double d = e - s.e0;
+  Resid r;
+  r.p0 = fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
+  r.A = EPi + r.p0;
+  const double em = e - E;
+  r.g = fma(em, r.A, M2);
+  const EosSeg<float>& sf = P.seg_f[i];
+  const float df = d2f_bits(d);
+  const float c2 = fmaf(df, fmaf(df, 3.f * sf.a3, 2.f * sf.a2), sf.a1);
+  const float Af = d2f_bits(r.A);
+  r.gp = Af - __fdividef(M2f * c2, Af);
+  return r;
+}
+
+// one Newton step on f: e - g / (A f')
+__device__ __forceinline__ double newton_step(double e, const Resid& r) {
+  return fma(-r.g, f2d_bits(__frcp_rn(r.gp)), e);
+}
+
+// P0(e) on the FP64 table
+__device__ __forceinline__ double eos_P_pos(const Params& P, double e) {
+  const EosSeg<double>& s = P.seg_d[eos_interval_pos(P, e)];
+  const double d = e - s.e0;
+  return fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
+}
+
+// Plain root-find: safeguarded Newton inside the bracket [e_min, E] (a step that leaves it
+// bisects), from `start` if it lies inside, else from E; stop at |de| <= 2^-50 E (g is known to
+// about one ulp of E A), at most 100 steps.  Table EOS only.
+__device__ __forceinline__ unsigned rootfind_plain(const Params& P, double E, double EPi, double M2, float M2f,
+                                                   double start, double& e, double& P0, unsigned& iters) {
+  double lo = (P.e_min > 0.0) ? P.e_min : 1e-300, hi = E;
+  e = (obits(start) >= obits(lo) && obits(start) <= obits(hi)) ? start : hi;
+  const long long stop = obits(E * 0x1p-50);
+  int it;
+  for (it = 0; it < 100; ++it) {
+    const Resid r = residual(P, e, E, EPi, M2, M2f);
+    if (abits(r.g) == 0) break;
+    if (obits(r.g) < 0) lo = e; else hi = e;
+    double en = newton_step(e, r);
+    if (!(obits(en) >= obits(lo) && obits(en) <= obits(hi))) en = 0.5 * (lo + hi);
+    const double de = en - e;
+    e = en;
+    if (abits(de) <= stop) { ++it; break; }
+  }
+  iters += (unsigned)it;
+  if (obits(e) < obits(P.e_min)) e = P.e_min;
+  P0 = eos_P_pos(P, e);
+  return (it >= 100) ? ST_INVERSION : 0u;
+}
+
 // ------------------------------------------------------------ d) inversion, FP64 (Sec. 2.4)
-// f(e) = e - E + M^2/(E + P0(e) + Pi) = 0 by Newton-Raphson inside the bracket [e_min, E], with
-// bisection whenever a step leaves it; stop at |de| <= 2^-50 E (at most 100 steps).  With the
-// conformal EOS and no bulk pressure, the closed form.
+// T^{tau mu} -> (e, P0, u^mu) at tau (Eqs. eInferred-uiInferred): the safeguarded Newton of
+// rootfind_plain from the cell's previous e; with the conformal EOS and no bulk pressure, the
+// closed form.
 __device__ __forceinline__ unsigned invert_fp64(const Params& P, double tau, const double (&qn)[NQ], double guess,
                                                 double& e, double& P0, double (&uo)[4], unsigned& iters) {
-  double E = qn[0] - qn[4];
-  double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
-  double Pi = qn[14];
-  double gnn = P.milne ? tau * tau : 1.0;
-  double M2 = fma(Mx, Mx, fma(My, My, gnn * Mn * Mn));
+  const double E = qn[0] - qn[4];
+  const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
+  const double Pi = qn[14];
+  const double gnn = P.milne ? tau * tau : 1.0;
+  const double M2 = fma(Mx, Mx, fma(My, My, gnn * Mn * Mn));
   unsigned st = 0;
   if (!(E > 0.0) || !isfinite(E) || !isfinite(M2) || !(M2 < E * E)) {
     st = ST_INVERSION;
     e = (P.e_min > 0.0) ? P.e_min : 1e-30;
-  } else if (!P.eos_table && (!P.bulk_on || Pi == 0.0)) {
-    double M = sqrt(M2);  // conformal closed form e = sqrt(4E^2 - 3M^2) - E, cancellation-free
+    P0 = eos_P<double>(P, e);
+  } else if (!P.eos_table) {  // (bulk pressure is evolved with a table EOS only)
+    const double M = sqrt(M2);  // conformal closed form e = sqrt(4E^2 - 3M^2) - E, cancellation-free
     e = 3.0 * (E - M) * (E + M) / (sqrt(fma(4.0 * E, E, -3.0 * M2)) + E);
+    if (e < P.e_min) e = P.e_min;
+    P0 = e * (1.0 / 3.0);
   } else {
-    double lo = (P.e_min > 0.0) ? P.e_min : 1e-300, hi = E;
-    e = (guess >= lo && guess <= hi) ? guess : hi;  // the cell's previous e, else E
-    int it;
-    for (it = 0; it < 100; ++it) {
-      double p0, c2;
-      eos_P_cs2<double>(P, e, p0, c2);
-      double A = E + p0 + Pi;
-      double rA = 1.0 / A;
-      double f = e - E + M2 * rA;
-      if (f == 0.0) break;
-      if (f < 0.0) lo = e; else hi = e;
-      double fp = 1.0 - M2 * c2 * rA * rA;
-      double en = e - f / fp;
-      if (!(en >= lo && en <= hi)) en = 0.5 * (lo + hi);
-      double de = fabs(en - e);
-      e = en;
-      if (de <= ldexp(E, -50)) { ++it; break; }  // f is known to about one ulp of E
-    }
-    iters += (unsigned)it;
-    if (it >= 100) st |= ST_INVERSION;
+    st = rootfind_plain(P, E, E + Pi, M2, d2f_bits(M2), guess, e, P0, iters);
   }
-  if (e < P.e_min) e = P.e_min;
-  P0 = eos_P<double>(P, e);
   if (st) {
     uo[0] = 1.0; uo[1] = uo[2] = uo[3] = 0.0;
   } else {
-    double Pt = P0 + Pi;
-    double ut = sqrt((E + Pt) / (e + Pt));
-    double w = 1.0 / ((e + Pt) * ut);
+    const double Pt = P0 + Pi;
+    const double ut = sqrt((E + Pt) / (e + Pt));
+    const double w = 1.0 / ((e + Pt) * ut);
     uo[0] = ut; uo[1] = Mx * w; uo[2] = My * w; uo[3] = Mn * w;
   }
   if (!isfinite(e) || !isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3]))
@@ -707,7 +784,7 @@ __device__ __forceinline__ void stage_cell(const Params& P, const Lattice& L, co
         }
       const R f = regulator_factor<R>(P, go, eR, P0R, uo, pm, qr[14]);
       if (f < R(0.999)) ++nreg;
-      if (STAGE == 2 && io.reg_out) io.reg_out[c] = (float)f;
+      if (STAGE == 2 && io.reg_out) io.reg_out[c] = to_f32(f);
       if (f != R(1)) {
         const double fd = to_f64<R>(f);
 #pragma unroll
