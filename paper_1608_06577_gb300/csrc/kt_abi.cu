@@ -186,6 +186,9 @@ void fill_pr(PR<R>& o, const Params& P) {
   o.inv_d[0] = (R)(1.0 / P.dx);
   o.inv_d[1] = (R)(1.0 / P.dy);
   o.inv_d[2] = (R)(1.0 / P.deta);
+  o.half_inv_d[0] = (R)(0.5 / P.dx);
+  o.half_inv_d[1] = (R)(0.5 / P.dy);
+  o.half_inv_d[2] = (R)(0.5 / P.deta);
   o.theta = (R)P.theta;
   o.inv_dtau = (R)(1.0 / P.dtau);
   o.dtau = (R)P.dtau;
@@ -333,8 +336,9 @@ __global__ void diag_kernel(const Params P, const Lattice L, const StageIO<R> io
   R dq[NQ], du[4][4], dv, dg[6];
   float amax = 0.f;
   Faces<R> Fx, Fy, Fz;
-  cell_faces<R>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
-  cell_sources<R, true>(P, L, io, c, G, du, dv, dq, dg);
+  R uc[4];
+  cell_faces<R, false, false>(P, L, io, c, u_global(L, io, c), G, dq, uc, du, dv, amax, Fx, Fy, Fz);
+  cell_sources<R, true>(P, L, io, c, G, uc, du, dv, dq, dg);
   for (int m = 0; m < 6; ++m) out[m * ncp + o] = to_f64<R>(dg[m]);
   out[6 * ncp + o] = f2d_bits(reg[c]);
 }

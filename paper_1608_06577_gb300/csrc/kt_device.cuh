@@ -63,6 +63,7 @@ struct Coef {
 template <typename R>
 struct PR {
   R inv_d[3];          // 1/dx, 1/dy, 1/deta
+  R half_inv_d[3];     // 1/(2 dx), 1/(2 dy), 1/(2 deta)
   R theta;             // minmod parameter
   R inv_dtau, dtau, half_dtau;
   R rate_max;          // 1/tau_relax_min (or +inf)
@@ -213,6 +214,12 @@ __device__ __forceinline__ R limited_slope_d(R dl, R dr, R theta) {
 // seed (b's leading 20 mantissa bits, approximate reciprocal: relative error ~2^-20), one step
 // r <- r + r (1 - b r) (~2^-40), then the quotient corrected once, q <- q + r (a - b q), which
 // leaves about one ulp; five FP64 instructions.  Other b take the IEEE division.
+// max(a, b) of non-negative a, b (FP64: compared as integers, off the FP64 pipe)
+__device__ __forceinline__ float nmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double nmax(double a, double b) {
+  return (__double_as_longlong(a) < __double_as_longlong(b)) ? b : a;
+}
+
 __device__ __forceinline__ float vdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double vdiv(double a, double b) {
   const unsigned hi = (unsigned)__double2hiint(b);
@@ -227,10 +234,11 @@ __device__ __forceinline__ double vdiv(double a, double b) {
   return fma(r1, fma(-b, q0, a), q0);
 }
 
-// a / b, exp, ln in the stencil precision: the correctly rounded library forms in FP64; in FP32
-// the fast hardware forms (a few ulp; division operands are velocities, u^tau >= 1 and
-// transport scales, far from the range where the fast division degrades)
-__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
+// a / b, exp, ln in the stencil precision.  FP64: the division of vdiv (about one ulp; the IEEE
+// division for denominators outside its range), the library exp and log.  FP32: the fast
+// hardware forms (a few ulp; division operands are velocities, u^tau >= 1 and transport scales,
+// far from the range where the fast division degrades).
+__device__ __forceinline__ double sdiv(double a, double b) { return vdiv(a, b); }
 __device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double sexp(double x) { return exp(x); }
 __device__ __forceinline__ float sexp(float x) { return __expf(x); }

@@ -97,9 +97,12 @@ __global__ void __maxnreg__(96)
     const int i = tl.i0 + (int)threadIdx.x, j = tl.j0 + (int)threadIdx.y, k = tl.k0 + (int)threadIdx.z;
     const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
     const long long c = valid ? L.idx(i + 2, j + 2, k + 2) : 0;
-    float dq[NQ], du[4][4], dv = 0.f;
+    float dq[NQ], uc[4], du[4][4], dv = 0.f;
     Faces<float> Fx, Fy, Fz;
-    if (valid) cell_faces<float, TH1, IFACE>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+    if (valid) {  // the sources first: du and dv are dead before the component loop (fewer spills)
+      cell_faces<float, TH1, IFACE>(P, L, io, c, u_global(L, io, c), G, dq, uc, du, dv, amax, Fx, Fy, Fz);
+      cell_sources<float>(P, L, io, c, G, uc, du, dv, dq);
+    }
 
 #pragma unroll  // unrolled: the component index, the rows it feeds and every branch become constants
     for (int n = 0; n < NQ; ++n) {
@@ -111,10 +114,9 @@ __global__ void __maxnreg__(96)
       const unsigned b = done & 1u;
       if (!mbar_wait(&s_bar[b], (done >> 1) & 1u, kWaitPolls)) { bad = true; continue; }
       ++done;
-      if (valid) component_rhs<float, true, TH1>(n, &s_q[b][own], 1, sy, sz, th, Fx, Fy, Fz, dq);
+      if (valid) component_rhs<float, true, TH1>(P, n, &s_q[b][own], 1, sy, sz, th, Fx, Fy, Fz, dq);
     }
     if (valid && !bad) {  // (a timed-out block leaves at the next tile's barrier)
-      cell_sources<float>(P, L, io, c, G, du, dv, dq);
       const float dt = pr<float>(P).dtau;
 #pragma unroll
       for (int n = 0; n < NQ; ++n) k_out[n * L.fstride + c] = dq[n] * dt;

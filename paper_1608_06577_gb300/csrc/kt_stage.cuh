@@ -53,7 +53,6 @@ template <typename R>
 struct Faces {
   R c0, wLm, wRp, dW;    // c0 = wLp + wRm, dW = wRm - wLp
   R vpl_h, vmi_h;        // v^d at i+1 and i-1, times 1/(2 dx)
-  R hinv;                // 1/(2 dx)
   int s;                 // element stride of direction d
 };
 
@@ -134,34 +133,48 @@ __device__ __forceinline__ void face_velocities_inverted(const Params& P, const 
   vLm = v[0]; vLp = v[1]; vRm = v[2]; vRp = v[3];
 }
 
+// How the stencil reads u^mu around cell c: from the field arrays, through the read-only cache.
+// (Staging u^mu in shared memory by TMA, like q, measured slower: the stencil's scattered u loads
+// hit L1, which the larger shared-memory carve-out shrinks.)
+template <typename R>
+struct UGlobal {
+  const R* u;
+  long long fs, c;
+  int sy, sz;  // row pitch, plane
+  __device__ __forceinline__ R operator()(int m, int off) const { return ld<R>(u + m * fs, c + off); }
+};
+template <typename R>
+__device__ __forceinline__ UGlobal<R> u_global(const Lattice& L, const StageIO<R>& io, long long c) {
+  return UGlobal<R>{io.u_in, L.fstride, c, L.pitch, (int)L.plane};
+}
+
 // Velocity part of direction D: limited face states of u^tau and u^d and their ratio v^d
 // (Sec. 3.1), the local speeds a = max(|v^p|, |v^m|) (Eq. ax), the central differences
 // d_d u^mu and d_d v^d, and the pressure part of S_c (App. B):
 // -d_d (v^d P delta^nu_tau - g^{d nu} P), P = P0 + Pi.
-template <typename R, int D, bool TH1 = false, bool IFACE = false>
+template <typename R, int D, bool TH1, bool IFACE, typename UA>
 __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
-                                           R inv_gnn, R sfac, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax,
-                                           Faces<R>& F) {
+                                           const UA& ua, const R (&uc)[4], R inv_gnn, R sfac, R (&dq)[NQ],
+                                           R (&du)[4][4], R& dv, float& amax, Faces<R>& F) {
   const long long fs = L.fstride;
-  const int s = (D == 0) ? 1 : ((D == 1) ? L.pitch : (int)L.plane);
-  const R invD = pr<R>(P).inv_d[D];
-  const R hinv = R(0.5) * invD;
+  const int s = (D == 0) ? 1 : ((D == 1) ? L.pitch : (int)L.plane);  // in the field arrays
+  const int us = (D == 0) ? 1 : ((D == 1) ? ua.sy : ua.sz);           // where u is read
+  const R hinv = pr<R>(P).half_inv_d[D];
   const R th = pr<R>(P).theta;
-  const R* u = io.u_in;
 
   R um1[4], up1[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    um1[m] = ld<R>(u + m * fs, c - s);
-    up1[m] = ld<R>(u + m * fs, c + s);
+    um1[m] = ua(m, -us);
+    up1[m] = ua(m, us);
   }
   R vLm, vLp, vRm, vRp;
   if constexpr (IFACE) {
     face_velocities_inverted<R, D, TH1>(P, L, io, c, s, th, sfac * sfac, vLm, vLp, vRm, vRp);
   } else {
-    const R u0t = ld<R>(u, c), u0d = ld<R>(u + (D + 1) * fs, c);
-    const R um2t = ld<R>(u, c - 2 * s), um2d = ld<R>(u + (D + 1) * fs, c - 2 * s);
-    const R up2t = ld<R>(u, c + 2 * s), up2d = ld<R>(u + (D + 1) * fs, c + 2 * s);
+    const R u0t = uc[0], u0d = uc[D + 1];
+    const R um2t = ua(0, -2 * us), um2d = ua(D + 1, -2 * us);
+    const R up2t = ua(0, 2 * us), up2d = ua(D + 1, 2 * us);
     R t0 = um1[0] - um2t, t1 = u0t - um1[0], t2 = up1[0] - u0t, t3 = up2t - up1[0];
     R d0 = um1[D + 1] - um2d, d1 = u0d - um1[D + 1], d2 = up1[D + 1] - u0d, d3 = up2d - up1[D + 1];
     const R st_m = limited_slope_d<R, TH1>(t0, t1, th), st_0 = limited_slope_d<R, TH1>(t1, t2, th),
@@ -174,8 +187,8 @@ __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, co
     vRm = vdiv(fma(h, sd_0, u0d), fma(h, st_0, u0t));
     vRp = vdiv(fma(-h, sd_p, up1[D + 1]), fma(-h, st_p, up1[0]));
   }
-  const R aL = fmax(fabs(vLp), fabs(vLm));
-  const R aR = fmax(fabs(vRp), fabs(vRm));
+  const R aL = nmax(fabs(vLp), fabs(vLm));
+  const R aR = nmax(fabs(vRp), fabs(vRm));
   amax = fmaxf(amax, to_f32((D == 2) ? aR * sfac : aR));
   const R wLp = (vLp - aL) * hinv, wRm = -(vRm + aR) * hinv;
   F.c0 = wLp + wRm;
@@ -189,7 +202,6 @@ __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, co
   dv += (vpl - vmi) * hinv;
   F.vpl_h = vpl * hinv;
   F.vmi_h = vmi * hinv;
-  F.hinv = hinv;
   F.s = s;
 
   const R* q = io.qr_in;
@@ -259,8 +271,9 @@ __device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const
 // p with strides sx, sy, sz: -div H in x, y, eta and the remaining S_c terms
 // -d_d(-v^d pi^{tau nu} + pi^{d nu}) by central differences, added to dq.
 template <typename R, bool SMEM, bool TH1 = false>
-__device__ __forceinline__ void component_rhs(int n, const R* p, int sx, int sy, int sz, R th, const Faces<R>& Fx,
-                                              const Faces<R>& Fy, const Faces<R>& Fz, R (&dq)[NQ]) {
+__device__ __forceinline__ void component_rhs(const Params& P, int n, const R* p, int sx, int sy, int sz, R th,
+                                              const Faces<R>& Fx, const Faces<R>& Fy, const Faces<R>& Fz,
+                                              R (&dq)[NQ]) {
   const R a0 = SMEM ? p[0] : ld<R>(p, 0);
   R a1x, b1x, a1y, b1y, a1z, b1z;
   R acc = component_flux<R, SMEM, TH1>(p, sx, a0, th, Fx, a1x, b1x, R(0));
@@ -273,9 +286,10 @@ __device__ __forceinline__ void component_rhs(int n, const R* p, int sx, int sy,
       add_row(dq, r0, (Fx.vpl_h * b1x - Fx.vmi_h * a1x) + (Fy.vpl_h * b1y - Fy.vmi_h * a1y) +
                           (Fz.vpl_h * b1z - Fz.vmi_h * a1z));
     const int rx = cross_row<0>(n, false), ry = cross_row<1>(n, false), rz = cross_row<2>(n, false);
-    if (rx >= 0) add_row(dq, rx, -(b1x - a1x) * Fx.hinv);
-    if (ry >= 0) add_row(dq, ry, -(b1y - a1y) * Fy.hinv);
-    if (rz >= 0) add_row(dq, rz, -(b1z - a1z) * Fz.hinv);
+    const R* hinv = pr<R>(P).half_inv_d;  // kernel parameters: no registers held across the loop
+    if (rx >= 0) add_row(dq, rx, -(b1x - a1x) * hinv[0]);
+    if (ry >= 0) add_row(dq, ry, -(b1y - a1y) * hinv[1]);
+    if (rz >= 0) add_row(dq, rz, -(b1z - a1z) * hinv[2]);
   }
 }
 
@@ -289,7 +303,7 @@ __device__ __forceinline__ void conserved_fluxes(const Params& P, const Lattice&
   const R th = pr<R>(P).theta;
   const R* p = io.qr_in + c;
 #pragma unroll 1
-  for (int n = 0; n < NQ; ++n, p += fs) component_rhs<R, false, TH1>(n, p, Fx.s, Fy.s, Fz.s, th, Fx, Fy, Fz, dq);
+  for (int n = 0; n < NQ; ++n, p += fs) component_rhs<R, false, TH1>(P, n, p, Fx.s, Fy.s, Fz.s, th, Fx, Fy, Fz, dq);
 }
 
 // ------------------------------------------------------------- d) the root-find (Sec. 2.4)
@@ -408,8 +422,8 @@ __device__ __forceinline__ unsigned invert_fp64(const Params& P, double tau, con
     uo[0] = 1.0; uo[1] = uo[2] = uo[3] = 0.0;
   } else {
     const double Pt = P0 + Pi;
-    const double ut = sqrt((E + Pt) / (e + Pt));
-    const double w = 1.0 / ((e + Pt) * ut);
+    const double ut = sqrt(vdiv(E + Pt, e + Pt));
+    const double w = vdiv(1.0, (e + Pt) * ut);
     uo[0] = ut; uo[1] = Mx * w; uo[2] = My * w; uo[3] = Mn * w;
   }
   if (!isfinite(e) || !isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3]))
@@ -436,12 +450,12 @@ __device__ __forceinline__ R regulator_factor(const Params& P, R gnn, R e, R P0,
   R rho = sdiv(nPP, pr<R>(P).rho_max * sqrt(e * e + R(3) * P0 * P0));
   R den = sdiv(R(1), pr<R>(P).xi0_rho_max * nPP);
   R tr = pi[0][0] - pi[1][1] - pi[2][2] - gnn * pi[3][3];
-  rho = fmax(rho, fabs(tr) * den);
+  rho = nmax(rho, fabs(tr) * den);
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
     R o = pi[l][0] * u[0] - pi[l][1] * u[1] - pi[l][2] * u[2] - gnn * pi[l][3] * u[3];
     if (l == 3 && P.milne) o *= sqrt(gnn);
-    rho = fmax(rho, fabs(o) * den);
+    rho = nmax(rho, fabs(o) * den);
   }
   if (rho < R(1e-4)) return R(1) - rho * rho * R(1.0 / 3.0);
   return sdiv(tanh(rho), rho);
@@ -516,34 +530,38 @@ __device__ __forceinline__ CellGeom<R> cell_geom(const Params& P, double tau_src
   return g;
 }
 
-template <typename R, bool TH1 = false, bool IFACE = false>
+// the three directions' face setups; uc returns u^mu at the cell
+template <typename R, bool TH1, bool IFACE, typename UA>
 __device__ __forceinline__ void cell_faces(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
-                                           const CellGeom<R>& G, R (&dq)[NQ], R (&du)[4][4], R& dv, float& amax,
-                                           Faces<R>& Fx, Faces<R>& Fy, Faces<R>& Fz) {
+                                           const UA& ua, const CellGeom<R>& G, R (&dq)[NQ], R (&uc)[4],
+                                           R (&du)[4][4], R& dv, float& amax, Faces<R>& Fx, Faces<R>& Fy,
+                                           Faces<R>& Fz) {
 #pragma unroll
   for (int n = 0; n < NQ; ++n) dq[n] = R(0);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) uc[m] = ua(m, 0);
   dv = R(0);
   const R sfac = P.milne ? G.tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
-  face_setup<R, 0, TH1, IFACE>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fx);
-  face_setup<R, 1, TH1, IFACE>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fy);
-  face_setup<R, 2, TH1, IFACE>(P, L, io, c, G.inv_gnn, sfac, dq, du, dv, amax, Fz);
+  face_setup<R, 0, TH1, IFACE>(P, L, io, c, ua, uc, G.inv_gnn, sfac, dq, du, dv, amax, Fx);
+  face_setup<R, 1, TH1, IFACE>(P, L, io, c, ua, uc, G.inv_gnn, sfac, dq, du, dv, amax, Fy);
+  face_setup<R, 2, TH1, IFACE>(P, L, io, c, ua, uc, G.inv_gnn, sfac, dq, du, dv, amax, Fz);
 }
 
 template <typename R, bool DIAG = false>
 __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
-                                             const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ],
-                                             R* dg = nullptr);
+                                             const CellGeom<R>& G, const R (&uc)[4], R (&du)[4][4], R dv,
+                                             R (&dq)[NQ], R* dg = nullptr);
 
 template <typename R, bool TH1 = false, bool IFACE = false>
 __device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
                                          double tau_src, R (&dq)[NQ], float& amax) {
   const CellGeom<R> G = cell_geom<R>(P, tau_src);
-  R du[4][4];
+  R uc[4], du[4][4];
   R dv;
   Faces<R> Fx, Fy, Fz;
-  cell_faces<R, TH1, IFACE>(P, L, io, c, G, dq, du, dv, amax, Fx, Fy, Fz);
+  cell_faces<R, TH1, IFACE>(P, L, io, c, u_global(L, io, c), G, dq, uc, du, dv, amax, Fx, Fy, Fz);
   conserved_fluxes<R, TH1>(P, L, io, c, Fx, Fy, Fz, dq);
-  cell_sources<R>(P, L, io, c, G, du, dv, dq);
+  cell_sources<R>(P, L, io, c, G, uc, du, dv, dq);
 }
 
 // The source vector J = S + G of App. B at the cell, added to dq.  DIAG: also the validity
@@ -553,7 +571,8 @@ __device__ __forceinline__ void cell_rhs(const Params& P, const Lattice& L, cons
 // quantity whose channel is off, or whose denominator vanishes, is 0.
 template <typename R, bool DIAG>
 __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, const StageIO<R>& io, long long c,
-                                             const CellGeom<R>& G, R (&du)[4][4], R dv, R (&dq)[NQ], R* dg) {
+                                             const CellGeom<R>& G, const R (&uc)[4], R (&du)[4][4], R dv,
+                                             R (&dq)[NQ], R* dg) {
   if constexpr (DIAG) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) dg[k] = R(0);
@@ -561,10 +580,8 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
   const long long fs = L.fstride;
   const R tau = G.tau, gnn = G.gnn, inv_gnn = G.inv_gnn;
   // ---- b) sources at the cell
-  R uc[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    uc[m] = ld<R>(io.u_in + m * fs, c);
     du[0][m] = (uc[m] - ld<R>(io.u_prev + m * fs, c)) * pr<R>(P).inv_dtau;  // backward difference
   }
   const R* q = io.qr_in;
