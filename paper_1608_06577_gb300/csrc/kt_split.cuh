@@ -47,9 +47,9 @@ __device__ __forceinline__ constexpr bool inversion_component(int n) { return n 
 constexpr int kBoxMax = 2176;               // floats per buffer: >= 36 * 12 * 5 and a multiple of 32
 constexpr unsigned kWaitPolls = 1u << 20;   // mbarrier polls before a wait gives up (far beyond any copy)
 
-// Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM; 64 (stage-1 update) 32
+// Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM; 72 (stage-1 update) 28
 // warps; 96 for the stage-2 update, which holds all 15 FP64 components; each measured faster than
-// the compiler's unconstrained choice.
+// the compiler's unconstrained choice and than the neighbouring caps (64 and 80 for stage 1).
 template <int STAGE, bool TH1, bool IFACE>
 __global__ void __maxnreg__(96)
     rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
@@ -212,7 +212,7 @@ __device__ __forceinline__ float increment(const UpdIO& io, long long a) {
 // One cell; all lanes of the warp call it together (the learned start is warp-wide).
 template <int STAGE, bool LEARNED>
 __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, const UpdIO& io, int i, int j, int k,
-                                            double tau_out, const uint32_t* s_mlp, unsigned& st, unsigned& nit,
+                                            double gnn, const uint32_t* s_mlp, unsigned& st, unsigned& nit,
                                             unsigned& nreg, unsigned& nfb) {
   const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
   const long long fs = L.fstride;
@@ -226,7 +226,6 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
       if (inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
   }
 
-  const double gnn = P.milne ? tau_out * tau_out : 1.0;
   double start;
   if constexpr (LEARNED) {
     start = learned_start(P, gnn, qn, s_mlp);
@@ -241,21 +240,30 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
 
   // the FP32 copy read by the next stencil (and the remaining FP64 components in stage 2)
   float qr[NQ];
+  double q8[6];  // stage 2: q^n and the increment of pi components 8-13
+  float inc8[6];
+  bool scaled = false;
   if constexpr (STAGE == 1) {
 #pragma unroll
     for (int n = 0; n < NQ; ++n) qr[n] = __ldg(io.qf_n + n * fs + c) + __ldg(io.k1 + n * fs + c);
-  } else {  // the pi components outside the inversion set are read once, here
+  } else {  // the pi components outside the inversion set are read once, here; their FP64 sum
+            // waits for the regulation factor (f q^n + f dq in one multiply-add)
 #pragma unroll
     for (int n = 0; n < NQ; ++n) {
-      if (!inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
-      qr[n] = from_f64<float>(qn[n]);
+      if (!inversion_component(n)) {
+        q8[n - 8] = __ldg(io.q + n * fs + c);
+        inc8[n - 8] = increment<STAGE>(io, n * fs + c);
+        qr[n] = from_f64<float>(q8[n - 8]) + inc8[n - 8];
+      } else {
+        qr[n] = from_f64<float>(qn[n]);
+      }
     }
   }
   const float eR = from_f64<float>(e), P0R = from_f64<float>(P0);
 
   // e) regulator (Eq. regPimunu), after the root-find, on pi only
   if (P.regulate) {
-    const float go = P.milne ? from_f64<float>(tau_out * tau_out) : 1.f;
+    const float go = from_f64<float>(gnn);
     float pm[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -279,10 +287,18 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
         const double fd = to_f64<float>(f);
 #pragma unroll
         for (int n = 4; n < 14; ++n) {
-          qn[n] *= fd;
+          if (n < 8) qn[n] *= fd;
+          else qn[n] = fma(fd, q8[n - 8], to_f64<float>(f * inc8[n - 8]));
           qr[n] *= f;
         }
+        scaled = true;
       }
+    }
+  }
+  if constexpr (STAGE == 2) {
+    if (!scaled) {
+#pragma unroll
+      for (int n = 8; n < 14; ++n) qn[n] = q8[n - 8] + to_f64<float>(inc8[n - 8]);
     }
   }
 #pragma unroll
@@ -306,7 +322,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
 }
 
 template <int STAGE, bool LEARNED>
-__global__ void __maxnreg__(STAGE == 1 ? 64 : 96)
+__global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     update_kernel(const Params P, const UpdIO io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
                   int ntiles) {
   unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
@@ -316,13 +332,14 @@ __global__ void __maxnreg__(STAGE == 1 ? 64 : 96)
     __syncthreads();
   }
   const double tau_out = io.d_tau[0] + P.dtau;
+  const double gnn = P.milne ? tau_out * tau_out : 1.0;  // -g_{eta eta} at tau^{n+1}
   int t0, t1;
   tile_range(ntiles, t0, t1);
   for (int t = t0; t < t1; ++t) {
     const Tile tl = tiles[t];
     const Lattice L = lats[tl.event];
     update_cell<STAGE, LEARNED>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z,
-                                tau_out, s_mlp, st, nit, nreg, nfb);
+                                gnn, s_mlp, st, nit, nreg, nfb);
   }
   block_stats(io.status, nullptr, io.counters, st, 0.f, nit, nreg, nfb);
 }
