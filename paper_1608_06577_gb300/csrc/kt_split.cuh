@@ -212,7 +212,7 @@ __device__ __forceinline__ float increment(const UpdIO& io, long long a) {
 // One cell; all lanes of the warp call it together (the learned start is warp-wide).
 template <int STAGE, bool LEARNED>
 __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, const UpdIO& io, int i, int j, int k,
-                                            double gnn, const uint32_t* s_mlp, unsigned& st, unsigned& nit,
+                                            double tau_out, const uint32_t* s_mlp, unsigned& st, unsigned& nit,
                                             unsigned& nreg, unsigned& nfb) {
   const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
   const long long fs = L.fstride;
@@ -226,6 +226,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
       if (inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
   }
 
+  const double gnn = P.milne ? tau_out * tau_out : 1.0;
   double start;
   if constexpr (LEARNED) {
     start = learned_start(P, gnn, qn, s_mlp);
@@ -239,15 +240,18 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   st |= invert_split<LEARNED>(P, gnn, qn, start, e, P0, uo, nit, nfb);
 
   // the FP32 copy read by the next stencil (and the remaining FP64 components in stage 2)
+  // Stage 2 with the plain root-find forms pi components 8-13 as f q^n + f dq in one FP64
+  // multiply-add once the regulation factor f is known; with the learned start the separate sum
+  // and product measured faster (the two instantiations allocate their registers differently).
+  constexpr bool kFusePi = (STAGE == 2) && !LEARNED;
   float qr[NQ];
-  double q8[6];  // stage 2: q^n and the increment of pi components 8-13
+  double q8[6];  // q^n and the increment of pi components 8-13 (kFusePi)
   float inc8[6];
   bool scaled = false;
   if constexpr (STAGE == 1) {
 #pragma unroll
     for (int n = 0; n < NQ; ++n) qr[n] = __ldg(io.qf_n + n * fs + c) + __ldg(io.k1 + n * fs + c);
-  } else {  // the pi components outside the inversion set are read once, here; their FP64 sum
-            // waits for the regulation factor (f q^n + f dq in one multiply-add)
+  } else if constexpr (kFusePi) {  // the pi components outside the inversion set are read once, here
 #pragma unroll
     for (int n = 0; n < NQ; ++n) {
       if (!inversion_component(n)) {
@@ -258,12 +262,18 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
         qr[n] = from_f64<float>(qn[n]);
       }
     }
+  } else {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) {
+      if (!inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
+      qr[n] = from_f64<float>(qn[n]);
+    }
   }
   const float eR = from_f64<float>(e), P0R = from_f64<float>(P0);
 
   // e) regulator (Eq. regPimunu), after the root-find, on pi only
   if (P.regulate) {
-    const float go = from_f64<float>(gnn);
+    const float go = P.milne ? from_f64<float>(tau_out * tau_out) : 1.f;
     float pm[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -287,7 +297,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
         const double fd = to_f64<float>(f);
 #pragma unroll
         for (int n = 4; n < 14; ++n) {
-          if (n < 8) qn[n] *= fd;
+          if (!kFusePi || n < 8) qn[n] *= fd;
           else qn[n] = fma(fd, q8[n - 8], to_f64<float>(f * inc8[n - 8]));
           qr[n] *= f;
         }
@@ -295,7 +305,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
       }
     }
   }
-  if constexpr (STAGE == 2) {
+  if constexpr (kFusePi) {
     if (!scaled) {
 #pragma unroll
       for (int n = 8; n < 14; ++n) qn[n] = q8[n - 8] + to_f64<float>(inc8[n - 8]);
@@ -332,14 +342,13 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     __syncthreads();
   }
   const double tau_out = io.d_tau[0] + P.dtau;
-  const double gnn = P.milne ? tau_out * tau_out : 1.0;  // -g_{eta eta} at tau^{n+1}
   int t0, t1;
   tile_range(ntiles, t0, t1);
   for (int t = t0; t < t1; ++t) {
     const Tile tl = tiles[t];
     const Lattice L = lats[tl.event];
     update_cell<STAGE, LEARNED>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z,
-                                gnn, s_mlp, st, nit, nreg, nfb);
+                                tau_out, s_mlp, st, nit, nreg, nfb);
   }
   block_stats(io.status, nullptr, io.counters, st, 0.f, nit, nreg, nfb);
 }
