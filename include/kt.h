@@ -207,6 +207,10 @@ int kt_get_state_event(kt_ctx* ctx, int event, double* tau, double* e, double* u
  * of (32,4,2), (32,8,1), (32,2,4), (32,1,8), (32,4,1), (32,2,2) with g = 0 a persistent grid (as
  * many blocks as are resident at once, each walking the tile table) or g = 1 one block per tile. */
 int kt_get_tuning(kt_ctx* ctx, int* block_xyz, int* grid_blocks, float* candidate_ms, int* n_candidates);
+/* Use candidate `candidate` (numbered as above) from now on, without autotuning; KT_ERR_ARG if it
+ * is out of range.  The results do not depend on the candidate: every candidate runs the same
+ * kernels on the same tiles. */
+int kt_set_tuning(kt_ctx* ctx, int candidate);
 
 /* Measurement (the paper has no counterpart): advance n_steps >= 1 steps exactly as kt_step does
  * but launch by launch, without the CUDA graph, with CUDA events on the context's stream between

@@ -87,6 +87,7 @@ def load_library():
     L.kt_set_state_event.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, vp, C.c_int]
     L.kt_get_state_event.argtypes = [vp, C.c_int, dp, vp, vp, vp, vp, vp, C.c_int]
     L.kt_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int)]
+    L.kt_set_tuning.argtypes = [vp, C.c_int]
     L.kt_time_kernels.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int)]
     L.kt_get_diagnostics.argtypes = [vp, C.c_int, vp, C.c_int]
     L.kt_selftest_wait.argtypes = [vp, C.c_uint]
@@ -252,10 +253,15 @@ class KT:
     def tuning(self) -> dict:
         blk = (C.c_int * 3)()
         grid = C.c_int()
-        ms = (C.c_float * 16)()
-        n = C.c_int(16)
+        ms = (C.c_float * 64)()
+        n = C.c_int(64)
         self._check(self.L.kt_get_tuning(self.ctx, blk, C.byref(grid), ms, C.byref(n)), "kt_get_tuning")
         return {"block": tuple(blk), "grid_blocks": grid.value, "candidate_ms": list(ms)[:n.value]}
+
+    def set_tuning(self, candidate: int) -> None:
+        """Use autotuner candidate `candidate` = 2 s + g (tile shape s, grid variant g) from now on
+        (kt_set_tuning)."""
+        self._check(self.L.kt_set_tuning(self.ctx, int(candidate)), "kt_set_tuning")
 
     KERNEL_SLOTS = ("stage1_rhs", "stage1_update", "stage2_rhs", "stage2_update", "tau_advance")
     DIAGNOSTICS = ("Kn_theta_pi", "Kn_theta_Pi", "Rinv_pi", "Rinv_Pi", "R2inv_pi", "R2inv_Pi", "regulation")

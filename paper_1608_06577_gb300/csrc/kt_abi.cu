@@ -1116,6 +1116,14 @@ int kt_get_tuning(kt_ctx* c, int* block_xyz, int* grid_blocks, float* candidate_
   return KT_OK;
 }
 
+int kt_set_tuning(kt_ctx* c, int candidate) {
+  if (!c || candidate < 0 || candidate >= kNumCandidates) return KT_ERR_ARG;
+  int rc = select_shape(c, candidate);
+  if (rc != KT_OK) return rc;
+  c->tuned = true;  // no autotuning on the next step
+  return KT_OK;
+}
+
 int kt_get_stats(kt_ctx* c, kt_stats* s) {
   if (!c || !s) return KT_ERR_ARG;
   *s = c->last;
