@@ -358,10 +358,14 @@ def run_ours(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            # about 10 s of host work: a slab of ~1e6 cells of the same workload, 20 steps
+            # about 10 s of host work each: a slab of ~1e6 cells of the same workload, 20 steps, on
+            # all cores; a slab of ~1.3e5 cells, 8 steps, on one core
             nz = max(4, min(prob.neta, (1 << 20) // (prob.nx * prob.ny)))
             v, cores, sample = oracle_rate(prob, nz, 20, threads=os.cpu_count())
-            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+            nz1 = max(2, min(prob.neta, (1 << 17) // (prob.nx * prob.ny)))
+            v1, _, sample1 = oracle_rate(prob, nz1, 8, threads=1)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                   "single_core": {"value": v1, "unit": UNIT, "sample": sample1}}
         except Exception as ex:  # the baseline never blocks the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
 

@@ -14,6 +14,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "libkt_oracle.so")
 SRC = os.path.join(HERE, "kt_oracle.c")
+FLOPS_LIB = os.path.join(HERE, "libkt_oracle_flops.so")
+FLOPS_SRC = os.path.join(HERE, "kt_oracle_flops.cpp")
+FLOP_KINDS = ("add", "mul", "div", "sqrt", "transcendental", "compare")
 
 
 def build(force: bool = False) -> str:
@@ -25,6 +28,18 @@ def build(force: bool = False) -> str:
                                "-shared", "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
+
+
+def build_flops(force: bool = False) -> str:
+    """Compile the operation-counting oracle (kt_oracle.c with the counted scalar of flops.hpp in
+    place of double; single-threaded, no FMA contraction, so it reproduces the plain oracle)."""
+    srcs = [SRC, FLOPS_SRC, os.path.join(HERE, "flops.hpp"), os.path.join(HERE, "kt_oracle.h")]
+    if force or not os.path.exists(FLOPS_LIB) or os.path.getmtime(FLOPS_LIB) < max(map(os.path.getmtime, srcs)):
+        tmp = FLOPS_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-Wno-return-type-c-linkage", "-o", tmp, FLOPS_SRC, "-lm"])
+        os.replace(tmp, FLOPS_LIB)
+    return FLOPS_LIB
 
 
 class _Params(C.Structure):
@@ -43,14 +58,13 @@ class _Params(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = C.CDLL(LIB)
+def lib(flops: bool = False):
+    """The plain oracle library, or (flops=True) the operation-counting build of it."""
+    if flops not in _libs:
+        L = C.CDLL(build_flops() if flops else build())
         dp = C.POINTER(C.c_double)
         L.ko_create.restype = C.c_void_p
         L.ko_create.argtypes = [C.POINTER(_Params)]
@@ -70,8 +84,17 @@ def lib():
         L.ko_tensor_terms.argtypes = [C.c_void_p, C.c_double, dp, dp, dp, dp]
         L.ko_regulator_factor.restype = C.c_double
         L.ko_regulator_factor.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, dp, dp, C.c_double]
-        _lib = L
-    return _lib
+        if flops:
+            L.ko_flops_read.argtypes = [C.POINTER(C.c_ulonglong), C.c_int]
+        _libs[flops] = L
+    return _libs[flops]
+
+
+def read_flops(reset: bool = True) -> dict:
+    """Operation counts of the counting build since the last reset, by kind."""
+    out = (C.c_ulonglong * len(FLOP_KINDS))()
+    lib(True).ko_flops_read(out, int(reset))
+    return dict(zip(FLOP_KINDS, [int(x) for x in out]))
 
 
 def _ptr(a):
@@ -87,8 +110,9 @@ def _kind(k):
 class Oracle:
     """One oracle context for a workload.Problem."""
 
-    def __init__(self, prob, threads: int | None = None):
-        L = lib()
+    def __init__(self, prob, threads: int | None = None, flops: bool = False):
+        L = lib(flops)
+        self.L = L
         if threads is not None:
             L.ko_set_threads(int(threads))
         self.prob = prob
@@ -125,7 +149,7 @@ class Oracle:
     def __del__(self):
         try:
             if getattr(self, "ctx", None):
-                lib().ko_free(self.ctx)
+                self.L.ko_free(self.ctx)
                 self.ctx = None
         except Exception:
             pass
@@ -134,7 +158,7 @@ class Oracle:
         conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
         e, u, pi, Pi, u_prev = map(conv, (e, u, pi, Pi, u_prev))
         self._state_keep = (e, u, pi, Pi, u_prev)
-        return lib().ko_set_state(self.ctx, float(tau), _ptr(e), _ptr(u), _ptr(pi), _ptr(Pi), _ptr(u_prev))
+        return self.L.ko_set_state(self.ctx, float(tau), _ptr(e), _ptr(u), _ptr(pi), _ptr(Pi), _ptr(u_prev))
 
     def set_state_q(self, tau, q, e, u, u_prev=None):
         """Restart from evolved variables: q [15, cells], e [cells], u [4, cells] (with u^tau),
@@ -142,21 +166,21 @@ class Oracle:
         conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
         q, e, u, u_prev = map(conv, (q, e, u, u_prev))
         self._state_keep = (q, e, u, u_prev)
-        return lib().ko_set_state_q(self.ctx, float(tau), _ptr(q), _ptr(e), _ptr(u), _ptr(u_prev))
+        return self.L.ko_set_state_q(self.ctx, float(tau), _ptr(q), _ptr(e), _ptr(u), _ptr(u_prev))
 
     def step(self, n=1) -> int:
-        return lib().ko_step(self.ctx, int(n))
+        return self.L.ko_step(self.ctx, int(n))
 
     def get_state(self):
         N = self.prob.ncells
         tau = C.c_double()
         e = np.empty(N); u = np.empty((4, N)); pi = np.empty((10, N)); Pi = np.empty(N); q = np.empty((15, N))
-        lib().ko_get_state(self.ctx, C.byref(tau), _ptr(e), _ptr(u), _ptr(pi), _ptr(Pi), _ptr(q))
+        self.L.ko_get_state(self.ctx, C.byref(tau), _ptr(e), _ptr(u), _ptr(pi), _ptr(Pi), _ptr(q))
         return {"tau": tau.value, "e": e, "u": u, "pi": pi, "Pi": Pi, "q": q}
 
     def rhs(self):
         out = np.empty((15, self.prob.ncells))
-        lib().ko_rhs(self.ctx, _ptr(out))
+        self.L.ko_rhs(self.ctx, _ptr(out))
         return out
 
     DIAGNOSTICS = ("Kn_theta_pi", "Kn_theta_Pi", "Rinv_pi", "Rinv_Pi", "R2inv_pi", "R2inv_Pi", "regulation")
@@ -164,31 +188,31 @@ class Oracle:
     def diagnostics(self):
         """The validity diagnostics of Sec. 7 at the current state, as a dict of [cells] arrays."""
         out = np.empty((7, self.prob.ncells))
-        lib().ko_diagnostics(self.ctx, _ptr(out))
+        self.L.ko_diagnostics(self.ctx, _ptr(out))
         return dict(zip(self.DIAGNOSTICS, out))
 
     def coefficients(self, T):
         """(eta/s, zeta/s) at temperature T (fm^-1)."""
         out = np.empty(2)
-        lib().ko_coefficients(self.ctx, float(T), _ptr(out))
+        self.L.ko_coefficients(self.ctx, float(T), _ptr(out))
         return out[0], out[1]
 
     # single-formula entry points
     def eos(self, e):
         out = np.empty(3)
-        lib().ko_eos(self.ctx, float(e), _ptr(out))
+        self.L.ko_eos(self.ctx, float(e), _ptr(out))
         return out
 
     def invert(self, tau, q15):
         q15 = np.ascontiguousarray(q15, dtype=np.float64)
         out = np.empty(6)
-        st = lib().ko_invert(self.ctx, float(tau), _ptr(q15), _ptr(out))
+        st = self.L.ko_invert(self.ctx, float(tau), _ptr(q15), _ptr(out))
         return st, out
 
     def tensor_terms(self, tau, u4, du16, pi16):
         out = np.empty(101)
         a = [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in (u4, du16, pi16)]
-        lib().ko_tensor_terms(self.ctx, float(tau), _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(out))
+        self.L.ko_tensor_terms(self.ctx, float(tau), _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(out))
         names = ["sigma", "omega", "I1", "I3", "I4", "Gpi"]
         d = {"theta": out[0], "Du": out[1:5]}
         for k, nm in enumerate(names):
@@ -197,8 +221,8 @@ class Oracle:
 
     def regulator_factor(self, tau, e, P0, u4, pi16, Pi):
         a = [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in (u4, pi16)]
-        return lib().ko_regulator_factor(self.ctx, float(tau), float(e), float(P0), _ptr(a[0]), _ptr(a[1]),
-                                         float(Pi))
+        return self.L.ko_regulator_factor(self.ctx, float(tau), float(e), float(P0), _ptr(a[0]), _ptr(a[1]),
+                                          float(Pi))
 
 
 def minmod3(x, y, z) -> float:
