@@ -454,16 +454,37 @@ void launch_rhs(Ctx* c, const StageIO<float>& io) {
   const Shape& s = kShapes[c->shape];
   const dim3 blk(s.x, s.y, s.z);
   const CUtensorMap* maps = c->d_tmaps + (STAGE == 1 ? 0 : c->nev);
+  const size_t sm = rhs_smem_bytes(s.x, s.y, s.z);
   float* k = k_buf(c, STAGE);
   const bool t1 = (c->P.theta == 1.0), inv = c->P.iface_invert;
   if (t1 && !inv)
-    rhs_kernel<STAGE, true, false><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
+    rhs_kernel<STAGE, true, false><<<c->grid_rhs, blk, sm, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
   else if (!inv)
-    rhs_kernel<STAGE, false, false><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
+    rhs_kernel<STAGE, false, false><<<c->grid_rhs, blk, sm, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
   else if (t1)
-    rhs_kernel<STAGE, true, true><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
+    rhs_kernel<STAGE, true, true><<<c->grid_rhs, blk, sm, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
   else
-    rhs_kernel<STAGE, false, true><<<c->grid_rhs, blk, 0, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
+    rhs_kernel<STAGE, false, true><<<c->grid_rhs, blk, sm, c->stream>>>(c->P, io, k, c->d_lat, c->d_tiles, c->ntiles, maps);
+}
+
+// every rhs kernel may take the dynamic shared memory of the largest tile shape
+int allow_rhs_smem(Ctx* c) {
+  int bytes = 0;
+  for (const auto& sh : kShapes) bytes = std::max(bytes, rhs_smem_bytes(sh.x, sh.y, sh.z));
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  set((const void*)rhs_kernel<1, true, false>);
+  set((const void*)rhs_kernel<1, false, false>);
+  set((const void*)rhs_kernel<1, true, true>);
+  set((const void*)rhs_kernel<1, false, true>);
+  set((const void*)rhs_kernel<2, true, false>);
+  set((const void*)rhs_kernel<2, false, false>);
+  set((const void*)rhs_kernel<2, true, true>);
+  set((const void*)rhs_kernel<2, false, true>);
+  if (e != cudaSuccess) return fail(c, KT_ERR_CUDA, "rhs shared memory: %s", cudaGetErrorString(e));
+  return KT_OK;
 }
 
 template <int STAGE, bool LEARNED>
@@ -526,17 +547,18 @@ int enqueue_step(Ctx* c, cudaEvent_t* ev = nullptr) {
 
 // persistent grid: as many blocks of kernel K as fit on the device at once
 template <typename K>
-int occupancy_blocks(K kernel, const Shape& s) {
+int occupancy_blocks(K kernel, const Shape& s, size_t dyn_smem = 0) {
   int nb = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, s.x * s.y * s.z, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, s.x * s.y * s.z, dyn_smem);
   return std::max(1, nb) * std::max(1, sms);
 }
 
 // The TMA descriptors of the FP32 copies of q read by the mixed-precision stencil: per event a
 // 4-d map (x: pitch, y: ny + 4, eta: neta + 4, component: 15) with the strides of the padded
-// lattice, and a box of the tile plus its two-cell halo, (bx + 4) x (by + 4) x (bz + 4) x 1.
+// lattice, and a box of the tile plus its two-cell halo for kCompPerBox components,
+// (bx + 4) x (by + 4) x (bz + 4) x kCompPerBox.
 int encode_tensor_maps(Ctx* c) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -556,7 +578,7 @@ int encode_tensor_maps(Ctx* c) {
       float* base = (w == 0 ? c->qf : c->qsf) + L.base;
       cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)NQ};
       cuuint64_t strides[3] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4, (cuuint64_t)c->gs * 4};
-      cuuint32_t box[4] = {(cuuint32_t)(s.x + 4), (cuuint32_t)(s.y + 4), (cuuint32_t)(s.z + 4), 1};
+      cuuint32_t box[4] = {(cuuint32_t)(s.x + 4), (cuuint32_t)(s.y + 4), (cuuint32_t)(s.z + 4), kCompPerBox};
       cuuint32_t estr[4] = {1, 1, 1, 1};
       CUresult r = encode(&maps[w * c->nev + e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -584,7 +606,7 @@ int select_shape(Ctx* c, int cand) {
   const Shape& sh = kShapes[shape];
   auto grid = [&](int cap) { return one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles)); };
   if (c->mixed) {
-    c->grid_rhs = grid(occupancy_blocks(rhs_kernel<1, true, false>, sh));  // the same register cap for all
+    c->grid_rhs = grid(occupancy_blocks(rhs_kernel<1, true, false>, sh, rhs_smem_bytes(sh.x, sh.y, sh.z)));
     c->grid_upd = grid(c->learned ? occupancy_blocks(update_kernel<1, true>, sh)
                                   : occupancy_blocks(update_kernel<1, false>, sh));
     c->grid_blocks = c->grid_rhs;
@@ -867,7 +889,8 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   CK(cudaMemcpyAsync(c->d_lat, c->lat.data(), c->lat.size() * sizeof(Lattice), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  int rc = select_shape(c, 0);
+  int rc = c->mixed ? allow_rhs_smem(c) : KT_OK;
+  if (rc == KT_OK) rc = select_shape(c, 0);
   if (rc != KT_OK) return bail(rc);
   *out = c;
   return KT_OK;

@@ -39,13 +39,22 @@ struct UpdIO {
 // inversion inputs of q: T^{tau mu} (0-3), pi^{tau mu} (4-7), Pi (14)
 __device__ __forceinline__ constexpr bool inversion_component(int n) { return n < 8 || n == 14; }
 
-// Shared-memory staging of the stencil: per tile and component, a box of (bx+4) x (by+4) x (bz+4)
-// FP32 values (the tile and its two-cell halo in x, y, eta) is copied by TMA from the event's
-// 4-d tensor map (x, y, eta, component), double-buffered so that the copy of component n+1
-// overlaps the fluxes of component n.  Parts of a box beyond the padded lattice are zero-filled
-// by TMA and read by no valid cell.
-constexpr int kBoxMax = 2176;               // floats per buffer: >= 36 * 12 * 5 and a multiple of 32
+// Shared-memory staging of the stencil: per tile, the box of (bx+4) x (by+4) x (bz+4) FP32 values
+// (the tile and its two-cell halo in x, y, eta) of kCompPerBox consecutive components is copied by
+// one TMA load from the event's 4-d tensor map (x, y, eta, component) into one of two buffers, so
+// that the copy of the next group overlaps the fluxes of the current one, with one block barrier
+// per group.  Parts of a box beyond the padded lattice are zero-filled by TMA and read by no valid
+// cell.  The buffers live in dynamic shared memory sized for the tile shape (rhs_smem_bytes).
+constexpr int kBoxMax = 2176;               // floats per component box: >= 36 * 12 * 5, a multiple of 32
+constexpr int kCompPerBox = 3;              // components per TMA load (15 = 5 groups)
+constexpr int kGroups = (NQ + kCompPerBox - 1) / kCompPerBox;
 constexpr unsigned kWaitPolls = 1u << 20;   // mbarrier polls before a wait gives up (far beyond any copy)
+__host__ __device__ constexpr int rhs_buffer_floats(int tx, int ty, int tz) {  // 128-byte multiple
+  return (kCompPerBox * (tx + 4) * (ty + 4) * (tz + 4) + 31) & ~31;
+}
+__host__ __device__ constexpr int rhs_smem_bytes(int tx, int ty, int tz) {  // two buffers + alignment slack
+  return 4 * (2 * rhs_buffer_floats(tx, ty, tz) + 32);
+}
 
 // Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM; 72 (stage-1 update) 28
 // warps; 96 for the stage-2 update, which holds all 15 FP64 components; each measured faster than
@@ -54,11 +63,14 @@ template <int STAGE, bool TH1, bool IFACE>
 __global__ void __maxnreg__(96)
     rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
                const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ tmaps) {
-  __shared__ alignas(128) float s_q[2][kBoxMax];
+  extern __shared__ __align__(128) float s_raw[];
   __shared__ alignas(8) uint64_t s_bar[2];
+  float* const s_q = s_raw + ((32u - ((smem_u32(s_raw) >> 2) & 31u)) & 31u);  // TMA wants 128-byte buffers
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int bx = blockDim.x + 4, by = blockDim.y + 4, bz = blockDim.z + 4;
-  const unsigned box_bytes = 4u * bx * by * bz;
+  const int vol = bx * by * bz;                  // floats per component in a buffer
+  const unsigned box_bytes = 4u * kCompPerBox * vol;
+  const int bfl = rhs_buffer_floats(blockDim.x, blockDim.y, blockDim.z);
   if (tid == 0) {
     mbar_init(&s_bar[0], 1);
     mbar_init(&s_bar[1], 1);
@@ -74,11 +86,11 @@ __global__ void __maxnreg__(96)
   const float th = pr<float>(P).theta;
   const int sy = bx, sz = bx * by;
   const int own = ((int)threadIdx.z + 2) * sz + ((int)threadIdx.y + 2) * sy + (int)threadIdx.x + 2;
-  auto stage_box = [&](const CUtensorMap* map, const Tile& tl, int n) {  // thread 0 only
+  auto stage_group = [&](const CUtensorMap* map, const Tile& tl, int g) {  // thread 0 only
     const unsigned b = issued & 1u;
     fence_proxy_async_smem();  // earlier reads of this buffer before the async-proxy write
     mbar_arrive_expect_tx(&s_bar[b], box_bytes);
-    tma_load_4d(s_q[b], map, tl.i0, tl.j0, tl.k0, n, &s_bar[b]);
+    tma_load_4d(s_q + b * bfl, map, tl.i0, tl.j0, tl.k0, kCompPerBox * g, &s_bar[b]);
   };
 
   int t0, t1;
@@ -90,7 +102,7 @@ __global__ void __maxnreg__(96)
     if (__syncthreads_or(bad)) { bad = true; break; }  // every thread is done with both buffers
     if (tid == 0) {
       fence_tensormap_acquire(map);
-      stage_box(map, tl, 0);
+      stage_group(map, tl, 0);
     }
     ++issued;
 
@@ -105,16 +117,22 @@ __global__ void __maxnreg__(96)
     }
 
 #pragma unroll  // unrolled: the component index, the rows it feeds and every branch become constants
-    for (int n = 0; n < NQ; ++n) {
-      if (n + 1 < NQ) {
+    for (int g = 0; g < kGroups; ++g) {
+      if (g + 1 < kGroups) {
         if (__syncthreads_or(bad)) { bad = true; break; }  // the other buffer is free again
-        if (tid == 0) stage_box(map, tl, n + 1);
+        if (tid == 0) stage_group(map, tl, g + 1);
         ++issued;
       }
       const unsigned b = done & 1u;
       if (!mbar_wait(&s_bar[b], (done >> 1) & 1u, kWaitPolls)) { bad = true; continue; }
       ++done;
-      if (valid) component_rhs<float, true, TH1>(P, n, &s_q[b][own], 1, sy, sz, th, Fx, Fy, Fz, dq);
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < kCompPerBox; ++m)
+          if (kCompPerBox * g + m < NQ)
+            component_rhs<float, true, TH1>(P, kCompPerBox * g + m, s_q + b * bfl + m * vol + own, 1, sy, sz, th,
+                                            Fx, Fy, Fz, dq);
+      }
     }
     if (valid && !bad) {  // (a timed-out block leaves at the next tile's barrier)
       const float dt = pr<float>(P).dtau;
@@ -128,6 +146,7 @@ __global__ void __maxnreg__(96)
   block_stats(io.status, io.max_speed_bits, io.counters, bad ? ST_TIMEOUT : 0u, amax, 0u, 0u, 0u);
 }
 
+// ------------------------------------------------------------- d) the root-find (Sec. 2.4)
 // Learned start: from e_start at most two Newton steps; the root is accepted as soon as
 // |f(e)| <= 1e-10 E, i.e. |g| <= 1e-10 E A; otherwise the plain root-find continues from the
 // last iterate and the cell counts as a fallback.
