@@ -206,13 +206,18 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- our arm
-MODES = {"learned": (1, 1), "mixed": (1, 0), "fp64": (0, 0)}  # (precision, inversion)
+# (precision, inversion); "network_off" is the learned mode with all-zero weights, i.e. started
+# from the conformal root alone: the ablation that shows what the trained network adds
+MODES = {"learned": (1, 1), "mixed": (1, 0), "fp64": (0, 0), "network_off": (1, 1)}
 
 
 def make_kt(prob, mode, weights, stream):
+    import numpy as np
     import torch
     from paper_1608_06577_gb300 import KT
     prec, inv = MODES[mode]
+    if mode == "network_off" and weights is not None:
+        weights = np.zeros_like(weights)
     with torch.cuda.stream(stream):
         return KT(prob, precision=prec, inversion=inv, mlp_weights=weights if inv else None)
 
@@ -266,7 +271,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         weights = params.cpu().numpy()
         train_info = {"samples": int(X.shape[0]), "epochs": args.epochs, "final_loss": losses[-1], "rms_err_y": rms,
-                      "max_err_y": mx, "seconds": time.perf_counter() - t0,
+                      "max_err_y": mx, "rms_err_y_conformal": float(Y.double().pow(2).mean().sqrt().item()),
+                      "seconds": time.perf_counter() - t0,
                       "data": f"hotspots {n}^3 seeds 2-11, every 10 steps of 100"}
 
     results = {}

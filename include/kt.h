@@ -227,11 +227,14 @@ int kt_time_kernels(kt_ctx* ctx, int n_steps, float* ms, int* n_kernels);
  * KT_INV_LEARNED starts it from a small network: features (computed by the library from
  * E = T^tt - pi^tt, M^2 = Mx^2 + My^2 + tau^2 Meta^2 and Pi):
  *   x = [(ln E - 1)/6, M^2/E^2, 5 Pi/E, ln(1 - M^2/E^2)/2, e_conf/E, |M|/E],
- * e_conf = sqrt(4E^2 - 3M^2) - E the conformal root; output y, start e = e_conf exp(y/10).
+ * e_conf = sqrt(4E^2 - 3M^2) - E the conformal root; output z, start e = e_conf exp(y/10) with
+ * y = (M^2/E^2) z where M^2/E^2 > KT_MLP_GATE_R2, else y = 0 (the correction vanishes at rest,
+ * where e_conf = E is the root).
  * At most 2 FP64 Newton steps follow; a cell whose residual |f(e)|/E then exceeds 1e-10 falls
  * back to the plain root-find.  Parameters: KT_MLP_NPARAM floats, layout as documented above
  * KT_MLP_NPARAM.  All pointers below are device pointers; work goes to `stream`. */
 #define KT_MLP_PACKED_BYTES 3396 /* scratch of kt_mlp_predict: packed BF16 weights + FP32 biases */
+#define KT_MLP_GATE_R2 1e-3      /* M^2/E^2 above which the network's correction is applied */
 
 /* Training samples from the context's current state: for n physical cells (packed indices
  * i + nx*(j + ny*k), device int64 array `cells`), write the features x [n][6] (float), the

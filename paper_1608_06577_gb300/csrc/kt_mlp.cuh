@@ -1,9 +1,10 @@
 // kt_mlp.cuh -- the learned start of the T^{tau mu} -> e root-find (device side).
 //
-// A 6 -> 32 -> 32 -> 1 ReLU network predicts y = 10 ln(e / e_conf), where e_conf is the
-// conformal closed-form root sqrt(4E^2 - 3M^2) - E of Sec. 2.4.  Inference runs inside the
-// stage kernel with warp-level BF16 tensor-core MMAs (FP32 accumulation); the Newton steps
-// that follow it and the residual test are FP64.
+// A 6 -> 32 -> 32 -> 1 ReLU network predicts z, the correction y = 10 ln(e / e_conf) = r^2 z of
+// the conformal closed-form root e_conf = sqrt(4E^2 - 3M^2) - E of Sec. 2.4 (r^2 = M^2/E^2), for
+// cells with r^2 > kMlpGateR2 (below it y = 0).  Inference runs inside the stage kernel with
+// warp-level BF16 tensor-core MMAs (FP32 accumulation); the Newton steps that follow it and the
+// residual test are FP64.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -13,6 +14,7 @@
 namespace kt {
 
 constexpr int MLP_IN = 6, MLP_H = 32;
+constexpr float kMlpGateR2 = 1e-3f;  // r^2 above which the network's correction is applied
 constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;  // 1313
 constexpr int OFF_W1 = 0, OFF_B1 = 192, OFF_W2 = 224, OFF_B2 = 1248, OFF_W3 = 1280, OFF_B3 = 1312;
 

@@ -728,9 +728,12 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
 }
 
 // The network's start for the root-find of the cell's new state qn (components 0-7 and 14 are
-// read): features in FP32, the warp-wide tensor-core inference, e = E e_conf/E exp(y/10).
-// All 32 lanes of the warp call it together.
-// E, M^2 in single precision from the FP64 components (they only feed the features).
+// read): features in FP32, the warp-wide tensor-core inference of z, and the conformal root
+// corrected by y = r^2 z (r^2 = M^2/E^2, feature 1): e = E (e_conf/E) exp(y/10).  The correction
+// vanishes at rest, where e_conf = E is the root, and the network's BF16 error scales with it;
+// a warp whose cells all have r^2 <= kMlpGateR2 skips the inference.  All 32 lanes of the warp
+// call it together.  E, M^2 in single precision from the FP64 components (they only feed the
+// features).
 __device__ __forceinline__ double learned_start(const Params& P, double gnn, const double (&qn)[NQ],
                                                 const uint32_t* s_mlp) {
   const float Ef = d2f_bits(qn[0]) - d2f_bits(qn[4]);
@@ -739,7 +742,8 @@ __device__ __forceinline__ double learned_start(const Params& P, double gnn, con
   const float M2f = fmaf(Mx, Mx, fmaf(My, My, d2f_bits(gnn) * Mn * Mn));
   float x[MLP_IN], ecE;
   mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_bits(qn[14]), x, ecE);
-  const float y = mlp_warp_infer(s_mlp, x);
+  const float z = __any_sync(0xffffffffu, x[1] > kMlpGateR2) ? mlp_warp_infer(s_mlp, x) : 0.f;
+  const float y = (x[1] > kMlpGateR2) ? x[1] * z : 0.f;
   return f2d_bits(Ef * ecE * __expf(0.1f * y));
 }
 

@@ -3,7 +3,10 @@ arithmetic step runs in libkt's CUDA kernels).
 
 Data: cells sampled uniformly from trajectories of the hotspot workload (the 128^3 grid of
 the benchmark by default), every `every` steps, seeds distinct from the evaluation seed.
-Training: Adam on the mean squared error of y = 10 ln(e / e_conf), BF16 forward pass.
+The network corrects the conformal root e_conf: y = 10 ln(e / e_conf) = r^2 z with r^2 = M^2/E^2
+(feature 1), applied where r^2 > GATE_R2 (the same threshold as the kernels, KT_MLP_GATE_R2);
+it is trained on z = y / r^2 over those cells.  Training: Adam on the mean squared error of z,
+BF16 forward pass.
 """
 from __future__ import annotations
 
@@ -12,6 +15,8 @@ import math
 import numpy as np
 
 from .binding import KT, KT_MIXED, MLP_NPARAM, mlp_adam, mlp_grad, mlp_predict
+
+GATE_R2 = 1e-3  # KT_MLP_GATE_R2
 
 
 def init_params(seed=0):
@@ -77,10 +82,22 @@ def train(X, Y, epochs=20, batch=8192, lr=3e-3, lr_min=1e-4, seed=0, log=None):
     return params, losses
 
 
+def network_targets(X, Y):
+    """The cells the network corrects (r^2 > GATE_R2) and their targets z = y / r^2."""
+    r2 = X[:, 1]
+    keep = r2 > GATE_R2
+    return X[keep].contiguous(), (Y[keep] / r2[keep]).contiguous()
+
+
+def predict_y(params, X):
+    """The correction y of the learned start for feature rows X (tensor-core inference of z)."""
+    r2 = X[:, 1]
+    return (mlp_predict(params, X) * r2) * (r2 > GATE_R2)
+
+
 def evaluate(params, X, Y):
-    """Max and rms error of the tensor-core inference on (X, Y)."""
-    y = mlp_predict(params, X)
-    d = (y - Y).double()
+    """Max and rms error in y of the learned start (tensor-core inference) on (X, Y)."""
+    d = (predict_y(params, X) - Y).double()
     return float(d.abs().max().item()), float(d.pow(2).mean().sqrt().item())
 
 
@@ -88,5 +105,5 @@ def train_default(n=128, seeds=range(2, 12), n_samples=1_000_000, epochs=20, log
     """The network used by the benchmark: trajectories of the n^3 hotspot workload, seeds 2-11."""
     from workload.problem import hotspot_problem
     X, Y = collect(lambda s: hotspot_problem(nx=n, ny=n, neta=n, seed=s), list(seeds), n_samples)
-    params, losses = train(X, Y, epochs=epochs, log=log)
+    params, losses = train(*network_targets(X, Y), epochs=epochs, log=log)
     return params, losses, (X, Y)

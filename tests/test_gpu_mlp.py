@@ -106,7 +106,7 @@ def test_adam_step_formula():
 def trained():
     from paper_1608_06577_gb300 import learned
     X, Y = learned.collect(lambda s: _small(s, n=48, nz=24), [2, 5, 6], 200_000, steps=40, every=4)
-    params, losses = learned.train(X, Y, epochs=12, batch=4096)
+    params, losses = learned.train(*learned.network_targets(X, Y), epochs=12, batch=4096)
     return params, losses, X, Y
 
 
@@ -118,6 +118,8 @@ def test_training_reduces_loss(trained):
     assert losses[-1] < 0.3 * losses[0]
     # rms 1e-2 in y = 10 ln(e/e_conf) is a 1e-3 relative start: two Newton steps reach 1e-10
     assert rms < 1e-2
+    # the correction beats the conformal root it corrects (y = 0)
+    assert rms < 0.5 * float(Y.double().pow(2).mean().sqrt().item())
 
 
 def test_learned_inversion_accuracy_and_gain(trained):
