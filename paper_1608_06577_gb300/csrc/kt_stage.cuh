@@ -634,14 +634,16 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int m = 0; m < 4; ++m) nab[a][m] = gup[a] * cov[m][a] - uc[a] * Dup[m];
-    R sig[4][4], om[4][4];
+    R sig[4][4], om[4][4];  // symmetric and antisymmetric: each pair is computed once
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
+      for (int b = a; b < 4; ++b) {
         R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
         sig[a][b] = R(0.5) * (nab[a][b] + nab[b][a]) - theta3 * Dab;
-        om[a][b] = R(0.5) * (nab[b][a] - nab[a][b]);  // App. A convention
+        sig[b][a] = sig[a][b];
+        om[a][b] = (a == b) ? R(0) : R(0.5) * (nab[b][a] - nab[a][b]);  // App. A convention
+        om[b][a] = -om[a][b];
       }
     R ps = R(0);  // pi^{mu nu} sigma_{mu nu}
 #pragma unroll
@@ -674,7 +676,7 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
           R sb = R(0), sc = R(0);
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
-            sb += pi[a][l] * glo[l] * om[b][l];
+            if (l != b) sb += pi[a][l] * glo[l] * om[b][l];  // omega^{bb} = 0
             sc += pi[a][l] * glo[l] * sig[b][l];
           }
           B[a][b] = sb;
