@@ -276,7 +276,7 @@ __device__ __forceinline__ void component_rhs(const Params& P, int n, const R* p
                                               R (&dq)[NQ]) {
   const R a0 = SMEM ? p[0] : ld<R>(p, 0);
   R a1x, b1x, a1y, b1y, a1z, b1z;
-  R acc = component_flux<R, SMEM, TH1>(p, sx, a0, th, Fx, a1x, b1x, R(0));
+  R acc = component_flux<R, SMEM, TH1>(p, sx, a0, th, Fx, a1x, b1x, R(-0.0));
   acc = component_flux<R, SMEM, TH1>(p, sy, a0, th, Fy, a1y, b1y, acc);
   acc = component_flux<R, SMEM, TH1>(p, sz, a0, th, Fz, a1z, b1z, acc);
   add_row(dq, n, acc);
@@ -437,12 +437,12 @@ __device__ __forceinline__ R regulator_factor(const Params& P, R gnn, R e, R P0,
                                               R Pi) {
   const R glo[4] = {R(1), R(-1), R(-1), -gnn};
   const R gup[4] = {R(1), R(-1), R(-1), -sdiv(R(1), gnn)};
-  R PP = R(0);
+  R PP = R(-0.0);  // -0 is the exact additive identity (x + -0 = x), so zero terms fold away
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      R X = Pi * (((a == b) ? gup[a] : R(0)) - u[a] * u[b]) + pi[a][b];
+      R X = Pi * (((a == b) ? gup[a] : R(-0.0)) - u[a] * u[b]) + pi[a][b];
       PP += X * X * glo[a] * glo[b];
     }
   if (!(PP > R(0))) return R(1);
@@ -537,10 +537,10 @@ __device__ __forceinline__ void cell_faces(const Params& P, const Lattice& L, co
                                            R (&du)[4][4], R& dv, float& amax, Faces<R>& Fx, Faces<R>& Fy,
                                            Faces<R>& Fz) {
 #pragma unroll
-  for (int n = 0; n < NQ; ++n) dq[n] = R(0);
+  for (int n = 0; n < NQ; ++n) dq[n] = R(-0.0);  // exact additive identity
 #pragma unroll
   for (int m = 0; m < 4; ++m) uc[m] = ua(m, 0);
-  dv = R(0);
+  dv = R(-0.0);
   const R sfac = P.milne ? G.tau : R(1);  // sqrt(-g_{eta eta}): speeds along eta in units of c
   face_setup<R, 0, TH1, IFACE>(P, L, io, c, ua, uc, G.inv_gnn, sfac, dq, du, dv, amax, Fx);
   face_setup<R, 1, TH1, IFACE>(P, L, io, c, ua, uc, G.inv_gnn, sfac, dq, du, dv, amax, Fy);
@@ -615,10 +615,10 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
     R cov[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      cov[0][a] = du[a][0] + ((a == 3) ? tg * uc[3] : R(0));
+      cov[0][a] = du[a][0] + ((a == 3) ? tg * uc[3] : R(-0.0));
       cov[1][a] = du[a][1];
       cov[2][a] = du[a][2];
-      cov[3][a] = du[a][3] + ((a == 0) ? it * uc[3] : ((a == 3) ? it * uc[0] : R(0)));
+      cov[3][a] = du[a][3] + ((a == 0) ? it * uc[3] : ((a == 3) ? it * uc[0] : R(-0.0)));
     }
     const R theta = cov[0][0] + cov[1][1] + cov[2][2] + cov[3][3];
     const R theta3 = theta * R(1.0 / 3.0);
@@ -639,13 +639,13 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = a; b < 4; ++b) {
-        R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
+        R Dab = ((a == b) ? gup[a] : R(-0.0)) - uc[a] * uc[b];
         sig[a][b] = R(0.5) * (nab[a][b] + nab[b][a]) - theta3 * Dab;
         sig[b][a] = sig[a][b];
         om[a][b] = (a == b) ? R(0) : R(0.5) * (nab[b][a] - nab[a][b]);  // App. A convention
         om[b][a] = -om[a][b];
       }
-    R ps = R(0);  // pi^{mu nu} sigma_{mu nu}
+    R ps = R(-0.0);  // pi^{mu nu} sigma_{mu nu}
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -663,7 +663,7 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
       R rate_pi = (es > R(0)) ? sdiv(T, R(5) * es) : R(INFINITY);
       rate_pi = fmin(rate_pi, pr<R>(P).rate_max);
       const R tpp = pr<R>(P).tpp;
-      R xs = R(0);  // sigma.sigma (diagnostics)
+      R xs = R(-0.0);  // sigma.sigma (diagnostics)
       R av[4];  // pi^{mu lambda} D u_lambda
 #pragma unroll
       for (int m = 0; m < 4; ++m) av[m] = pi[m][0] * Dlo[0] + pi[m][1] * Dlo[1] + pi[m][2] * Dlo[2] + pi[m][3] * Dlo[3];
@@ -673,7 +673,7 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          R sb = R(0), sc = R(0);
+          R sb = R(-0.0), sc = R(-0.0);
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
             if (l != b) sb += pi[a][l] * glo[l] * om[b][l];  // omega^{bb} = 0
@@ -686,7 +686,7 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = a; b < 4; ++b) {
-          R Dab = ((a == b) ? gup[a] : R(0)) - uc[a] * uc[b];
+          R Dab = ((a == b) ? gup[a] : R(-0.0)) - uc[a] * uc[b];
           R I1 = av[a] * uc[b] + av[b] * uc[a];
           R I3 = B[a][b] + B[b][a];
           R I4 = R(0.5) * (Cm[a][b] + Cm[b][a]) - Dab * ps3;
@@ -700,9 +700,10 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
             xs += sig[a][b] * sig[a][b] * w;
           }
           // -G^{ab}/u^tau with G^{ab} = u^c Gamma^a_{cd} pi^{db} + (a <-> b)
-          R ha = (a == 0) ? tg * uc[3] * pi[3][b] : ((a == 3) ? it * (uc[0] * pi[3][b] + uc[3] * pi[0][b]) : R(0));
-          R hb = (b == 0) ? tg * uc[3] * pi[3][a] : ((b == 3) ? it * (uc[0] * pi[3][a] + uc[3] * pi[0][a]) : R(0));
-          dq[pix(a, b)] += S - (ha + hb) * iu0;
+          R ha = (a == 0) ? tg * uc[3] * pi[3][b] : ((a == 3) ? it * (uc[0] * pi[3][b] + uc[3] * pi[0][b]) : R(-0.0));
+          R hb = (b == 0) ? tg * uc[3] * pi[3][a] : ((b == 3) ? it * (uc[0] * pi[3][a] + uc[3] * pi[0][a]) : R(-0.0));
+          const bool geo = (a == 0 || a == 3 || b == 0 || b == 3);  // (a, b) in {1, 2}^2: G^{ab} = 0
+          dq[pix(a, b)] += geo ? S - (ha + hb) * iu0 : S;
         }
       if constexpr (DIAG) {
         dg[0] = sdiv(R(5) * es, T) * theta;
