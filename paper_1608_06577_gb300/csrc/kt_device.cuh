@@ -209,6 +209,24 @@ __device__ __forceinline__ R limited_slope_d(R dl, R dr, R theta) {
   }
 }
 
+// The three slopes of a five-point stencil, s_{i-1}, s_i, s_{i+1}, from its one-sided differences
+// d0..d3.  FP32 with theta = 1: minmod(a, b) = clamp(a, min(0, b), max(0, b)) (zero when the signs
+// differ or either is zero, else the smaller magnitude), so s_i and s_{i+1} share the bounds from
+// d2: ten min/max instructions for the three.  Otherwise limited_slope_d for each.
+template <typename R, bool TH1>
+__device__ __forceinline__ void three_slopes(R d0, R d1, R d2, R d3, R th, R& sm, R& s0, R& sp) {
+  if constexpr (sizeof(R) == 4 && TH1) {
+    const R lo1 = fminf(d1, 0.f), hi1 = fmaxf(d1, 0.f), lo2 = fminf(d2, 0.f), hi2 = fmaxf(d2, 0.f);
+    sm = fminf(fmaxf(d0, lo1), hi1);
+    s0 = fminf(fmaxf(d1, lo2), hi2);
+    sp = fminf(fmaxf(d3, lo2), hi2);
+  } else {
+    sm = limited_slope_d<R, TH1>(d0, d1, th);
+    s0 = limited_slope_d<R, TH1>(d1, d2, th);
+    sp = limited_slope_d<R, TH1>(d2, d3, th);
+  }
+}
+
 // a / b for b > 0 (face velocities: b is an extrapolated u^tau >= 1).  FP32: the fast hardware
 // division.  FP64, for b within [2^-125, 2^125): Newton-Raphson for 1/b from a single-precision
 // seed (b's leading 20 mantissa bits, approximate reciprocal: relative error ~2^-20), one step

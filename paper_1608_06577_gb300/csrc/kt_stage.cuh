@@ -110,8 +110,8 @@ __device__ __forceinline__ void face_velocities_inverted(const Params& P, const 
     const R a2 = ld<R>(p, c - 2 * s), a1 = ld<R>(p, c - s), a0 = ld<R>(p, c), b1 = ld<R>(p, c + s),
             b2 = ld<R>(p, c + 2 * s);
     const R d0 = a1 - a2, d1 = a0 - a1, d2 = b1 - a0, d3 = b2 - b1;
-    const R sm = limited_slope_d<R, TH1>(d0, d1, th), s0 = limited_slope_d<R, TH1>(d1, d2, th),
-            sp = limited_slope_d<R, TH1>(d2, d3, th);
+    R sm, s0, sp;
+    three_slopes<R, TH1>(d0, d1, d2, d3, th, sm, s0, sp);
     const R x[4] = {fma(h, sm, a1), fma(-h, s0, a0), fma(h, s0, a0), fma(-h, sp, b1)};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -177,10 +177,9 @@ __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, co
     const R up2t = ua(0, 2 * us), up2d = ua(D + 1, 2 * us);
     R t0 = um1[0] - um2t, t1 = u0t - um1[0], t2 = up1[0] - u0t, t3 = up2t - up1[0];
     R d0 = um1[D + 1] - um2d, d1 = u0d - um1[D + 1], d2 = up1[D + 1] - u0d, d3 = up2d - up1[D + 1];
-    const R st_m = limited_slope_d<R, TH1>(t0, t1, th), st_0 = limited_slope_d<R, TH1>(t1, t2, th),
-            st_p = limited_slope_d<R, TH1>(t2, t3, th);
-    const R sd_m = limited_slope_d<R, TH1>(d0, d1, th), sd_0 = limited_slope_d<R, TH1>(d1, d2, th),
-            sd_p = limited_slope_d<R, TH1>(d2, d3, th);
+    R st_m, st_0, st_p, sd_m, sd_0, sd_p;
+    three_slopes<R, TH1>(t0, t1, t2, t3, th, st_m, st_0, st_p);
+    three_slopes<R, TH1>(d0, d1, d2, d3, th, sd_m, sd_0, sd_p);
     const R h = R(0.5);
     vLm = vdiv(fma(h, sd_m, um1[D + 1]), fma(h, st_m, um1[0]));
     vLp = vdiv(fma(-h, sd_0, u0d), fma(-h, st_0, u0t));
@@ -258,8 +257,8 @@ __device__ __forceinline__ R component_flux(const R* p, int s, R a0, R th, const
     a2 = ld<R>(p, -2 * s); a1 = ld<R>(p, -s); b1 = ld<R>(p, s); b2 = ld<R>(p, 2 * s);
   }
   const R d0 = a1 - a2, d1 = a0 - a1, d2 = b1 - a0, d3 = b2 - b1;
-  const R sm = limited_slope_d<R, TH1>(d0, d1, th), s0 = limited_slope_d<R, TH1>(d1, d2, th),
-          sp = limited_slope_d<R, TH1>(d2, d3, th);
+  R sm, s0, sp;
+  three_slopes<R, TH1>(d0, d1, d2, d3, th, sm, s0, sp);
   const R slopes = fma(F.wLm, sm, fma(F.dW, s0, -F.wRp * sp));
   acc = fma(F.c0, a0, acc);
   acc = fma(F.wLm, a1, acc);
