@@ -296,6 +296,8 @@ def run_ours(args, world, rank, local):
                          "stats": st}
         if mode == args.mode:  # per-launch durations (CUDA events between launches, after the timed steps)
             results[mode]["slots_ms"] = kt.time_kernels(max(3, min(steps, 10)))
+            tu = kt.tuning()
+            results[mode]["tuning"] = {"tile": list(tu["block"]), "grid_blocks": tu["grid_blocks"]}
         del kt
         torch.cuda.empty_cache()
 
@@ -388,7 +390,8 @@ def run_ours(args, world, rank, local):
                                         f"zeta/s of Eq. (zetas), dtau 0.005 fm"),
                            "global_batch": world, "seq_len": None,
                            "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)",
-                           "mode": args.mode, "iface": args.iface, "eos": args.eos},
+                           "mode": args.mode, "iface": args.iface, "eos": args.eos,
+                           "tuning": main.get("tuning")},
                 "modes": {m: {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
                               "newton_iters_per_cell_stage": r["stats"]["newton_iters"] / ncs(r),
                               "fallbacks_per_cell_stage": r["stats"]["fallbacks"] / ncs(r)}
