@@ -229,7 +229,8 @@ int kt_time_kernels(kt_ctx* ctx, int n_steps, float* ms, int* n_kernels);
  *   x = [(ln E - 1)/6, M^2/E^2, 5 Pi/E, ln(1 - M^2/E^2)/2, e_conf/E, |M|/E],
  * e_conf = sqrt(4E^2 - 3M^2) - E the conformal root; output z, start e = e_conf exp(y/10) with
  * y = (M^2/E^2) z where M^2/E^2 > KT_MLP_GATE_R2, else y = 0 (the correction vanishes at rest,
- * where e_conf = E is the root).
+ * where e_conf = E is the root).  The network runs once per cell and step, in the first
+ * Runge-Kutta stage; the second stage applies the same z to its own E, M^2 and Pi.
  * At most 2 FP64 Newton steps follow; a cell whose residual |f(e)|/E then exceeds 1e-10 falls
  * back to the plain root-find.  Parameters: KT_MLP_NPARAM floats, layout as documented above
  * KT_MLP_NPARAM.  All pointers below are device pointers; work goes to `stream`. */

@@ -67,6 +67,7 @@ struct Ctx {
   Tile* d_tiles = nullptr;
   CUtensorMap* d_tmaps = nullptr;  // mixed precision: per event, the 4-d maps of qf (first nev) and qsf
   float* reg = nullptr;            // regulation factor of the last step, per cell (diagnostics)
+  float* z_net = nullptr;          // learned start: the network's output per cell within a step
   int max_tiles = 0;
   // work decomposition
   int shape = 0;
@@ -170,6 +171,7 @@ size_t state_bytes(const std::vector<Lattice>& lat, long long gs, size_t max_cel
   b += align_up((size_t)max_tiles * sizeof(Tile), 256);
   if (mixed) b += align_up(2 * lat.size() * sizeof(CUtensorMap), 256);
   b += align_up(fs * 4, 256);                  // regulation factors
+  b += align_up(fs * 4, 256);                  // network outputs (learned start)
   return b;
 }
 
@@ -430,6 +432,7 @@ UpdIO make_uio(Ctx* c, int stage) {
   u.counters = (unsigned long long*)(c->d_stat + 4);
   u.mlp_packed = c->learned ? c->d_mlp_packed : nullptr;
   u.reg_out = io.reg_out;
+  u.z_net = c->z_net;
   return u;
 }
 
@@ -856,6 +859,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   c->d_tiles = (Tile*)carve((size_t)c->max_tiles * sizeof(Tile));
   if (c->mixed) c->d_tmaps = (CUtensorMap*)carve(2 * c->lat.size() * sizeof(CUtensorMap));
   c->reg = (float*)carve(fs * 4);
+  c->z_net = (float*)carve(fs * 4);
   P.seg_d = c->seg_d;
   P.seg_f = c->seg_f;
 

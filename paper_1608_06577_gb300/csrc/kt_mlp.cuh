@@ -2,9 +2,9 @@
 //
 // A 6 -> 32 -> 32 -> 1 ReLU network predicts z, the correction y = 10 ln(e / e_conf) = r^2 z of
 // the conformal closed-form root e_conf = sqrt(4E^2 - 3M^2) - E of Sec. 2.4 (r^2 = M^2/E^2), for
-// cells with r^2 > kMlpGateR2 (below it y = 0).  Inference runs inside the stage kernel with
-// warp-level BF16 tensor-core MMAs (FP32 accumulation); the Newton steps that follow it and the
-// residual test are FP64.
+// cells with r^2 > kMlpGateR2 (below it y = 0).  Inference runs inside the first stage's update
+// kernel with warp-level BF16 tensor-core MMAs (FP32 accumulation); the second stage applies the
+// same z to its own features.  The Newton steps that follow and the residual test are FP64.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>

@@ -34,6 +34,7 @@ struct UpdIO {
   unsigned long long* counters;
   const uint32_t* mlp_packed;
   float* reg_out;           // stage 2: the regulation factor applied at each cell, or null
+  float* z_net;             // learned start: the network's output z per cell (stage 1 writes, stage 2 reads)
 };
 
 // inversion inputs of q: T^{tau mu} (0-3), pi^{tau mu} (4-7), Pi (14)
@@ -248,7 +249,9 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   const double gnn = P.milne ? tau_out * tau_out : 1.0;
   double start;
   if constexpr (LEARNED) {
-    start = learned_start(P, gnn, qn, s_mlp);
+    float z = (STAGE == 2 && valid) ? __ldg(io.z_net + c) : 0.f;
+    start = learned_start<STAGE == 1>(P, gnn, qn, s_mlp, z);
+    if (STAGE == 1 && valid) io.z_net[c] = z;
   } else {
     start = valid ? to_f64<float>(__ldg(io.e_guess + c)) : 1.0;
   }
@@ -355,8 +358,9 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     update_kernel(const Params P, const UpdIO io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
                   int ntiles) {
   unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
-  __shared__ uint32_t s_mlp[LEARNED ? PK_WORDS : 1];
-  if constexpr (LEARNED) {
+  constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
+  __shared__ uint32_t s_mlp[kInfer ? PK_WORDS : 1];
+  if constexpr (kInfer) {
     mlp_load_shared(s_mlp, io.mlp_packed);
     __syncthreads();
   }

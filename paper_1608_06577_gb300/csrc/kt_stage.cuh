@@ -730,22 +730,25 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
 }
 
 // The network's start for the root-find of the cell's new state qn (components 0-7 and 14 are
-// read): features in FP32, the warp-wide tensor-core inference of z, and the conformal root
-// corrected by y = r^2 z (r^2 = M^2/E^2, feature 1): e = E (e_conf/E) exp(y/10).  The correction
-// vanishes at rest, where e_conf = E is the root, and the network's BF16 error scales with it;
-// a warp whose cells all have r^2 <= kMlpGateR2 skips the inference.  All 32 lanes of the warp
-// call it together.  E, M^2 in single precision from the FP64 components (they only feed the
-// features).
+// read): features in FP32, the network's output z, and the conformal root corrected by
+// y = r^2 z (r^2 = M^2/E^2, feature 1): e = E (e_conf/E) exp(y/10).  The correction vanishes at
+// rest, where e_conf = E is the root, and the network's BF16 error scales with it.  The network
+// runs once per cell and step: with INFER (the first stage) the warp-wide tensor-core inference
+// gives z, which is returned in z_io (a warp whose cells all have r^2 <= kMlpGateR2 skips it);
+// otherwise (the second stage, whose state differs by O(dtau)) z_io holds that z on entry.  All
+// 32 lanes of the warp call it together.  E, M^2 in single precision from the FP64 components
+// (they only feed the features).
+template <bool INFER>
 __device__ __forceinline__ double learned_start(const Params& P, double gnn, const double (&qn)[NQ],
-                                                const uint32_t* s_mlp) {
+                                                const uint32_t* s_mlp, float& z_io) {
   const float Ef = d2f_bits(qn[0]) - d2f_bits(qn[4]);
   const float Mx = d2f_bits(qn[1]) - d2f_bits(qn[5]), My = d2f_bits(qn[2]) - d2f_bits(qn[6]),
               Mn = d2f_bits(qn[3]) - d2f_bits(qn[7]);
   const float M2f = fmaf(Mx, Mx, fmaf(My, My, d2f_bits(gnn) * Mn * Mn));
   float x[MLP_IN], ecE;
   mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_bits(qn[14]), x, ecE);
-  const float z = __any_sync(0xffffffffu, x[1] > kMlpGateR2) ? mlp_warp_infer(s_mlp, x) : 0.f;
-  const float y = (x[1] > kMlpGateR2) ? x[1] * z : 0.f;
+  if constexpr (INFER) z_io = __any_sync(0xffffffffu, x[1] > kMlpGateR2) ? mlp_warp_infer(s_mlp, x) : 0.f;
+  const float y = (x[1] > kMlpGateR2) ? x[1] * z_io : 0.f;
   return f2d_bits(Ef * ecE * __expf(0.1f * y));
 }
 
