@@ -69,3 +69,16 @@ def test_invalid_arguments_rejected(libpath):
     nb = ctypes.c_size_t()
     assert L.kt_state_bytes(ctypes.byref(binding.Grid(128, 128, 128)), None, ctypes.byref(nb)) == 0
     assert nb.value > 30 * 132 * 132 * 132 * 8
+
+
+def test_network_constants_agree():
+    """The gate of the learned start and the parameter count are written in the header, the
+    kernels and the Python training driver; they must agree."""
+    from paper_1608_06577_gb300 import binding, learned
+    hdr = open(os.path.join(ROOT, "include", "kt.h")).read()
+    cuh = open(os.path.join(ROOT, "paper_1608_06577_gb300", "csrc", "kt_mlp.cuh")).read()
+    gate_h = float(re.search(r"#define KT_MLP_GATE_R2\s+([0-9.eE+-]+)", hdr).group(1))
+    gate_k = float(re.search(r"kMlpGateR2\s*=\s*([0-9.eE+-]+)f", cuh).group(1))
+    assert gate_h == gate_k == learned.GATE_R2
+    npar_h = eval(re.search(r"#define KT_MLP_NPARAM\s+(\([^)]*\))", hdr).group(1))
+    assert npar_h == binding.MLP_NPARAM == 1313
