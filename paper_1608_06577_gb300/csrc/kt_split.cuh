@@ -262,10 +262,9 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   st |= invert_split<LEARNED>(P, gnn, qn, start, e, P0, uo, nit, nfb);
 
   // the FP32 copy read by the next stencil (and the remaining FP64 components in stage 2)
-  // Stage 2 with the plain root-find forms pi components 8-13 as f q^n + f dq in one FP64
-  // multiply-add once the regulation factor f is known; with the learned start the separate sum
-  // and product measured faster (the two instantiations allocate their registers differently).
-  constexpr bool kFusePi = (STAGE == 2) && !LEARNED;
+  // Stage 2 forms pi components 8-13 as f q^n + f dq in one FP64 multiply-add once the
+  // regulation factor f is known (measured faster than the separate sum and product).
+  constexpr bool kFusePi = (STAGE == 2);
   float qr[NQ];
   double q8[6];  // q^n and the increment of pi components 8-13 (kFusePi)
   float inc8[6];
