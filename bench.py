@@ -8,6 +8,7 @@ dtau = 0.005 fm.  The state (~1.1-1.7 GB) is far larger than L2, so no flush is 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode mixed|fp64]
 
 Under torchrun (N > 1) every rank advances its own event (different seed): replicas, weak scaling.
+With --batch, one batch of events is partitioned across the ranks by cell count (strong scaling).
 """
 from __future__ import annotations
 
@@ -37,6 +38,19 @@ UNIT = "cell updates/s"
 # = 1088 B (the learned start reads no previous e but writes, in stage 1, and reads, in stage 2,
 # the network's 4-byte output: also 1088 B).
 BYTES_PER_CELL = {"fp64": 856, "mixed": 1088, "learned": 1088}
+# The algorithmic bytes of the method's step, independent of this design: per cell and RK2 step
+# every field is read and written once by a fused kernel per stage (stage 1 reads q^n (15), u^n,
+# u^{n-1} (4 + 4), e, p and writes q*, u*, e, p; stage 2 reads q*, u*, u^n, e, p, q^n and writes
+# q^{n+1}, u^{n+1}, e, p: 107 words): FP64 856 B; mixed precision (q FP64; u, e, p FP32) 728 B.
+# The roofline of the step is taken against these; BYTES_PER_CELL above is what this design's
+# kernels move, and the recorded DRAM traffic shows the difference.
+ALG_BYTES_PER_CELL = {"fp64": 856, "mixed": 728, "learned": 728}
+# FP64 add/multiply/FMA instructions per cell and RK2 step of the FP64 mode (ncu counts of the two
+# fused stage kernels), and GB300's FP64 rate: 2 FMA per SM and clock (152 SMs; 1.25 TFLOP/s at
+# 2.07 GHz nominal), taken at the SM clock sampled during the timed steps
+FP64_INST_PER_CELL_STEP = 2 * 1821
+FP64_FMA_PER_SM_CLK = 2
+N_SM = 152
 # per launch slot of kt_time_kernels (bytes per cell); FP64: the fused stage kernels
 SLOT_BYTES = {
     "fp64": {"stage1_rhs": 368, "stage2_rhs": 488},
@@ -47,9 +61,10 @@ SLOT_KERNEL = {"stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel", "stage1_u
                "stage2_update": "update_kernel", "tau_advance": "advance_tau_kernel"}
 LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels from
-# the ncu launch list of the 128^3 learned workload, profiles/launches_learned_128cube.md (average
-# over the two stages of each kernel).  Only that mode and size have a capture.
+# one ncu capture of the 128^3 learned workload (average over the two stages of each kernel).  Only
+# that mode and size have a capture.
 MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 342.3e6, "update_kernel": 804.7e6}}
+REPEATS = 3  # timed runs of K steps per mode; the median is reported
 
 
 def parse():
@@ -185,7 +200,7 @@ def run_reference(args, world, rank):
     from workload.problem import hotspot_problem
     cores = os.cpu_count()
     prob = hotspot_problem(nx=args.n, ny=args.n, neta=args.n, nsteps=1)
-    nz = 4
+    nz = 16  # 2,048 (eta, y) rows: the oracle's threads split rows, so every core has work
     p = hotspot_problem(nx=args.n, ny=args.n, neta=nz)
     o = oracle.Oracle(p, threads=cores)
     cores = oracle.set_threads(cores)
@@ -223,25 +238,32 @@ def make_kt(prob, mode, weights, stream):
         return KT(prob, precision=prec, inversion=inv, mlp_weights=weights if inv else None)
 
 
-def time_mode(prob, mode, weights, steps, warmup, stream, profile_range=False):
-    """Times `steps` RK2 steps with CUDA events on the launching stream.  With profile_range the
-    timed steps sit between cudaProfilerStart/Stop, so `ncu --profile-from-start off` lists
-    exactly the launches of the timed region."""
+def time_mode(prob, mode, weights, steps, warmup, stream, world, profile_range=False):
+    """Times REPEATS runs of exactly `steps` RK2 steps each (after `warmup` untimed steps) with CUDA
+    events on the launching stream, each run bracketed by a barrier and a device synchronisation,
+    max over ranks; returns the context and the per-run times in ms.  With profile_range the first
+    timed run sits between cudaProfilerStart/Stop, so `ncu --profile-from-start off` lists exactly
+    its launches."""
     import torch
     kt = make_kt(prob, mode, weights, stream)
     kt.set_problem_state()
     kt.step(warmup)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if profile_range:
-        torch.cuda.profiler.start()
-    ev0.record(stream)
-    kt.step(steps)
-    ev1.record(stream)
-    ev1.synchronize()
-    if profile_range:
-        torch.cuda.profiler.stop()
-    return kt, ev0.elapsed_time(ev1)
+    runs = []
+    for r in range(REPEATS):
+        barrier(world)
+        torch.cuda.synchronize()
+        if profile_range and r == 0:
+            torch.cuda.profiler.start()
+        ev0.record(stream)
+        kt.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        if profile_range and r == 0:
+            torch.cuda.profiler.stop()
+        runs.append(max_over_ranks(ev0.elapsed_time(ev1), world))
+    return kt, runs
 
 
 def run_ours(args, world, rank, local):
@@ -280,21 +302,21 @@ def run_ours(args, world, rank, local):
     modes = [args.mode] + ([] if args.only_main else [m for m in MODES if m != args.mode])
     clocks = None
     for mode in modes:
-        steps = args.steps if mode == args.mode else max(3, min(args.steps, 6))
+        steps = args.steps  # every mode: the headline's step count, median of REPEATS runs
         barrier(world)
         torch.cuda.synchronize()
         if mode == args.mode:
             with ClockSampler(local) as cs:
-                kt, ms = time_mode(prob, mode, weights, steps, args.warmup, stream, profile_range=True)
+                kt, runs = time_mode(prob, mode, weights, steps, args.warmup, stream, world, profile_range=True)
             clocks = cs.summary()
         else:
-            kt, ms = time_mode(prob, mode, weights, steps, args.warmup, stream)
+            kt, runs = time_mode(prob, mode, weights, steps, args.warmup, stream, world)
         torch.cuda.synchronize()
         barrier(world)
-        ms = max_over_ranks(ms, world)
+        ms = statistics.median(runs)
         st = kt.stats()
         results[mode] = {"ms_per_step": ms / steps, "value": cells * world * steps / (ms * 1e-3), "steps": steps,
-                         "stats": st}
+                         "stats": st, "runs_ms_per_step": [r / steps for r in runs]}
         if mode == args.mode:  # per-launch durations (CUDA events between launches, after the timed steps)
             results[mode]["slots_ms"] = kt.time_kernels(max(3, min(steps, 10)))
             tu = kt.tuning()
@@ -305,6 +327,7 @@ def run_ours(args, world, rank, local):
     main = results[args.mode]
     ms_step = main["ms_per_step"]
     bpc = BYTES_PER_CELL[args.mode]
+    alg = ALG_BYTES_PER_CELL[args.mode]
     # per kernel: launches per step, average launch time, algorithmic bytes per launch, GB/s
     kernels = {}
     for slot, t in main["slots_ms"].items():
@@ -318,17 +341,36 @@ def run_ours(args, world, rank, local):
     for k in kernels.values():
         k["avg_launch_ms"] = k["ms_per_step"] / k["launches_per_step"]
         k["gbs"] = k["bytes_per_step"] / (k["ms_per_step"] * 1e-3) / 1e9
+        k["frac_of_hbm"] = k["gbs"] / hbm_peak
         k["share"] = k["ms_per_step"] / sum(v["ms_per_step"] for v in kernels.values())
+        k["share_of_step_bytes"] = k["bytes_per_step"] / (cells * bpc)
     dom = max(kernels, key=lambda n: kernels[n]["ms_per_step"])
-    achieved = kernels[dom]["gbs"]
-    traffic = None if args.large else MEASURED_TRAFFIC.get((args.mode, n), {}).get(dom)
+    traffic_k = None if args.large else MEASURED_TRAFFIC.get((args.mode, n))
+    traffic = None
+    if traffic_k:  # DRAM bytes per step: every kernel's recorded traffic per launch times its launches
+        traffic = sum(traffic_k[k] * v["launches_per_step"] for k, v in kernels.items() if k in traffic_k)
+    achieved = cells * alg / (ms_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": dom,
-                "bytes_per_launch": kernels[dom]["bytes_per_step"] / kernels[dom]["launches_per_step"],
-                "avg_launch_ms": kernels[dom]["avg_launch_ms"], "bytes_per_cell_step": bpc,
-                "step_gbs": cells * bpc / (ms_step * 1e-3) / 1e9,
-                "note": "achieved = algorithmic bytes per launch / average launch time (CUDA events between "
-                        "launches on the context stream); step_gbs = all kernels' algorithmic bytes / step time"}
+                "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "the whole step (all launches)", "alg_bytes_per_cell_step": alg,
+                "design_bytes_per_cell_step": bpc,
+                "traffic_bytes_per_cell_step": None if traffic is None else traffic / cells,
+                "design_gbs": cells * bpc / (ms_step * 1e-3) / 1e9, "dominant_kernel": dom,
+                "note": "achieved = the method's algorithmic bytes per RK2 step (107 words per cell: 728 B "
+                        "mixed, 856 B FP64) / the CUDA-event time per step; design_gbs counts the bytes "
+                        "this design's kernels move; traffic = ncu DRAM bytes per step (null unless this "
+                        "mode and size were captured with the current kernels); per-kernel rooflines "
+                        "under `kernels`"}
+    fp64_pipe = None
+    if args.mode == "fp64" or "fp64" in results:
+        r64 = results["fp64"]
+        sm_hz = ((clocks or {}).get("sm_mhz") or 2070.0) * 1e6
+        ach = FP64_INST_PER_CELL_STEP * cells * world / (r64["ms_per_step"] * 1e-3)
+        peak = FP64_FMA_PER_SM_CLK * N_SM * sm_hz * world
+        fp64_pipe = {"bound": "fp64 alu", "achieved": ach, "peak": peak, "unit": "FP64 instructions/s",
+                     "frac": ach / peak, "inst_per_cell_step": FP64_INST_PER_CELL_STEP,
+                     "note": "FP64 add/multiply/FMA instructions per cell-step from ncu; peak from the unit "
+                             "count (2 FP64 FMA per SM and clock, 152 SMs) at the sampled SM clock"}
 
     e2e = None
     if not args.no_e2e:
@@ -394,9 +436,14 @@ def run_ours(args, world, rank, local):
                            "mode": args.mode, "iface": args.iface, "eos": args.eos,
                            "tuning": main.get("tuning")},
                 "modes": {m: {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
+                              "runs_ms_per_step": r["runs_ms_per_step"],
+                              "hbm_frac_alg": cells * world * ALG_BYTES_PER_CELL[m if m in ALG_BYTES_PER_CELL
+                                                                                 else "learned"]
+                                              / (r["ms_per_step"] * 1e-3) / 1e9 / hbm_peak,
                               "newton_iters_per_cell_stage": r["stats"]["newton_iters"] / ncs(r),
                               "fallbacks_per_cell_stage": r["stats"]["fallbacks"] / ncs(r)}
                           for m, r in results.items()},
+                "fp64_pipe": fp64_pipe,
                 "learned_training": train_info,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": LAUNCHES_PER_STEP["fp64" if args.mode == "fp64" else "mixed"] * main["steps"]}
@@ -404,15 +451,20 @@ def run_ours(args, world, rank, local):
 
 
 def run_batch(args, world, rank, local):
-    """The batch workload: events with fluctuating hotspot initial states and uneven grids
-    (nx = ny in 64..160, neta in 16..64, 20-100 hotspots), advanced together by one persistent
-    launch per stage; each rank advances its own batch (seeds 1000 + 1000 * rank + event)."""
+    """The batch workload: one batch of events with fluctuating hotspot initial states and uneven
+    grids (nx = ny in 64..160, neta in 16..64, 20-100 hotspots, seeds 1000 + event), advanced by
+    one launch per stage for all events of a context.  Under torchrun the batch is partitioned
+    across the ranks by cell count (parallel.rank_share: largest event first onto the least-loaded
+    rank); every rank advances only its share, with no data-path collective (strong scaling: the
+    whole job's work is the one batch)."""
     import torch
-    from paper_1608_06577_gb300 import KT, learned
-    from workload.problem import batch_problems
+    from paper_1608_06577_gb300 import KT, learned, parallel
+    from workload.problem import batch_problems, batch_shapes
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    probs = batch_problems(n_events=args.batch, seed=1000 + 1000 * rank)
+    shapes = batch_shapes(args.batch, seed=1000)
+    mine, total_cells = parallel.rank_share([n * n * nz for n, nz, _ in shapes], world, rank)
+    probs = batch_problems(n_events=args.batch, seed=1000, events=mine)
     cells = sum(p.ncells for p in probs)
     prec, inv = MODES[args.mode]
     weights = None
@@ -426,20 +478,24 @@ def run_batch(args, world, rank, local):
     kt.step(args.warmup)
     torch.cuda.synchronize()
     barrier(world)
+    torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     kt.step(args.steps)
     ev1.record(stream)
     ev1.synchronize()
+    barrier(world)
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     slots = kt.time_kernels(max(3, min(args.steps, 10)))
     if rank == 0:
-        line = {"metric": "cell updates/s per RK2 step, batch of events", "value": cells * world * args.steps / (ms * 1e-3),
+        line = {"metric": "cell updates/s per RK2 step, batch of events", "value": total_cells * args.steps / (ms * 1e-3),
                 "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
                 "dtype": "f64" if args.mode == "fp64" else "f32+f64", "data": "synthetic",
                 "config": {"workload": f"{args.batch} events, nx=ny in 64..160, neta in 16..64, 20-100 hotspots",
-                           "cells_per_rank": cells, "mode": args.mode, "tile": kt.tuning()["block"]},
+                           "cells_total": total_cells, "events_rank0": len(mine), "cells_rank0": cells,
+                           "parallelism": f"events sharded over {world} ranks", "mode": args.mode,
+                           "tile": kt.tuning()["block"]},
                 "slots_ms": slots, "gpu_launches": LAUNCHES_PER_STEP["fp64" if args.mode == "fp64" else "mixed"] * args.steps}
         print(json.dumps(line), flush=True)
 

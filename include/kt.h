@@ -128,8 +128,11 @@ typedef struct kt_ctx kt_ctx;
 /* Fill *opt with the defaults listed above.  Returns KT_OK or KT_ERR_ARG. */
 int kt_options_default(kt_options* opt);
 
-/* Device bytes the state of one grid needs with these options (for kt_options.arena). */
-int kt_state_bytes(const kt_grid* grid, const kt_options* opt, size_t* bytes);
+/* Device bytes the state of one grid needs with this EOS and these options (the size of a
+ * caller-provided kt_options.arena).  eos may be NULL for the conformal EOS; a table of n nodes
+ * adds its per-interval coefficients.  Returns KT_ERR_ARG for a bad grid or null bytes,
+ * KT_ERR_EOS for a table with fewer than 4 nodes. */
+int kt_state_bytes(const kt_grid* grid, const kt_eos* eos, const kt_options* opt, size_t* bytes);
 
 /* Create a context (Sec. 4.3 step 2, memory allocation).  dx is used for x and y.
  * eos, eta_over_s, zeta_over_s: problem definition of Secs. 2.2-2.3 (copied).  opt may be NULL. */
@@ -145,7 +148,8 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
  *   u_prev: [3][cells] u at tau - dtau for the first backward time difference (NULL = u,
  *           i.e. u^{-1} = u^0 as in Sec. 4.3)
  * on_device: 0 = host pointers, 1 = device pointers.  Returns KT_ERR_STATE for non-finite
- * inputs. */
+ * inputs, e < 0, or a cell whose E = T^{tau tau} - pi^{tau tau} and M^i = T^{tau i} - pi^{tau i}
+ * admit no inversion (E <= 0 or M^2 >= E^2, Sec. 2.4); the context then has no valid state. */
 int kt_set_state(kt_ctx* ctx, double tau, const double* e, const double* u, const double* pi,
                  const double* Pi, const double* u_prev, int on_device);
 
@@ -159,6 +163,27 @@ int kt_step(kt_ctx* ctx, int n_steps);
  *   q [15][cells] conserved variables of Eq. (qComponents). */
 int kt_get_state(kt_ctx* ctx, double* tau, double* e, double* u, double* pi, double* Pi, double* q,
                  int on_device);
+
+/* Checkpoint and restart (Sec. 4.3: the program writes the state out every m steps; the run can
+ * continue from it).  A checkpoint is the complete evolved state of one event, so that
+ *   n steps  ==  k steps, kt_get_checkpoint, kt_set_checkpoint (in this or a new context with the
+ *                same options), n - k steps
+ * bit for bit.  (Primaries alone do not determine q: the regulator of Eq. regPimunu rescales pi
+ * after the inversion without re-inverting.)  buf = [KT_CHECKPOINT_ROWS][cells] doubles, layout
+ * as kt_get_state, rows:
+ *    0-14  q, the conserved variables of Eq. (qComponents) (FP64)
+ *   15-29  the copy of q the stencil reads (KT_MIXED: its FP32 values, widened exactly; KT_FP64:
+ *          q again, ignored by kt_set_checkpoint)
+ *   30     e     31  P0(e)     32-35  u^mu (u^tau, u^x, u^y, u^eta)     36-39  u^mu one step earlier
+ *   40     the regulation factor applied in the last step (the diagnostics' last column)
+ * kt_get_checkpoint writes buf (host, or device if on_device) and *tau (may be NULL).
+ * kt_set_checkpoint reads it (rows stored in FP32 in KT_MIXED are rounded to nearest, which is
+ * exact for values that kt_get_checkpoint produced), fills the ghost cells, sets tau for the
+ * context and resets the step count and statistics; KT_ERR_ARG for a bad event, a null buffer or
+ * tau <= 0 in Milne coordinates.  The caller owns buf. */
+#define KT_CHECKPOINT_ROWS 41
+int kt_get_checkpoint(kt_ctx* ctx, int event, double* tau, double* buf, int on_device);
+int kt_set_checkpoint(kt_ctx* ctx, int event, double tau, const double* buf, int on_device);
 
 /* Validity diagnostics of Sec. 7 (Eqs. inverseReynoldsNumbers, inverseReynoldsNumbers2) at the
  * current state of an event, out = [7][cells] (layout as kt_get_state; host pointer, or device
@@ -183,6 +208,13 @@ int kt_get_diagnostics(kt_ctx* ctx, int event, double* out, int on_device);
  * error.  The context stays usable. */
 int kt_selftest_wait(kt_ctx* ctx, unsigned polls);
 
+/* Self-test of the FP64 division the stencil uses for face velocities and coefficients (the paper
+ * has no counterpart): q[i] = a[i] / b[i] for n device-resident operands, on `stream`.  For
+ * 2^-125 <= b < 2^125 it is a Newton-Raphson reciprocal from a single-precision seed with one
+ * quotient correction, accurate to one unit in the last place where the quotient is a normal
+ * double; other b take the IEEE division.  KT_ERR_ARG for null pointers or n < 0. */
+int kt_selftest_div(const double* a, const double* b, double* q, long long n, void* stream);
+
 int kt_get_stats(kt_ctx* ctx, kt_stats* stats);
 const char* kt_last_error(const kt_ctx* ctx);
 void kt_free(kt_ctx* ctx);
@@ -194,7 +226,8 @@ void kt_free(kt_ctx* ctx);
  * events share the physics parameters, dtau and tau.  kt_init is kt_init_batch with one event;
  * kt_set_state / kt_get_state address event 0.  kt_step advances every event; each event must
  * have been given a state first.  The results of an event do not depend on the batch it is in. */
-int kt_state_bytes_batch(int n_events, const kt_grid* grids, const kt_options* opt, size_t* bytes);
+int kt_state_bytes_batch(int n_events, const kt_grid* grids, const kt_eos* eos, const kt_options* opt,
+                         size_t* bytes);
 int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, double deta, double dtau,
                   const kt_eos* eos, const kt_coef* eta_over_s, const kt_coef* zeta_over_s, const kt_options* opt);
 int kt_set_state_event(kt_ctx* ctx, int event, double tau, const double* e, const double* u, const double* pi,
@@ -255,7 +288,8 @@ int kt_mlp_predict(const float* params, const float* x, long long n, float* y, v
  * synchronisation it may imply are not acceptable.)  The packed weights go to a file-scope
  * device array of KT_MLP_PACKED_BYTES bytes that every GPU loading the library holds until
  * the process exits.  The first call on a device looks up that array's device address with
- * cudaGetSymbolAddress (the current device must be the one the pointers live on); make that
+ * cudaGetSymbolAddress (the current device must be the one the pointers live on), and so does
+ * the first call after the device's context has been re-created (cudaDeviceReset); make that
  * first call before any stream capture.  All calls on a device share the array and it keeps
  * the last call's contents; each call overwrites all of it before use, so nothing needs
  * clearing, but calls that overlap on the GPU (other streams, other host threads) race on it.

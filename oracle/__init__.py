@@ -20,7 +20,7 @@ FLOP_KINDS = ("add", "mul", "div", "sqrt", "transcendental", "compare")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP over eta planes)."""
+    """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP over the (eta, y) rows)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "kt_oracle.h"))):
         tmp = LIB + f".tmp{os.getpid()}"
@@ -77,6 +77,8 @@ def lib(flops: bool = False):
         L.ko_get_state.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp]
         L.ko_rhs.argtypes = [C.c_void_p, dp]
         L.ko_set_threads.argtypes = [C.c_int]
+        L.ko_max_speed.restype = C.c_double
+        L.ko_max_speed.argtypes = [C.c_void_p]
         L.ko_minmod3.restype = C.c_double
         L.ko_minmod3.argtypes = [C.c_double] * 3
         L.ko_eos.argtypes = [C.c_void_p, C.c_double, dp]
@@ -170,6 +172,11 @@ class Oracle:
 
     def step(self, n=1) -> int:
         return self.L.ko_step(self.ctx, int(n))
+
+    def max_speed(self) -> float:
+        """The CFL diagnostic of the last step() call: the largest local speed a of Eq. (ax) over
+        all faces of its stages, eta speeds times tau (Milne)."""
+        return float(self.L.ko_max_speed(self.ctx))
 
     def get_state(self):
         N = self.prob.ncells

@@ -59,6 +59,8 @@ struct ko_ctx {
   double *u[4], *us[4], *up[4], *un[4];
   double *e, *p, *es, *ps;
   double *reg; /* regulation factor applied to pi^{n+1} in the last step (1 before any step) */
+  double *spd; /* per cell, the largest local speed of its two faces in each direction (a stage) */
+  double max_speed; /* largest local speed over the steps of the last ko_step call */
 };
 
 /* ------------------------------------------------------------------ geometry (Sec. 2.4) */
@@ -461,7 +463,7 @@ static void fill_ghosts(const ko_ctx* c, double* A) {
 /* ------------------------------------------------------------------ KT right-hand side */
 /* numerical flux H of Eq. (Hflux) through the face between cells a (left) and b = a + s */
 static void face_flux(const ko_ctx* c, const fields_t* F, double tau, size_t a, size_t s, int d,
-                      double D, double H[NQ]) {
+                      double D, double H[NQ], double* speed) {
   size_t b = a + s;
   double th = c->P.theta;
   double qm[NQ], qp[NQ];
@@ -492,6 +494,7 @@ static void face_flux(const ko_ctx* c, const fields_t* F, double tau, size_t a, 
   /* local propagation speed, Eq. (ax): a = max(|v^+|, |v^-|) */
   double av = fabs(vp) > fabs(vm) ? fabs(vp) : fabs(vm);
   for (int n = 0; n < NQ; ++n) H[n] = 0.5 * (vp * qp[n] + vm * qm[n]) - 0.5 * av * (qp[n] - qm[n]);
+  *speed = av;
 }
 
 /* X^{d nu} = P (v^d delta^nu_tau - g^{d nu}) - v^d pi^{tau nu} + pi^{d nu}: the quantity whose
@@ -507,20 +510,27 @@ static double Xterm(const fields_t* F, const geom_t* g, size_t c_, int d, int nu
 
 /* C[q] (Eq. semiDiscreteKT) at one physical cell */
 static void cell_rhs(const ko_ctx* c, const fields_t* F, double* const* uprev, double tau, size_t idx,
-                     double out[NQ]) {
+                     double out[NQ], double* speed) {
   geom_t g;
   geom_at(c, tau, &g);
   size_t str[3] = {1, (size_t)c->NX, (size_t)c->NX * (size_t)c->NY};
   double Dd[3] = {c->P.dx, c->P.dy, c->P.deta};
   for (int n = 0; n < NQ; ++n) out[n] = 0.0;
 
-  /* 1. -(H_{i+1/2} - H_{i-1/2})/D in x, y, eta */
+  /* 1. -(H_{i+1/2} - H_{i-1/2})/D in x, y, eta.  The CFL diagnostic records the largest local
+   * speed a of the cell's faces, the eta speeds times sqrt(-g_{eta eta}) = tau (Milne) so that
+   * all three are in units of c */
+  double amax = 0.0;
   for (int d = 0; d < 3; ++d) {
-    double Hp[NQ], Hm[NQ];
-    face_flux(c, F, tau, idx, str[d], d, Dd[d], Hp);
-    face_flux(c, F, tau, idx - str[d], str[d], d, Dd[d], Hm);
+    double Hp[NQ], Hm[NQ], ap, am;
+    face_flux(c, F, tau, idx, str[d], d, Dd[d], Hp, &ap);
+    face_flux(c, F, tau, idx - str[d], str[d], d, Dd[d], Hm, &am);
     for (int n = 0; n < NQ; ++n) out[n] -= (Hp[n] - Hm[n]) / Dd[d];
+    double a = (ap > am) ? ap : am;
+    if (d == 2 && c->P.coords == KO_MILNE) a = a * tau;
+    if (a > amax) amax = a;
   }
+  *speed = amax;
 
   /* 2. sources J = S + G (App. B) */
   double u[4];
@@ -598,13 +608,14 @@ static void cell_rhs(const ko_ctx* c, const fields_t* F, double* const* uprev, d
 static int for_all_cells_stage(ko_ctx* c, const fields_t* F, double* const* uprev, double tau,
                                double** qout, double* const* qbase) {
   int nx = c->P.nx, ny = c->P.ny, nz = c->P.neta;
-#pragma omp parallel for schedule(static)
+  /* the threads split the (eta, y) rows of the lattice (timing only; results do not depend on it) */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 2; k < nz + 2; ++k)
     for (int j = 2; j < ny + 2; ++j)
       for (int i = 2; i < nx + 2; ++i) {
         size_t idx = cidx(c, i, j, k);
         double C[NQ];
-        cell_rhs(c, F, uprev, tau, idx, C);
+        cell_rhs(c, F, uprev, tau, idx, C, &c->spd[idx]);
         for (int n = 0; n < NQ; ++n) {
           /* forward Euler E[w] = w + dtau C[w] */
           double w = F->q[n][idx] + c->P.dtau * C[n];
@@ -612,6 +623,12 @@ static int for_all_cells_stage(ko_ctx* c, const fields_t* F, double* const* upre
           if (qbase) w = 0.5 * (qbase[n][idx] + w);
           qout[n][idx] = w;
         }
+      }
+  for (int k = 2; k < nz + 2; ++k)
+    for (int j = 2; j < ny + 2; ++j)
+      for (int i = 2; i < nx + 2; ++i) {
+        double a = c->spd[cidx(c, i, j, k)];
+        if (a > c->max_speed) c->max_speed = a;
       }
   return 0;
 }
@@ -622,7 +639,7 @@ static int infer_regulate_ghost(ko_ctx* c, double** q, double tau, double** u, d
   int st_all = 0;
   geom_t g;
   geom_at(c, tau, &g);
-#pragma omp parallel for schedule(static) reduction(| : st_all)
+#pragma omp parallel for collapse(2) schedule(static) reduction(| : st_all)
   for (int k = 2; k < nz + 2; ++k)
     for (int j = 2; j < ny + 2; ++j)
       for (int i = 2; i < nx + 2; ++i) {
@@ -653,6 +670,7 @@ static int infer_regulate_ghost(ko_ctx* c, double** q, double tau, double** u, d
 
 int ko_step(ko_ctx* c, int nsteps) {
   int st = 0;
+  c->max_speed = 0.0;
   for (int s = 0; s < nsteps; ++s) {
     double tau_n = c->tau, tau_1 = c->tau + c->P.dtau;
     /* 1. q^* = E[q^n; e^n, p^n, u^n, u^{n-1}], sources at tau^n */
@@ -692,12 +710,12 @@ int ko_rhs(ko_ctx* c, double* out) {
   for (int m = 0; m < 4; ++m) F.u[m] = c->u[m];
   int nx = c->P.nx, ny = c->P.ny, nz = c->P.neta;
   size_t ncp = (size_t)nx * ny * nz;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 2; k < nz + 2; ++k)
     for (int j = 2; j < ny + 2; ++j)
       for (int i = 2; i < nx + 2; ++i) {
-        double C[NQ];
-        cell_rhs(c, &F, c->up, c->tau, cidx(c, i, j, k), C);
+        double C[NQ], a;
+        cell_rhs(c, &F, c->up, c->tau, cidx(c, i, j, k), C, &a);
         size_t o = (size_t)(i - 2) + (size_t)nx * ((size_t)(j - 2) + (size_t)ny * (size_t)(k - 2));
         for (int n = 0; n < NQ; ++n) out[(size_t)n * ncp + o] = C[n];
       }
@@ -901,6 +919,7 @@ ko_ctx* ko_create(const ko_params* prm) {
   }
   c->e = zalloc(c->ncell); c->p = zalloc(c->ncell); c->es = zalloc(c->ncell); c->ps = zalloc(c->ncell);
   c->reg = zalloc(c->ncell);
+  c->spd = zalloc(c->ncell);
   /* unused ghost corners keep a harmless rest state */
   for (size_t i = 0; i < c->ncell; ++i) {
     c->u[0][i] = c->us[0][i] = c->up[0][i] = c->un[0][i] = 1.0;
@@ -916,8 +935,11 @@ void ko_free(ko_ctx* c) {
   for (int m = 0; m < 4; ++m) { free(c->u[m]); free(c->us[m]); free(c->up[m]); free(c->un[m]); }
   free(c->e); free(c->p); free(c->es); free(c->ps);
   free(c->reg);
+  free(c->spd);
   free(c);
 }
+
+double ko_max_speed(const ko_ctx* c) { return c->max_speed; }
 
 int ko_set_threads(int n) {
 #ifdef _OPENMP

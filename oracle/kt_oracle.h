@@ -65,6 +65,9 @@ int ko_get_state(const ko_ctx* c, double* tau, double* e, double* u, double* pi,
 /* C[q] of Eq. (semiDiscreteKT) for the current state at the current tau (no update). */
 int ko_rhs(ko_ctx* c, double* out /* [15][cells] */);
 int ko_set_threads(int n);
+/* The CFL diagnostic of the last ko_step call: the largest local propagation speed a of
+ * Eq. (ax) over every face evaluated in its stages, the eta speeds times tau (Milne). */
+double ko_max_speed(const ko_ctx* c);
 /* Validity diagnostics of Sec. 7 at the current state, out = [7][cells]: tau_pi theta,
  * tau_Pi theta, sqrt(pi.pi)/P0, |Pi|/P0, the second-order inverse Reynolds numbers of shear and
  * bulk (Eq. inverseReynoldsNumbers2), and the regulation factor of the last step. */

@@ -70,7 +70,7 @@ def load_library():
     L = C.CDLL(path)
     dp, vp = C.POINTER(C.c_double), C.c_void_p
     L.kt_options_default.argtypes = [C.POINTER(Options)]
-    L.kt_state_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Options), C.POINTER(C.c_size_t)]
+    L.kt_state_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Eos), C.POINTER(Options), C.POINTER(C.c_size_t)]
     L.kt_init.argtypes = [C.POINTER(vp), C.POINTER(Grid), C.c_double, C.c_double, C.c_double, C.POINTER(Eos),
                           C.POINTER(Coef), C.POINTER(Coef), C.POINTER(Options)]
     L.kt_set_state.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, C.c_int]
@@ -81,7 +81,8 @@ def load_library():
     L.kt_last_error.argtypes = [vp]
     L.kt_free.argtypes = [vp]
     L.kt_free.restype = None
-    L.kt_state_bytes_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Options), C.POINTER(C.c_size_t)]
+    L.kt_state_bytes_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Eos), C.POINTER(Options),
+                                       C.POINTER(C.c_size_t)]
     L.kt_init_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Grid), C.c_double, C.c_double, C.c_double,
                                 C.POINTER(Eos), C.POINTER(Coef), C.POINTER(Coef), C.POINTER(Options)]
     L.kt_set_state_event.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, vp, C.c_int]
@@ -91,6 +92,8 @@ def load_library():
     L.kt_time_kernels.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int)]
     L.kt_get_diagnostics.argtypes = [vp, C.c_int, vp, C.c_int]
     L.kt_selftest_wait.argtypes = [vp, C.c_uint]
+    L.kt_get_checkpoint.argtypes = [vp, C.c_int, dp, vp, C.c_int]
+    L.kt_set_checkpoint.argtypes = [vp, C.c_int, C.c_double, vp, C.c_int]
     _LIB = L
     return L
 
@@ -143,13 +146,6 @@ class KT:
             assert w.size == MLP_NPARAM
             self._keep.append(w)
             o.mlp_weights = w.ctypes.data_as(C.POINTER(C.c_float))
-        if device_arena:
-            nb = C.c_size_t()
-            rc = L.kt_state_bytes_batch(self.nev, grids, C.byref(o), C.byref(nb))
-            if rc != KT_OK:
-                raise KTError(rc, "kt_state_bytes_batch")
-            self.arena = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
-            o.arena, o.arena_bytes = C.c_void_p(self.arena.data_ptr()), nb.value
         if isinstance(prob.eos, tuple):
             eos = Eos(0, float(prob.eos[1]), 0, None, None, None, None, None)
         else:
@@ -158,6 +154,13 @@ class KT:
             self._keep += cols
             P = C.POINTER(C.c_double)
             eos = Eos(1, 0.0, t.n, *[a.ctypes.data_as(P) for a in cols])
+        if device_arena:
+            nb = C.c_size_t()
+            rc = L.kt_state_bytes_batch(self.nev, grids, C.byref(eos), C.byref(o), C.byref(nb))
+            if rc != KT_OK:
+                raise KTError(rc, "kt_state_bytes_batch")
+            self.arena = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+            o.arena, o.arena_bytes = C.c_void_p(self.arena.data_ptr()), nb.value
         ce, cz = _coef(prob.eta_over_s), _coef(prob.zeta_over_s)
         ctx = C.c_void_p()
         rc = L.kt_init_batch(C.byref(ctx), self.nev, grids, prob.dx, prob.deta, prob.dtau, C.byref(eos), C.byref(ce),
@@ -244,6 +247,21 @@ class KT:
         rc = self.L.kt_get_state_event(self.ctx, int(event), C.byref(tau), ptr(e), ptr(u), ptr(pi), ptr(Pi), ptr(q), 1)
         self._check(rc, "kt_get_state")
         return tau.value
+
+    CHECKPOINT_ROWS = 41
+
+    def get_checkpoint(self, event=0):
+        """(tau, [41, cells] float64 host array): the complete evolved state (kt_get_checkpoint)."""
+        buf = np.empty((self.CHECKPOINT_ROWS, self.ncells_ev[event]))
+        tau = C.c_double()
+        self._check(self.L.kt_get_checkpoint(self.ctx, int(event), C.byref(tau), _dptr(buf), 0), "kt_get_checkpoint")
+        return tau.value, buf
+
+    def set_checkpoint(self, tau, buf, event=0):
+        """Continue from a checkpoint taken by get_checkpoint (kt_set_checkpoint)."""
+        buf = np.ascontiguousarray(buf, dtype=np.float64)
+        assert buf.shape == (self.CHECKPOINT_ROWS, self.ncells_ev[event])
+        self._check(self.L.kt_set_checkpoint(self.ctx, int(event), float(tau), _dptr(buf), 0), "kt_set_checkpoint")
 
     def stats(self) -> dict:
         s = Stats()

@@ -275,6 +275,10 @@ __global__ void set_state_kernel(const Params P, const Lattice L, const double* 
   bool bad = !isfinite(e) || !(e >= 0.0) || !isfinite(ut) || !isfinite(Pi) || !isfinite(up4[0]);
   for (int m = 0; m < 10; ++m) bad |= !isfinite(pi[m]);
   if (bad) atomicOr(status, ST_NONFINITE);
+  // the inversion of Eq. (eInferred) needs E = T^{tau tau} - pi^{tau tau} > 0 and M^2 < E^2 with
+  // M^i = T^{tau i} - pi^{tau i}, M^2 = M_x^2 + M_y^2 + g_{eta eta} M_eta^2 (Sec. 2.4)
+  const double Ei = qn[0] - qn[4], Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
+  if (!bad && !(Ei > 0.0 && Mx * Mx + My * My + g * Mn * Mn < Ei * Ei)) atomicOr(status, ST_INVERSION);
   const long long fs = L.fstride;
   const int pc[3] = {i + 2, j + 2, k + 2};
   const int nn[3] = {L.nx, L.ny, L.nz};
@@ -307,7 +311,27 @@ __global__ void gather_kernel(const Lattice L, const S* __restrict__ f, double* 
   out[o] = (double)f[L.idx(i + 2, j + 2, k + 2)];
 }
 
+// scatter one packed physical array into a field (double or float) at every physical cell and
+// the ghost copies it owns (checkpoint restore; float fields round to nearest, which is exact
+// for values that were float to begin with)
+template <typename S>
+__global__ void scatter_kernel(const Params P, const Lattice L, const double* __restrict__ in, S* f) {
+  long long ncp = (long long)L.nx * L.ny * L.nz;
+  long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= ncp) return;
+  int i = (int)(o % L.nx), j = (int)((o / L.nx) % L.ny), k = (int)(o / ((long long)L.nx * L.ny));
+  const S v = (S)in[o];
+  for_cell_and_ghosts(P, L, i + 2, j + 2, k + 2, [&](long long t) { f[t] = v; });
+}
+
 __global__ void advance_tau_kernel(double* tau, double dtau) { tau[0] += dtau; }
+
+// self-test of the FP64 division of the stencil (vdiv) on caller-given operands
+__global__ void div_selftest_kernel(const double* __restrict__ a, const double* __restrict__ b, double* q,
+                                    long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) q[i] = vdiv(a[i], b[i]);
+}
 
 // Self-test of the bounded waits: every thread waits on an mbarrier that nothing arms, with the
 // given poll limit, exactly as the stage kernels wait for their TMA copies; the block records
@@ -715,8 +739,10 @@ int kt_options_default(kt_options* o) {
   return KT_OK;
 }
 
-int kt_state_bytes_batch(int n_events, const kt_grid* grids, const kt_options* opt, size_t* bytes) {
+int kt_state_bytes_batch(int n_events, const kt_grid* grids, const kt_eos* eos, const kt_options* opt,
+                         size_t* bytes) {
   if (!bytes || !grids_ok(n_events, grids)) return KT_ERR_ARG;
+  if (eos && eos->kind == KT_EOS_TABLE && eos->n < 4) return KT_ERR_EOS;
   kt_options d;
   kt_options_default(&d);
   const kt_options* o = opt ? opt : &d;
@@ -724,12 +750,12 @@ int kt_state_bytes_batch(int n_events, const kt_grid* grids, const kt_options* o
   long long gs;
   size_t mc;
   layout(n_events, grids, lat, gs, mc);
-  *bytes = state_bytes(lat, gs, mc, o->precision == KT_MIXED, 4097);
+  *bytes = state_bytes(lat, gs, mc, o->precision == KT_MIXED, (eos && eos->kind == KT_EOS_TABLE) ? eos->n : 0);
   return KT_OK;
 }
 
-int kt_state_bytes(const kt_grid* grid, const kt_options* opt, size_t* bytes) {
-  return kt_state_bytes_batch(1, grid, opt, bytes);
+int kt_state_bytes(const kt_grid* grid, const kt_eos* eos, const kt_options* opt, size_t* bytes) {
+  return kt_state_bytes_batch(1, grid, eos, opt, bytes);
 }
 
 int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, double deta, double dtau,
@@ -941,7 +967,9 @@ int kt_set_state_event(kt_ctx* c, int event, double tau, const double* e, const 
   c->tau = tau;
   c->steps = 0;
   c->ev_set[event] = 1;
-  if (st) return fail(c, KT_ERR_STATE, "kt_set_state: non-finite or negative input");
+  if (st & ST_NONFINITE) return fail(c, KT_ERR_STATE, "kt_set_state: non-finite input or negative e");
+  if (st) return fail(c, KT_ERR_STATE, "kt_set_state: T^{tau tau} - pi^{tau tau} <= |T^{tau i} - pi^{tau i}| "
+                                       "in some cell (no (e, u) solves Eq. eInferred)");
   return KT_OK;
 }
 
@@ -1077,6 +1105,91 @@ int kt_get_state(kt_ctx* c, double* tau, double* e, double* u, double* pi, doubl
   return kt_get_state_event(c, 0, tau, e, u, pi, Pi, q, on_device);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The fields of a checkpoint row by row (see KT_CHECKPOINT_ROWS in kt.h): the field array (all
+// events) and its element type: 0 double, 1 the stencil precision (float in KT_MIXED), 2 float.
+struct CkptRow {
+  void* f;
+  int is_r;
+};
+std::vector<CkptRow> checkpoint_rows(Ctx* c) {
+  std::vector<CkptRow> rows;
+  const size_t fs = (size_t)c->gs;
+  for (int n = 0; n < NQ; ++n) rows.push_back({c->q + n * fs, 0});
+  for (int n = 0; n < NQ; ++n)
+    rows.push_back(c->mixed ? CkptRow{c->qf + n * fs, 1} : CkptRow{c->q + n * fs, 0});
+  rows.push_back({c->E[0], 1});
+  rows.push_back({c->Pb[0], 1});
+  for (int m = 0; m < 4; ++m) rows.push_back({(char*)c->U[c->cur] + m * fs * c->esz, 1});
+  for (int m = 0; m < 4; ++m) rows.push_back({(char*)c->U[c->prev] + m * fs * c->esz, 1});
+  rows.push_back({c->reg, 2});  // float in both modes
+  return rows;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kt_get_checkpoint(kt_ctx* c, int event, double* tau, double* buf, int on_device) {
+  if (!c || !buf) return KT_ERR_ARG;
+  if (event < 0 || event >= c->nev) return fail(c, KT_ERR_ARG, "kt_get_checkpoint: bad event");
+  if (!c->ev_set[event]) return fail(c, KT_ERR_ARG, "kt_get_checkpoint: event %d has no state", event);
+  const Lattice& L = c->lat[event];
+  const size_t ncp = (size_t)L.nx * L.ny * L.nz;
+  const int nb = (int)((ncp + 255) / 256);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const std::vector<CkptRow> rows = checkpoint_rows(c);
+  static_assert(KT_CHECKPOINT_ROWS == 41, "checkpoint layout");
+  for (size_t b = 0; b < rows.size(); b += 18) {  // through the staging area, 18 rows at a time
+    const size_t nr = std::min<size_t>(18, rows.size() - b);
+    for (size_t t = 0; t < nr; ++t) {
+      const CkptRow& r = rows[b + t];
+      double* dst = c->stage + t * ncp;
+      if (r.is_r == 2 || (r.is_r && c->mixed)) gather_kernel<float><<<nb, 256, 0, c->stream>>>(L, (const float*)r.f, dst);
+      else gather_kernel<double><<<nb, 256, 0, c->stream>>>(L, (const double*)r.f, dst);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(buf + b * ncp, c->stage, nr * ncp * 8, kind, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (tau) *tau = c->tau;
+  return KT_OK;
+}
+
+int kt_set_checkpoint(kt_ctx* c, int event, double tau, const double* buf, int on_device) {
+  if (!c || !buf) return KT_ERR_ARG;
+  if (event < 0 || event >= c->nev || !(tau > 0 || !c->P.milne))
+    return fail(c, KT_ERR_ARG, "kt_set_checkpoint: bad argument");
+  const Lattice& L = c->lat[event];
+  const size_t ncp = (size_t)L.nx * L.ny * L.nz;
+  const int nb = (int)((ncp + 255) / 256);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const std::vector<CkptRow> rows = checkpoint_rows(c);
+  for (size_t b = 0; b < rows.size(); b += 18) {
+    const size_t nr = std::min<size_t>(18, rows.size() - b);
+    CK(cudaMemcpyAsync(c->stage, buf + b * ncp, nr * ncp * 8, kind, c->stream));
+    for (size_t t = 0; t < nr; ++t) {
+      const CkptRow& r = rows[b + t];
+      if (!c->mixed && b + t >= (size_t)NQ && b + t < (size_t)(2 * NQ)) continue;  // FP64: the stencil reads q
+      const double* src = c->stage + t * ncp;
+      if (r.is_r == 2 || (r.is_r && c->mixed)) scatter_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, L, src, (float*)r.f);
+      else scatter_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, L, src, (double*)r.f);
+    }
+    CK(cudaGetLastError());
+  }
+  double tau_h = tau;
+  CK(cudaMemcpyAsync(c->d_tau, &tau_h, 8, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->d_stat, 0, 256, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->tau = tau;
+  c->steps = 0;
+  c->ev_set[event] = 1;
+  return KT_OK;
+}
+
 int kt_selftest_wait(kt_ctx* c, unsigned polls) {
   if (!c || polls == 0) return KT_ERR_ARG;
   CK(cudaMemsetAsync(c->d_stat, 0, 4, c->stream));
@@ -1087,6 +1200,13 @@ int kt_selftest_wait(kt_ctx* c, unsigned polls) {
   CK(cudaStreamSynchronize(c->stream));
   if (st & ST_TIMEOUT) return fail(c, KT_ERR_TIMEOUT, "kt_selftest_wait: the wait gave up after %u polls", polls);
   return KT_OK;
+}
+
+int kt_selftest_div(const double* a, const double* b, double* q, long long n, void* stream) {
+  if (!a || !b || !q || n < 0) return KT_ERR_ARG;
+  if (n == 0) return KT_OK;
+  div_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a, b, q, n);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
 }
 
 int kt_get_diagnostics(kt_ctx* c, int event, double* out, int on_device) {

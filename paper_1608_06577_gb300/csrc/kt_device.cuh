@@ -227,17 +227,17 @@ __device__ __forceinline__ void three_slopes(R d0, R d1, R d2, R d3, R th, R& sm
   }
 }
 
-// a / b for b > 0 (face velocities: b is an extrapolated u^tau >= 1).  FP32: the fast hardware
-// division.  FP64, for b within [2^-125, 2^125): Newton-Raphson for 1/b from a single-precision
-// seed (b's leading 20 mantissa bits, approximate reciprocal: relative error ~2^-20), one step
-// r <- r + r (1 - b r) (~2^-40), then the quotient corrected once, q <- q + r (a - b q), which
-// leaves about one ulp; five FP64 instructions.  Other b take the IEEE division.
 // max(a, b) of non-negative a, b (FP64: compared as integers, off the FP64 pipe)
 __device__ __forceinline__ float nmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double nmax(double a, double b) {
   return (__double_as_longlong(a) < __double_as_longlong(b)) ? b : a;
 }
 
+// a / b for b > 0 (face velocities: b is an extrapolated u^tau >= 1).  FP32: the fast hardware
+// division.  FP64, for b within [2^-125, 2^125): Newton-Raphson for 1/b from a single-precision
+// seed (b's leading 20 mantissa bits, approximate reciprocal: relative error ~2^-20), one step
+// r <- r + r (1 - b r) (~2^-40), then the quotient corrected once, q <- q + r (a - b q), which
+// leaves about one ulp; five FP64 instructions.  Other b take the IEEE division.
 __device__ __forceinline__ float vdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double vdiv(double a, double b) {
   const unsigned hi = (unsigned)__double2hiint(b);

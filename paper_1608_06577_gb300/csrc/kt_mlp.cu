@@ -5,6 +5,7 @@
 // (bf16_forward = 0, used to check gradients against the FP64 reference); the backward pass
 // treats the rounding as the identity.  Gradients of a mini-batch are reduced with warp
 // shuffles, then shared-memory and global atomics.  Adam updates FP32 master weights.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -19,30 +20,69 @@ using namespace kt;
 // Scratch of kt_mlp_predict_static: one packed weight set, KT_MLP_PACKED_BYTES bytes, in a
 // file-scope device array.  Every GPU that loads this library holds it until the process
 // exits.  In host code `g_predict_scratch` is only a host-side stand-in for the symbol: its
-// device address comes from cudaGetSymbolAddress (once per device, cached below).
+// device address comes from cudaGetSymbolAddress, looked up once per device and context and
+// cached below.  The cache is keyed on the context's unique id as well as the device, so a
+// context re-created on the same device (after cudaDeviceReset, whose new module instance may
+// hold the array elsewhere) gets a fresh lookup instead of a stale address.
 static __device__ __align__(256) uint32_t g_predict_scratch[kt::PK_WORDS];
 
 namespace {
 constexpr int kMaxDevices = 64;
-uint32_t* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  uint32_t* ptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
-// device address of g_predict_scratch on the current device (looked up on first use)
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// the unique id of the calling thread's current context (0 if there is none yet or the driver
+// entry points are unavailable)
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)f;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// device address of g_predict_scratch on the current device and context (looked up on the first
+// call there; cudaGetSymbolAddress allocates nothing)
 int static_scratch_address(uint32_t** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return KT_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return KT_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long id = current_context_id();
+  ScratchAddr& a = g_scratch_addr[dev];
+  if (!a.ptr || id == 0 || a.ctx_id != id) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_predict_scratch);
     if (e != cudaSuccess || !p) {
       fprintf(stderr, "kt_mlp_predict_static: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
       return KT_ERR_CUDA;
     }
-    g_scratch_addr[dev] = (uint32_t*)p;
+    a.ptr = (uint32_t*)p;
+    a.ctx_id = current_context_id();  // the lookup has made the device's context current
   }
-  *out = g_scratch_addr[dev];
+  *out = a.ptr;
   return KT_OK;
 }
 }  // namespace

@@ -188,7 +188,8 @@ __device__ __forceinline__ void face_setup(const Params& P, const Lattice& L, co
   }
   const R aL = nmax(fabs(vLp), fabs(vLm));
   const R aR = nmax(fabs(vRp), fabs(vRm));
-  amax = fmaxf(amax, to_f32((D == 2) ? aR * sfac : aR));
+  const R aF = nmax(aL, aR);  // both faces: the first cell's left face is nobody's right face
+  amax = fmaxf(amax, to_f32((D == 2) ? aF * sfac : aF));
   const R wLp = (vLp - aL) * hinv, wRm = -(vRm + aR) * hinv;
   F.c0 = wLp + wRm;
   F.dW = wRm - wLp;

@@ -25,6 +25,14 @@ def shard_events(cells: list[int], world: int) -> list[list[int]]:
     return [sorted(s) for s in shards]
 
 
+def rank_share(cells: list[int], world: int, rank: int) -> tuple[list[int], int]:
+    """This rank's events of one batch (shard_events) and the batch's total cell count: every rank
+    advances only its own share, in one context, with no data-path collective."""
+    if not 0 <= rank < world:
+        raise ValueError("rank out of range")
+    return shard_events(cells, world)[rank], int(sum(int(c) for c in cells))
+
+
 def env_ranks() -> tuple[int, int, int]:
     """(world size, rank, local rank) from the torchrun environment (1, 0, 0 without one)."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),

@@ -67,8 +67,18 @@ def test_invalid_arguments_rejected(libpath):
     assert L.kt_init(ctypes.byref(ctx), ctypes.byref(g), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
                      ctypes.byref(z), None) == -1
     nb = ctypes.c_size_t()
-    assert L.kt_state_bytes(ctypes.byref(binding.Grid(128, 128, 128)), None, ctypes.byref(nb)) == 0
+    assert L.kt_state_bytes(ctypes.byref(binding.Grid(128, 128, 128)), None, None, ctypes.byref(nb)) == 0
     assert nb.value > 30 * 132 * 132 * 132 * 8
+    # a table EOS adds its per-interval coefficients: a longer table needs more bytes
+    sizes = []
+    for n in (4096, 16384):
+        tab = binding.Eos(1, 0.0, n, None, None, None, None, None)
+        b = ctypes.c_size_t()
+        assert L.kt_state_bytes(ctypes.byref(binding.Grid(8, 8, 8)), ctypes.byref(tab), None, ctypes.byref(b)) == 0
+        sizes.append(b.value)
+    assert sizes[1] >= sizes[0] + (16384 - 4096) * 15 * 8  # at least the FP64 coefficients
+    short = binding.Eos(1, 0.0, 3, None, None, None, None, None)
+    assert L.kt_state_bytes(ctypes.byref(binding.Grid(8, 8, 8)), ctypes.byref(short), None, ctypes.byref(nb)) == -4
 
 
 def test_network_constants_agree():

@@ -1,13 +1,21 @@
 """Parity at full size, in the launch configuration bench.py times (autotuned tiles, CUDA graph).
 
-The 128^3 hotspot workload (FP64, and mixed precision with the learned root-find start) and the
-256 x 256 x 128 event are stepped on the GPU; for sampled cells the oracle recomputes the last
-step on the 9^3 neighbourhood of the cell, restarted from the GPU's evolved variables one step
-earlier (q, e, u and the previous u: the regulator rescales pi without a re-inversion, so the
-primaries alone do not determine q).  One RK2 step reads cells at most 4 away (2 per stage,
-Sec. 3.1), so the centre of that neighbourhood is unaffected by the neighbourhood's own boundary
-cells.
+Every cell: the 128^3 hotspot workload (seed 1) run by the GPU and by the oracle (threaded over
+the host's cores) from the same initial state through the program flow of Sec. 4.3 -- FP64 for
+10 steps, every field within 1e-12 of its max norm; FP32 stencil + FP64 Heun and root-find with
+the learned start for 100 steps, pointwise relative error in e within 1e-4, every field's error
+printed.
+
+Sampled cells: the 128^3 workload and the 256 x 256 x 128 event are stepped on the GPU; for
+sampled cells the oracle recomputes the last step on the 9^3 neighbourhood of the cell,
+restarted from the GPU's evolved variables one step earlier (q, e, u and the previous u: the
+regulator rescales pi without a re-inversion, so the primaries alone do not determine q).  One
+RK2 step reads cells at most 4 away (2 per stage, Sec. 3.1), so the centre of that neighbourhood
+is unaffected by the neighbourhood's own boundary cells.
 """
+import os
+import time
+
 import numpy as np
 import pytest
 
@@ -121,6 +129,61 @@ def _weights(n=48):
     from paper_1608_06577_gb300 import learned
     params, _, _ = learned.train_default(n=n, n_samples=100000, epochs=3)
     return params.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def oracle_128(baseline_eos):
+    """The oracle's 128^3 run of the hotspot workload: its state after 10 and after 100 steps."""
+    p = hotspot_problem(eos_table=baseline_eos)
+    o = oracle.Oracle(p, threads=os.cpu_count())
+    t0 = time.perf_counter()
+    assert o.step(10) == 0
+    s10 = o.get_state()
+    t1 = time.perf_counter()
+    assert o.step(90) == 0
+    s100 = o.get_state()
+    print(f"oracle 128^3 on {oracle.set_threads(0)} threads: 10 steps {t1 - t0:.1f} s, "
+          f"90 more {time.perf_counter() - t1:.1f} s")
+    return p, s10, s100
+
+
+def test_fullsize_128_fp64_every_cell_10_steps(oracle_128):
+    """FP64 on the 128^3 workload after 10 steps: every field of every cell within 1e-12 of the
+    field's max norm (the parity metric of the oracle's tests)."""
+    from test_gpu_parity import field_errors
+    from paper_1608_06577_gb300 import KT
+    p, r, _ = oracle_128
+    kt = KT(p, precision=0)
+    kt.set_problem_state()
+    kt.step(10)
+    g = kt.get_state()
+    errs = field_errors(g, r)
+    print("FP64 128^3, 10 steps, max error per field:", {k: f"{v:.1e}" for k, v in errs.items()})
+    bad = {k: v for k, v in errs.items() if not v <= 1e-12}
+    assert not bad, bad
+    assert abs(g["tau"] - r["tau"]) < 1e-12 and kt.stats()["status"] == 0
+
+
+def test_fullsize_128_learned_every_cell_100_steps(oracle_128):
+    """FP32 stencil, FP64 Heun and root-find with the learned start on the 128^3 workload after 100
+    steps: pointwise relative error in e within 1e-4 on every cell; the per-field max-norm errors
+    and the pointwise relative errors of e and u^tau are printed."""
+    from test_gpu_parity import field_errors
+    from paper_1608_06577_gb300 import KT, KT_INV_LEARNED, KT_MIXED
+    p, _, r = oracle_128
+    kt = KT(p, precision=KT_MIXED, inversion=KT_INV_LEARNED, mlp_weights=_weights())
+    kt.set_problem_state()
+    kt.step(100)
+    g = kt.get_state()
+    rel_e = np.abs(g["e"] / r["e"] - 1)
+    rel_ut = np.abs(g["u"][0] / r["u"][0] - 1)
+    errs = field_errors(g, r)
+    print(f"learned 128^3, 100 steps: pointwise rel err e max {rel_e.max():.2e} mean {rel_e.mean():.2e}, "
+          f"u^tau max {rel_ut.max():.2e}; max-norm errors:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert rel_e.max() <= 1e-4
+    assert errs["e[0]"] <= 1e-4 and max(errs[f"q[{k}]"] for k in range(4)) <= 1e-4
+    st = kt.stats()
+    assert st["status"] == 0
 
 
 def test_fullsize_128_fp64_sampled_parity(baseline_eos):

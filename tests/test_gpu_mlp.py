@@ -122,29 +122,72 @@ def test_training_reduces_loss(trained):
     assert rms < 0.5 * float(Y.double().pow(2).mean().sqrt().item())
 
 
+def _newton_counts(p, params, nsteps):
+    """Newton steps and fallbacks per cell-stage with the trained network, with the network
+    switched off (all-zero weights: the start is the conformal root e_conf it corrects), and with
+    the plain root-find (previous e, full-precision stop), plus the learned run's state."""
+    from paper_1608_06577_gb300 import KT, KT_INV_LEARNED, KT_MIXED
+    ncs = p.ncells * 2 * nsteps
+    out = {}
+    for name, w in (("trained", params), ("network_off", np.zeros_like(params)), ("plain", None)):
+        kw = {"precision": KT_MIXED}
+        if w is not None:
+            kw.update(inversion=KT_INV_LEARNED, mlp_weights=w)
+        kt = KT(p, **kw)
+        kt.set_problem_state()
+        kt.step(nsteps)
+        st = kt.stats()
+        out[name] = (st["newton_iters"] / ncs, st["fallbacks"] / ncs)
+        if name == "trained":
+            out["state"] = kt.get_state(fields=("e", "u"))
+    return out
+
+
 def test_learned_inversion_accuracy_and_gain(trained):
-    """Mixed precision with the learned start vs the oracle after 40 steps (held-out seed),
-    and what it gains over the plain start: Newton steps per cell and stage."""
-    from paper_1608_06577_gb300 import KT, KT_MIXED, KT_INV_LEARNED
+    """Mixed precision with the learned start vs the oracle after 40 steps (held-out seed), and
+    what the trained network gains: Newton steps per cell-stage against the same method with the
+    network switched off (the conformal start e_conf alone) and against the plain root-find.
+
+    Measured result: the trained network does not beat its own conformal start here.  The
+    learned path accepts a root at |f| <= 1e-10 E, which one Newton step from any start within
+    ~1e-5 of the root reaches; e_conf is already that close in most cells (M^2/E^2 is small in
+    this workload), and a BF16 network cannot bring a start within 1e-10, so both need one step
+    in nearly every cell.  The test therefore asserts only that the network costs at most 5% more
+    steps than the conformal start, while both beat the plain root-find by a wide margin."""
     params, _, _, _ = trained
     p = _small(4)
-    ktl = KT(p, precision=KT_MIXED, inversion=KT_INV_LEARNED, mlp_weights=params.cpu().numpy())
-    ktl.set_problem_state()
-    ktl.step(40)
-    sl = ktl.stats()
-    g = ktl.get_state(fields=("e", "u"))
-    ktp = KT(p, precision=KT_MIXED)
-    ktp.set_problem_state()
-    ktp.step(40)
-    sp = ktp.stats()
+    c = _newton_counts(p, params.cpu().numpy(), 40)
     o = oracle.Oracle(p)
     o.step(40)
-    r = o.get_state()
-    rel = np.max(np.abs(g["e"] / r["e"] - 1))
-    ncs = p.ncells * 2 * 40
-    it_l, it_p = sl["newton_iters"] / ncs, sp["newton_iters"] / ncs
-    fb = sl["fallbacks"] / ncs
-    print(f"learned: rel err e {rel:.2e}, Newton/cell-stage {it_l:.3f} (plain {it_p:.3f}), fallback rate {fb:.2e}")
+    rel = np.max(np.abs(c["state"]["e"] / o.get_state()["e"] - 1))
+    (it_l, fb), (it_off, fb_off), (it_p, _) = c["trained"], c["network_off"], c["plain"]
+    print(f"learned: rel err e {rel:.2e}; Newton/cell-stage trained {it_l:.3f} (fallbacks {fb:.2e}), "
+          f"network off {it_off:.3f} (fallbacks {fb_off:.2e}), plain {it_p:.3f}")
     assert rel < 1e-4
     assert fb < 0.02
-    assert it_l < it_p
+    assert it_l < 0.5 * it_p and it_off < 0.5 * it_p
+    assert it_l <= 1.05 * it_off
+
+
+def test_learned_start_near_tc_on_the_lattice_eos():
+    """Where a start matters more: the paper's lattice EOS (Sec. 2.3), whose c_s^2 dips far below
+    1/3 near T_c so that e_conf is a worse start, with eta/s = 0.2 and the zeta/s of Eq. (zetas).
+    The network is trained on that EOS's own trajectories (other seeds) and compared with the
+    conformal start and the plain root-find on a held-out event; the counts are printed and the
+    same bounds as on the workload EOS are asserted."""
+    from paper_1608_06577_gb300 import learned
+    from workload.eos import lattice_table
+    tab = lattice_table()
+
+    def prob(seed):
+        return hotspot_problem(nx=40, ny=40, neta=16, nhot=10, seed=seed, r_max=1.2, eta_over_s=0.2, zeta="paper",
+                               eos_table=tab)
+    X, Y = learned.collect(prob, [2, 5, 6], 150_000, steps=40, every=4)
+    params, _ = learned.train(*learned.network_targets(X, Y), epochs=12, batch=4096)
+    c = _newton_counts(prob(4), params.cpu().numpy(), 40)
+    (it_l, fb), (it_off, _), (it_p, _) = c["trained"], c["network_off"], c["plain"]
+    print(f"lattice EOS: Newton/cell-stage trained {it_l:.3f} (fallbacks {fb:.2e}), network off {it_off:.3f}, "
+          f"plain {it_p:.3f}")
+    assert fb < 0.02
+    assert it_l < 0.5 * it_p
+    assert it_l <= 1.05 * it_off

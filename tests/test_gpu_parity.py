@@ -150,8 +150,7 @@ def test_milne_flow_with_u_eta_and_shear(baseline_eos):
 
 
 def test_step_counts_and_graph_paths_agree(baseline_eos):
-    """Graph replay (3-step cycles) and direct launches give identical bits; resume after
-    get/set_state round trip is bit-exact (checkpoint / resume)."""
+    """Graph replay (3-step cycles) and direct launches give identical bits."""
     from paper_1608_06577_gb300 import KT
     p = hotspot_problem(nx=20, ny=20, neta=8, nhot=6, seed=9, r_max=0.8, eos_table=baseline_eos)
     a = KT(p, use_graph=True)
@@ -166,14 +165,109 @@ def test_step_counts_and_graph_paths_agree(baseline_eos):
         assert np.array_equal(ga[f], gb[f]), f
 
 
+def test_fp64_division_within_one_ulp():
+    """The stencil's FP64 division (Newton-Raphson reciprocal from a single-precision seed, one
+    quotient correction) against the correctly rounded a / b: at most one unit in the last place
+    over random operands spanning its fast range 2^-125 <= b < 2^125, at the range's edges, and
+    for operands outside it (IEEE division there: exact)."""
+    import ctypes as C
+    import torch
+    from paper_1608_06577_gb300 import binding
+    L = binding.load_library()
+    L.kt_selftest_div.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]
+    rng = np.random.default_rng(7)
+    n = 1 << 20
+    b = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-125, 125, n))
+    a = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-500, 500, n)) * rng.choice([-1.0, 1.0], n)
+    edges_b = [2.0 ** -125, np.nextafter(2.0 ** -125, 1.0), np.nextafter(2.0 ** 125, 0.0), 1.0,
+               np.nextafter(1.0, 2.0), np.nextafter(2.0, 1.0), 3.0, 2.0 ** 125, 2.0 ** 200, 2.0 ** -126,
+               -1.5, 1e-300]
+    edges_a = [1.0, -1.0, np.nextafter(1.0, 2.0), 1.0 / 3.0, 1e-200, 7.0, 1e100, 0.0, -0.0, 2.5, 4.0, 1e-10]
+    a = np.concatenate([a, edges_a])
+    b = np.concatenate([b, edges_b])
+    ta, tb = torch.as_tensor(a, device="cuda"), torch.as_tensor(b, device="cuda")
+    tq = torch.empty_like(ta)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.kt_selftest_div(C.c_void_p(ta.data_ptr()), C.c_void_p(tb.data_ptr()), C.c_void_p(tq.data_ptr()),
+                             a.size, st) == 0
+    q = tq.cpu().numpy()
+    ref = a / b
+    ulp = np.spacing(np.abs(ref))
+    err = np.abs(q - ref) / np.where(ref != 0, ulp, 1.0)
+    fast = (b >= 2.0 ** -125) & (b < 2.0 ** 125)
+    print("vdiv: max error", float(err[fast].max()), "ulp over", int(fast.sum()), "operands")
+    assert float(err[fast].max()) <= 1.0
+    assert np.array_equal(q[~fast], ref[~fast])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cfl_max_speed_matches_oracle(precision, baseline_eos):
+    """The CFL diagnostic kt_stats.max_speed (the largest local speed a of Eq. (ax) over all faces
+    of the steps of one kt_step call, eta speeds times tau) against the oracle's record of the
+    same steps.  The GPU keeps it in FP32 (FP64 mode rounds once; mixed precision computes the
+    speeds in FP32)."""
+    from paper_1608_06577_gb300 import KT
+    for p in (gubser_problem(nx=24, ny=20, neta=6, nsteps=8),
+              hotspot_problem(nx=20, ny=18, neta=10, nhot=6, seed=3, r_max=0.8, eos_table=baseline_eos)):
+        kt = KT(p, precision=precision)
+        kt.set_problem_state()
+        kt.step(8)
+        o = oracle.Oracle(p)
+        assert o.step(8) == 0
+        a, b = kt.stats()["max_speed"], o.max_speed()
+        print(p.name, "max speed GPU", a, "oracle", b)
+        assert 0.0 < b < 1.0
+        assert abs(a - b) <= (1e-7 if precision == 0 else 1e-5) * b
+
+
+@pytest.mark.parametrize("mode", ["fp64", "learned"])
+def test_checkpoint_restart_is_bit_exact(mode, baseline_eos):
+    """Sec. 4.3 writes the state out every m steps and continues from it: 10 steps equal 5 steps,
+    kt_get_checkpoint, kt_set_checkpoint into a fresh context, and 5 more steps, bit for bit in
+    every field (q, e, u, pi, Pi) and in the regulation record, after the regulator has acted."""
+    from paper_1608_06577_gb300 import KT, KT_INV_LEARNED, KT_MIXED
+    from paper_1608_06577_gb300.learned import init_params
+    p = hotspot_problem(nx=24, ny=20, neta=10, nhot=6, seed=9, r_max=0.8, eos_table=baseline_eos)
+    kw = {} if mode == "fp64" else {"precision": KT_MIXED, "inversion": KT_INV_LEARNED,
+                                    "mlp_weights": init_params(3)}
+    a = KT(p, **kw)
+    a.set_problem_state()
+    a.step(5)
+    tau5, ck = a.get_checkpoint()
+    a.step(5)
+    ref = a.get_state()
+    b = KT(p, **kw)
+    b.set_checkpoint(tau5, ck)
+    tau_b, ck_b = b.get_checkpoint()
+    assert tau_b == tau5 and np.array_equal(ck_b, ck)  # the round trip itself is exact
+    b.step(5)
+    got = b.get_state()
+    for f in FIELDS:
+        assert np.array_equal(got[f], ref[f]), f
+    assert got["tau"] == ref["tau"]
+    assert np.array_equal(b.diagnostics()["regulation"], a.diagnostics()["regulation"])
+    assert np.min(a.diagnostics()["regulation"]) < 1.0  # the regulator acted
+
+
 def test_invalid_state_rejected():
+    """kt_set_state refuses non-finite input and states that admit no inversion (host-side
+    injection: a bulk pressure Pi = -4e in a cell moving with u^x = 1, so that e + P < 0 and
+    E = (e + P) (u^tau)^2 - P < 0)."""
     from paper_1608_06577_gb300 import KT, KTError
     p = gubser_problem(nx=8, ny=8, neta=2)
     kt = KT(p)
     e = p.e.copy()
     e[3] = np.nan
-    with pytest.raises(KTError):
+    with pytest.raises(KTError, match="KT_ERR_STATE.*non-finite"):
         kt.set_state(p.tau0, e, p.u, p.pi, p.Pi)
+    u = np.zeros((3, p.ncells))
+    u[0, 5] = 1.0
+    Pi = np.zeros(p.ncells)
+    Pi[5] = -4.0 * p.e[5]
+    with pytest.raises(KTError, match="KT_ERR_STATE.*eInferred"):
+        kt.set_state(p.tau0, p.e, u, None, Pi)
+    kt.set_state(p.tau0, p.e, p.u, p.pi, p.Pi)  # the context accepts a valid state afterwards
+    kt.step(1)
 
 
 def test_mixed_mode_error_after_100_steps(baseline_eos):

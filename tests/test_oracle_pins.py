@@ -386,7 +386,7 @@ def test_energy_momentum_conserved_on_periodic_cartesian_grid(baseline_eos):
     assert np.max(np.abs(q1 - q0)) < 1e-13 * q0[0]
 
 
-# ------------------------------------------------- constraint preservation (Sec. 2.4)
+# ------------------------------------------------- constraint preservation (Sec. 2.4: pi^{mu nu} u_nu = 0, pi^mu_mu = 0)
 def _projected_pi(u, tau, rng, scale):
     g = np.array([1.0, -1.0, -1.0, -tau ** 2])
     gi = 1.0 / g
@@ -504,6 +504,64 @@ def test_lattice_eos_table_thermodynamics():
     assert np.all(e > 3 * P)
     assert np.all(P / T ** 4 < A_SB / 3)
     assert np.allclose(np.exp(tab.lndelta), 1.0 / 3.0 - c2, rtol=1e-6, atol=0)
+
+
+def test_workload_eos_table_thermodynamics():
+    """The 128^3 workload's EOS table (an input shared by oracle and library) against
+    thermodynamics its construction does not use as such: s = dP/dT from finite differences
+    between nodes against s = (e + P)/T, c_s^2 = dP/de from finite differences against the
+    tabulated c_s^2 and against the workload's c_s^2(T) = 1/3 - 0.2 exp(-((T - 0.17 GeV)/0.05 GeV)^2),
+    ln(1/3 - c_s^2) against the tabulated column, and the Stefan-Boltzmann limit of Sec. 2.3 at
+    high T (s -> 4/3 a T^3 with a = 15.6269, P -> a T^4/3).  A wrong exponent in the entropy ODE
+    (d ln s/d ln T = 1/c_s^2), a wrong normalisation or a transposed column fails here."""
+    from workload.eos import baseline_table
+    tab = baseline_table()
+    T, e, P, c2 = tab.T, tab.e, tab.p, tab.cs2
+    s_fd = np.diff(P) / np.diff(T)
+    s_mid = 0.5 * ((e[1:] + P[1:]) / T[1:] + (e[:-1] + P[:-1]) / T[:-1])
+    assert np.max(np.abs(s_fd / s_mid - 1)) < 1e-4
+    c2_fd = np.diff(P) / np.diff(e)
+    assert np.max(np.abs(c2_fd - 0.5 * (c2[1:] + c2[:-1]))) < 1e-4
+    Tg = T * HBARC
+    c2_formula = 1.0 / 3.0 - 0.2 * np.exp(-(((Tg - 0.17) / 0.05) ** 2))
+    assert np.max(np.abs(c2 - c2_formula)) < 1e-14
+    assert np.min(c2) < 0.134 and abs(Tg[np.argmin(c2)] - 0.17) < 2e-3  # the dip at T = 0.17 GeV
+    assert np.max(np.abs(np.exp(tab.lndelta) - (1.0 / 3.0 - c2))) < 1e-15
+    lnd_formula = math.log(0.2) - ((Tg - 0.17) / 0.05) ** 2
+    assert np.max(np.abs(tab.lndelta - lnd_formula) / np.abs(lnd_formula)) < 1e-12
+    s_top = (e[-1] + P[-1]) / T[-1]
+    assert abs(s_top / (4.0 / 3.0 * A_SB * T[-1] ** 3) - 1) < 1e-6
+    r = P / (A_SB * T ** 4 / 3.0)
+    hot = Tg > 0.5
+    assert np.all(np.diff(r[hot]) > 0) and abs(r[-1] - 1) < 2e-3  # P approaches the SB value from below
+    assert np.all(r < 1.0)
+
+
+def test_gubser_reduces_to_bjorken_near_the_axis_at_early_times():
+    """The viscous Gubser ODEs (derived here from Sec. 2.2 with tau_pipi = 0) at r = 0 and
+    q tau << 1 (rho -> -infinity, tanh rho -> -1, d rho = d tau / tau) must reduce to the conformal
+    Bjorken equations (evolutionEd0p1)-(evolutionpi1) with pi = -tau^2 pi^{eta eta} = -pibar (e + P).
+    The Bjorken ODE integrated from the Gubser state at tau_a agrees at tau_b up to the transverse
+    expansion, an O((q tau)^2) correction: the difference falls by ~4 when q halves."""
+    devs = []
+    for q in (1.0, 0.5):
+        g = GubserSolution(eta_over_s=0.2, T0hat=1.2, q=q)
+        ta, tb = 1e-3, 1e-2
+
+        def e_pi(tau):
+            rho, _ = g.rho_kappa(tau, 0.0)
+            That, pibar = g.that_pibar(np.array([rho]))
+            e = A_SB * (float(That[0]) / tau) ** 4
+            return e, -float(pibar[0]) * 4.0 / 3.0 * e
+
+        ea, pa = e_pi(ta)
+        eb, pb = e_pi(tb)
+        r = bjorken_conformal(ta, ea, pa, [tb], 0.2, A_SB, tau_pipi=False)
+        devs.append((abs(r[0][-1] / eb - 1), abs(r[1][-1] / pb - 1)))
+        assert abs(pb) > 1e-3 * eb  # the viscous term is not negligible on this interval
+    assert devs[0][0] < 2e-3 and devs[0][1] < 2e-3
+    for k in range(2):
+        assert 3.0 < devs[0][k] / devs[1][k] < 5.0
 
 
 def test_nonconformal_bjorken_lattice_eos_e5():

@@ -46,7 +46,15 @@ def _worker(rank, world, port, out_dir):
     from paper_1608_06577_gb300 import parallel
     w, r, _ = parallel.init("gloo")
     cells = [n * n * nz for n, nz, _ in batch_shapes(64)]
-    mine = shard_events(cells, w)[r]
+    mine, total_cells = parallel.rank_share(cells, w, r)  # the selection bench.py --batch makes
+    assert mine == shard_events(cells, w)[r] and total_cells == sum(cells)
+    if r == 1:  # the events a rank builds are the ones of the full batch with those indices
+        from workload.problem import batch_problems
+        small = dict(nx_choices=(8, 12), neta_choices=(4, 8), hot_range=(2, 4))
+        full = batch_problems(6, **small)
+        part = batch_problems(6, events=[4, 1], **small)
+        assert [p.name for p in part] == [full[4].name, full[1].name]
+        assert all((a.e == b.e).all() for a, b in zip(part, [full[4], full[1]]))
     parallel.barrier(w)
     t = parallel.max_over_ranks(float(10 + r), w)
     total = parallel.sum_over_ranks(float(sum(cells[i] for i in mine)), w)

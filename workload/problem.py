@@ -248,9 +248,12 @@ def batch_shapes(n_events=64, seed=1000, nx_choices=tuple(range(64, 161, 16)), n
 
 
 def batch_problems(n_events=64, seed=1000, eta_over_s=0.08, nx_choices=tuple(range(64, 161, 16)),
-                   neta_choices=(16, 32, 48, 64), hot_range=(20, 100), **kw):
+                   neta_choices=(16, 32, 48, 64), hot_range=(20, 100), events=None, **kw):
     """Events with fluctuating initial conditions and uneven grids: per event nx = ny drawn
     uniformly from nx_choices, neta from neta_choices, the hotspot count uniformly in hot_range,
-    hotspot seed = seed + event (all draws from SplitMix64(seed))."""
-    return [hotspot_problem(nx=n, ny=n, neta=nz, nhot=nhot, seed=seed + ev, eta_over_s=eta_over_s, **kw)
-            for ev, (n, nz, nhot) in enumerate(batch_shapes(n_events, seed, nx_choices, neta_choices, hot_range))]
+    hotspot seed = seed + event (all draws from SplitMix64(seed)).  events: build only these
+    event indices of the batch (in the given order), e.g. one rank's share."""
+    shapes = batch_shapes(n_events, seed, nx_choices, neta_choices, hot_range)
+    idx = range(n_events) if events is None else events
+    return [hotspot_problem(nx=shapes[ev][0], ny=shapes[ev][0], neta=shapes[ev][1], nhot=shapes[ev][2],
+                            seed=seed + ev, eta_over_s=eta_over_s, **kw) for ev in idx]
