@@ -48,6 +48,7 @@ enum {
 enum { KT_MILNE = 0, KT_CARTESIAN = 1 };              /* coordinates (Cartesian: Sec. 5.1) */
 enum { KT_BC_COPY = 0, KT_BC_PERIODIC = 1 };          /* ghost cells: Eqs. ghostCells_1/2 or periodic */
 enum { KT_FP64 = 0, KT_MIXED = 1 };                   /* precision mode */
+enum { KT_STORE_FP64 = 0, KT_STORE_PI_FP32 = 1 };     /* KT_MIXED storage of pi, Pi (kt_options.pi_storage) */
 enum { KT_INV_PLAIN = 0, KT_INV_LEARNED = 1 };        /* inversion start: previous e, or MLP */
 enum { KT_IFACE_RECON = 0, KT_IFACE_INVERT = 1 };     /* face velocities (see kt_options.iface) */
 enum { KT_EOS_CONFORMAL = 0, KT_EOS_TABLE = 1 };
@@ -106,6 +107,12 @@ typedef struct {
                             inverted (Eq. eInferred), 12 root-finds per cell and stage, each started
                             from the e of the cell the state was extrapolated from; a state with no
                             root gets v = 0.  FP64 root-finds in KT_FP64, FP32 in KT_MIXED. */
+  int pi_storage;        /* KT_MIXED only.  KT_STORE_FP64 (default): all 15 components of q (Eq.
+                            qComponents) are stored and Heun-summed in FP64.  KT_STORE_PI_FP32: only
+                            T^{tau mu} is; pi^{mu nu} and Pi -- the dissipative quantities the scheme
+                            promotes to conserved variables (Sec. 3.1) -- are stored and summed in FP32
+                            (the storage variant of Sec. 4.2's remark on memory).  The inversion and
+                            the T^{tau mu} accumulation stay FP64 either way. */
 } kt_options;
 
 /* Learned inversion start: an MLP 6 -> 32 -> 32 -> 1 with ReLU; weights row-major
@@ -121,6 +128,10 @@ typedef struct {
   long long newton_iters;/* total Newton iterations in the last kt_step (all cells, both stages) */
   long long fallbacks;   /* learned mode: cells that fell back to the plain root-find */
   long long regulated;   /* cells whose pi was scaled by a factor < 0.999 in the last kt_step */
+  /* of the current state, over every event's physical cells (reduced on the device when
+   * kt_get_stats is called; 0 before any state is set): */
+  double e_min, e_max;   /* smallest and largest energy density (fm^-4, in the stored precision) */
+  double reg_min;        /* smallest regulation factor tanh(rho)/rho applied to pi in the last step */
 } kt_stats;
 
 typedef struct kt_ctx kt_ctx;
@@ -236,9 +247,12 @@ int kt_get_state_event(kt_ctx* ctx, int event, double* tau, double* e, double* u
                        int on_device);
 /* The tile shape in use (threads per block x, y, z), the grid size in blocks and, after
  * autotuning, the measured first-stage time in ms of each candidate (up to *n_candidates
- * entries; *n_candidates is set to the number of candidates).  Candidate 2 s + g is tile shape s
- * of (32,4,2), (32,8,1), (32,2,4), (32,1,8), (32,4,1), (32,2,2) with g = 0 a persistent grid (as
- * many blocks as are resident at once, each walking the tile table) or g = 1 one block per tile. */
+ * entries; *n_candidates is set to the number of candidates, 24; candidates that do not apply
+ * to the context report 0).  Candidate 12 v + 2 s + g is tile shape s of (32,4,2), (32,8,1),
+ * (32,2,4), (32,1,8), (32,4,1), (32,2,2) with g = 0 a persistent grid (as many blocks as are
+ * resident at once, each walking the tile table) or g = 1 one block per tile, and v = 1 (KT_MIXED
+ * with FP64 pi storage only) the update kernels' inputs staged in shared memory by TMA bulk copies
+ * of each tile (double-buffered on a persistent grid) instead of read by each thread. */
 int kt_get_tuning(kt_ctx* ctx, int* block_xyz, int* grid_blocks, float* candidate_ms, int* n_candidates);
 /* Use candidate `candidate` (numbered as above) from now on, without autotuning; KT_ERR_ARG if it
  * is out of range.  The results do not depend on the candidate: every candidate runs the same
@@ -304,6 +318,26 @@ int kt_mlp_predict_static(const float* params, const float* x, long long n, floa
  * 0 runs it in FP32. */
 int kt_mlp_grad(const float* params, const float* x, const float* y_target, long long n, int bf16_forward,
                 float* grad, float* loss, void* stream);
+
+/* The network's training set from samples of kt_mlp_features (the paper has no counterpart):
+ * of the n rows x [n][6], y [n] (device), keep in their order those the network corrects, feature
+ * 1 (M^2/E^2) above KT_MLP_GATE_R2, writing their features to x_out [*n_out][6] and the target
+ * z = y / (M^2/E^2) (IEEE division) to z_out; *n_out is a device int64.  x_out and z_out need
+ * room for n rows.  workspace: caller-owned device memory of kt_mlp_targets_workspace(n) bytes.
+ * Asynchronous on `stream`; KT_ERR_ARG for null pointers, n < 0 or a small workspace. */
+int kt_mlp_targets_workspace(long long n, size_t* bytes);
+int kt_mlp_targets(const float* x, const float* y, long long n, float* x_out, float* z_out, long long* n_out,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
+/* Mini-batch b (>= 0) of epoch `epoch` of a shuffled pass over n training rows (device x [n][6],
+ * y [n]): rows p(b batch + i), i < count = min(batch, n - b batch), into xb [count][6], yb [count],
+ * where p is a pseudo-random permutation of [0, n) keyed by (seed, epoch) -- a 4-round Feistel
+ * network on the smallest 4^h >= n with cycle walking -- so that the batches of an epoch cover
+ * every row exactly once.  *flag (device) gets bit 1 if a walk exceeded its bound (not expected;
+ * that row is then taken unpermuted).  KT_ERR_ARG for null pointers, n <= 0, batch <= 0 or
+ * b batch >= n. */
+int kt_mlp_batch(const float* x, const float* y, long long n, unsigned long long seed, int epoch, long long b,
+                 long long batch, float* xb, float* yb, unsigned* flag, void* stream);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step number `step` >= 1; m, v are the
  * caller's moment buffers of KT_MLP_NPARAM floats (zero before the first step). */

@@ -18,6 +18,7 @@ ERRORS = {-1: "KT_ERR_ARG", -2: "KT_ERR_CUDA", -3: "KT_ERR_OOM", -4: "KT_ERR_EOS
           -6: "KT_ERR_INVERSION", -7: "KT_ERR_NONFINITE", -8: "KT_ERR_TIMEOUT"}
 KT_FP64, KT_MIXED = 0, 1
 KT_INV_PLAIN, KT_INV_LEARNED = 0, 1
+KT_STORE_FP64, KT_STORE_PI_FP32 = 0, 1
 MLP_NPARAM = 32 * 6 + 32 + 32 * 32 + 32 + 32 + 1
 
 
@@ -47,12 +48,13 @@ class Options(C.Structure):
                 ("xi0", C.c_double), ("e_min", C.c_double), ("tau_relax_min", C.c_double),
                 ("stream", C.c_void_p), ("arena", C.c_void_p), ("arena_bytes", C.c_size_t),
                 ("mlp_weights", C.POINTER(C.c_float)), ("use_graph", C.c_int), ("autotune", C.c_int),
-                ("iface", C.c_int)]
+                ("iface", C.c_int), ("pi_storage", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("tau", C.c_double), ("steps", C.c_longlong), ("max_speed", C.c_float), ("status", C.c_uint),
-                ("newton_iters", C.c_longlong), ("fallbacks", C.c_longlong), ("regulated", C.c_longlong)]
+                ("newton_iters", C.c_longlong), ("fallbacks", C.c_longlong), ("regulated", C.c_longlong),
+                ("e_min", C.c_double), ("e_max", C.c_double), ("reg_min", C.c_double)]
 
 
 def lib_path() -> str:
@@ -112,7 +114,7 @@ class KT:
     or for a batch: a list of problems that differ only in grid and initial state."""
 
     def __init__(self, prob, precision: int = KT_FP64, inversion: int = KT_INV_PLAIN, mlp_weights=None,
-                 use_graph: bool = True, device_arena: bool = True, autotune: bool = True):
+                 use_graph: bool = True, device_arena: bool = True, autotune: bool = True, pi_fp32: bool = False):
         import torch
         self.torch = torch
         L = load_library()
@@ -138,6 +140,7 @@ class KT:
         o.e_min, o.tau_relax_min = prob.e_min, prob.tau_relax_min
         o.use_graph = int(bool(use_graph))
         o.autotune = int(bool(autotune))
+        o.pi_storage = KT_STORE_PI_FP32 if pi_fp32 else KT_STORE_FP64
         self.stream = torch.cuda.current_stream()
         o.stream = C.c_void_p(self.stream.cuda_stream)
         self._keep = []
@@ -312,6 +315,9 @@ def _mlp_lib():
         L.kt_mlp_predict.argtypes = [vp, vp, ll, vp, vp, C.c_size_t, vp]
         L.kt_mlp_grad.argtypes = [vp, vp, vp, ll, C.c_int, vp, vp, vp]
         L.kt_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, vp]
+        L.kt_mlp_targets_workspace.argtypes = [ll, C.POINTER(C.c_size_t)]
+        L.kt_mlp_targets.argtypes = [vp, vp, ll, vp, vp, vp, vp, C.c_size_t, vp]
+        L.kt_mlp_batch.argtypes = [vp, vp, ll, C.c_ulonglong, C.c_int, ll, ll, vp, vp, vp, vp]
         L._mlp_ready = True
     return L
 
@@ -358,16 +364,50 @@ def mlp_adam(params, grad, m, v, step, lr):
         raise KTError(rc, "kt_mlp_adam")
 
 
-def _kt_mlp_features(self, cells):
+def mlp_targets(X, Y):
+    """The rows the network corrects and their targets z = y / r^2 (kt_mlp_targets), in order."""
+    import torch
+    L = _mlp_lib()
+    n = X.shape[0]
+    nb = C.c_size_t()
+    if L.kt_mlp_targets_workspace(n, C.byref(nb)) != KT_OK:
+        raise KTError(-1, "kt_mlp_targets_workspace")
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=X.device)
+    xo = torch.empty_like(X)
+    zo = torch.empty_like(Y)
+    cnt = torch.empty(1, dtype=torch.int64, device=X.device)
+    rc = L.kt_mlp_targets(_p(X), _p(Y), n, _p(xo), _p(zo), _p(cnt), _p(ws), nb.value, _stream_handle())
+    if rc != KT_OK:
+        raise KTError(rc, "kt_mlp_targets")
+    k = int(cnt.cpu().item())
+    return xo[:k], zo[:k]
+
+
+def mlp_batch(X, Y, seed, epoch, b, batch, xb, yb, flag):
+    """Mini-batch b of a shuffled epoch into xb, yb (kt_mlp_batch); returns the row count."""
+    L = _mlp_lib()
+    rc = L.kt_mlp_batch(_p(X), _p(Y), X.shape[0], int(seed), int(epoch), int(b), int(batch), _p(xb), _p(yb),
+                        _p(flag), _stream_handle())
+    if rc != KT_OK:
+        raise KTError(rc, "kt_mlp_batch")
+    return min(batch, X.shape[0] - b * batch)
+
+
+def _kt_mlp_features(self, cells, out=None):
     """Training samples at physical cells (CUDA int64 tensor): features [n, 6], target [n],
-    exact root e [n] (float64)."""
+    exact root e [n] (float64); `out` may hold (x, y, e) tensors to write into (e.g. views of a
+    preallocated training set)."""
     import torch
     L = _mlp_lib()
     n = cells.numel()
     cells = cells.to(dtype=torch.int64).contiguous()
-    x = torch.empty((n, 6), dtype=torch.float32, device="cuda")
-    y = torch.empty(n, dtype=torch.float32, device="cuda")
-    e = torch.empty(n, dtype=torch.float64, device="cuda")
+    if out is not None:
+        x, y, e = out
+        assert x.shape == (n, 6) and y.shape == (n,) and e.shape == (n,) and x.is_contiguous()
+    else:
+        x = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+        y = torch.empty(n, dtype=torch.float32, device="cuda")
+        e = torch.empty(n, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     self._check(L.kt_mlp_features(self.ctx, n, _p(cells), _p(x), _p(y), _p(e)), "kt_mlp_features")
     return x, y, e

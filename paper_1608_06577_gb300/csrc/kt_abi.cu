@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -30,8 +31,10 @@ struct Shape {
 // candidate tile shapes of the autotuner (threads per block; x stays 32 so a warp is one x-row)
 constexpr Shape kShapes[] = {{32, 4, 2}, {32, 8, 1}, {32, 2, 4}, {32, 1, 8}, {32, 4, 1}, {32, 2, 2}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
-// candidates: every shape with a persistent grid (blocks resident at once) and with one block per tile
-constexpr int kNumCandidates = 2 * kNumShapes;
+// candidates: every shape with a persistent grid (blocks resident at once) and with one block per tile,
+// each (mixed precision) with the update kernel reading its inputs directly or staged by TMA
+constexpr int kNumBase = 2 * kNumShapes;
+constexpr int kNumCandidates = 2 * kNumBase;
 
 struct Ctx {
   kt_options opt;
@@ -66,6 +69,9 @@ struct Ctx {
   Lattice* d_lat = nullptr;
   Tile* d_tiles = nullptr;
   CUtensorMap* d_tmaps = nullptr;  // mixed precision: per event, the 4-d maps of qf (first nev) and qsf
+  CUtensorMap* d_umaps = nullptr;  // mixed precision: per event, the kUpdMaps maps of the staged update
+  int staged = 0;                  // the update kernels read their inputs staged by TMA
+  int upd_nbuf = 1;                // staged update: buffers per block (2 on a persistent grid)
   float* reg = nullptr;            // regulation factor of the last step, per cell (diagnostics)
   float* z_net = nullptr;          // learned start: the network's output per cell within a step
   int max_tiles = 0;
@@ -79,6 +85,7 @@ struct Ctx {
   int cand = 0;
   float tune_ms[kNumCandidates] = {};
   int learned = 0;
+  int pi32 = 0;          // KT_STORE_PI_FP32: pi, Pi live in the FP32 array qf (components 4-14)
   int cur = 0, prev = 1, spare = 2;
   double tau = 0.0;
   long long steps = 0;
@@ -96,6 +103,12 @@ int fail(Ctx* c, int code, const char* fmt, ...) {
   }
   return code;
 }
+
+// NVTX range for the duration of a host call (visible in Nsight timelines; no cost without a tool)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 #define CK(call)                                                                                 \
   do {                                                                                           \
@@ -170,6 +183,7 @@ size_t state_bytes(const std::vector<Lattice>& lat, long long gs, size_t max_cel
   b += align_up(lat.size() * sizeof(Lattice), 256);
   b += align_up((size_t)max_tiles * sizeof(Tile), 256);
   if (mixed) b += align_up(2 * lat.size() * sizeof(CUtensorMap), 256);
+  if (mixed) b += align_up(kUpdMaps * lat.size() * sizeof(CUtensorMap), 256);
   b += align_up(fs * 4, 256);                  // regulation factors
   b += align_up(fs * 4, 256);                  // network outputs (learned start)
   return b;
@@ -326,6 +340,31 @@ __global__ void scatter_kernel(const Params P, const Lattice L, const double* __
 
 __global__ void advance_tau_kernel(double* tau, double dtau) { tau[0] += dtau; }
 
+// smallest and largest e and smallest regulation factor over one event's physical cells (all
+// positive, so their float bit patterns order like the values): out[0] min e, [1] max e, [2] min f
+template <typename R>
+__global__ void state_extrema_kernel(const Lattice L, const R* __restrict__ e, const float* __restrict__ reg,
+                                     unsigned* out) {
+  const long long ncp = (long long)L.nx * L.ny * L.nz;
+  unsigned lo = 0x7f800000u, hi = 0u, rl = 0x7f800000u;
+  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < ncp; o += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(o % L.nx), j = (int)((o / L.nx) % L.ny), k = (int)(o / ((long long)L.nx * L.ny));
+    const long long c = L.idx(i + 2, j + 2, k + 2);
+    const unsigned b = __float_as_uint(fmaxf(to_f32(e[c]), 0.f));
+    lo = min(lo, b);
+    hi = max(hi, b);
+    rl = min(rl, __float_as_uint(fmaxf(reg[c], 0.f)));
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  rl = __reduce_min_sync(0xffffffffu, rl);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(out, lo);
+    atomicMax(out + 1, hi);
+    atomicMin(out + 2, rl);
+  }
+}
+
 // self-test of the FP64 division of the stencil (vdiv) on caller-given operands
 __global__ void div_selftest_kernel(const double* __restrict__ a, const double* __restrict__ b, double* q,
                                     long long n) {
@@ -371,9 +410,10 @@ __global__ void diag_kernel(const Params P, const Lattice L, const StageIO<R> io
 
 // training samples of the learned start: features as the stage kernel forms them, the exact
 // FP64 root and the target 10 ln(e / e_conf)
-__global__ void mlp_features_kernel(const Params P, const Lattice L, const double* __restrict__ q, double tau,
-                                    long long n, const long long* __restrict__ cells, float* X, float* Y,
-                                    double* Eexact, unsigned* status) {
+__global__ void mlp_features_kernel(const Params P, const Lattice L, const double* __restrict__ q,
+                                    const float* __restrict__ qf, int pi32, double tau, long long n,
+                                    const long long* __restrict__ cells, float* X, float* Y, double* Eexact,
+                                    unsigned* status) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const long long ncp = (long long)L.nx * L.ny * L.nz;
@@ -385,7 +425,7 @@ __global__ void mlp_features_kernel(const Params P, const Lattice L, const doubl
   const int i = (int)(o % L.nx), j = (int)((o / L.nx) % L.ny), k = (int)(o / ((long long)L.nx * L.ny));
   const long long c = L.idx(i + 2, j + 2, k + 2);
   double qn[NQ];
-  for (int m = 0; m < NQ; ++m) qn[m] = q[m * L.fstride + c];
+  for (int m = 0; m < NQ; ++m) qn[m] = (pi32 && m >= 4) ? (double)qf[m * L.fstride + c] : q[m * L.fstride + c];
   const float Ef = d2f_bits(qn[0] - qn[4]);
   const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
   const double g = P.milne ? tau * tau : 1.0;
@@ -444,6 +484,7 @@ UpdIO make_uio(Ctx* c, int stage) {
   StageIO<float> io = make_io<float>(c, stage);
   u.q = c->q;
   u.qf_n = c->qf;
+  u.qsf = c->qsf;
   u.k1 = k_buf(c, 1);
   u.k2 = k_buf(c, 2);
   u.qr_out = io.qr_out;
@@ -511,15 +552,45 @@ int allow_rhs_smem(Ctx* c) {
   set((const void*)rhs_kernel<2, true, true>);
   set((const void*)rhs_kernel<2, false, true>);
   if (e != cudaSuccess) return fail(c, KT_ERR_CUDA, "rhs shared memory: %s", cudaGetErrorString(e));
+  bytes = 0;
+  for (const auto& sh : kShapes) bytes = std::max(bytes, upd_smem_bytes(sh.x, sh.y, sh.z, 2));
+  set((const void*)update_staged_kernel<1, true>);
+  set((const void*)update_staged_kernel<1, false>);
+  set((const void*)update_staged_kernel<2, true>);
+  set((const void*)update_staged_kernel<2, false>);
+  if (e != cudaSuccess) return fail(c, KT_ERR_CUDA, "update shared memory: %s", cudaGetErrorString(e));
   return KT_OK;
 }
 
-template <int STAGE, bool LEARNED>
-void launch_split_stage(Ctx* c, const StageIO<float>& io, const UpdIO& uio) {
+// the update kernel of a stage for the context's root-find start and pi storage
+template <int STAGE>
+void launch_update(Ctx* c, const UpdIO& uio) {
   const Shape& s = kShapes[c->shape];
   const dim3 blk(s.x, s.y, s.z);
+  if (c->staged && !c->pi32) {
+    const size_t sm = upd_smem_bytes(s.x, s.y, s.z, c->upd_nbuf);
+    if (c->learned)
+      update_staged_kernel<STAGE, true><<<c->grid_upd, blk, sm, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles,
+                                                                             c->ntiles, c->d_umaps, c->upd_nbuf);
+    else
+      update_staged_kernel<STAGE, false><<<c->grid_upd, blk, sm, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles,
+                                                                              c->ntiles, c->d_umaps, c->upd_nbuf);
+    return;
+  }
+  if (c->learned && c->pi32)
+    update_kernel<STAGE, true, true><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
+  else if (c->learned)
+    update_kernel<STAGE, true, false><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
+  else if (c->pi32)
+    update_kernel<STAGE, false, true><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
+  else
+    update_kernel<STAGE, false, false><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
+}
+
+template <int STAGE>
+void launch_split_stage(Ctx* c, const StageIO<float>& io, const UpdIO& uio) {
   launch_rhs<STAGE>(c, io);
-  update_kernel<STAGE, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
+  launch_update<STAGE>(c, uio);
 }
 
 // ev (optional, kNumTimed + 1 events): recorded between the launches of one step, in the order
@@ -530,21 +601,17 @@ void mark(Ctx* c, cudaEvent_t* ev, int i) {
   if (ev) cudaEventRecord(ev[i], c->stream);
 }
 
-template <typename R, bool LEARNED>
+template <typename R>
 void launch_step_stages(Ctx* c, cudaEvent_t* ev) {
   if constexpr (sizeof(R) == 4) {
-    const Shape& s = kShapes[c->shape];
-    const dim3 blk(s.x, s.y, s.z);
     mark(c, ev, 0);
     launch_rhs<1>(c, make_io<float>(c, 1));
     mark(c, ev, 1);
-    update_kernel<1, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, make_uio(c, 1), c->d_lat, c->d_tiles,
-                                                                  c->ntiles);
+    launch_update<1>(c, make_uio(c, 1));
     mark(c, ev, 2);
     launch_rhs<2>(c, make_io<float>(c, 2));
     mark(c, ev, 3);
-    update_kernel<2, LEARNED><<<c->grid_upd, blk, 0, c->stream>>>(c->P, make_uio(c, 2), c->d_lat, c->d_tiles,
-                                                                  c->ntiles);
+    launch_update<2>(c, make_uio(c, 2));
     mark(c, ev, 4);
   } else {
     mark(c, ev, 0);
@@ -559,9 +626,8 @@ void launch_step_stages(Ctx* c, cudaEvent_t* ev) {
 
 // enqueue one full step (two stages + tau advance) for the current rotation phase, then rotate
 int enqueue_step(Ctx* c, cudaEvent_t* ev = nullptr) {
-  if (c->mixed && c->learned) launch_step_stages<float, true>(c, ev);
-  else if (c->mixed) launch_step_stages<float, false>(c, ev);
-  else launch_step_stages<double, false>(c, ev);
+  if (c->mixed) launch_step_stages<float>(c, ev);
+  else launch_step_stages<double>(c, ev);
   advance_tau_kernel<<<1, 1, 0, c->stream>>>(c->d_tau, c->P.dtau);
   mark(c, ev, 5);
   // u^{n-1} <- u^n, u^n <- u^{n+1}; the old u^{n-1} buffer (holding u^*) becomes the spare
@@ -613,12 +679,38 @@ int encode_tensor_maps(Ctx* c) {
       if (r != CUDA_SUCCESS) return fail(c, KT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for event %d", (int)r, e);
     }
   CK(cudaMemcpyAsync(c->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
+  // the staged update's boxes: the tile's cells in y and eta, bx + 4 cells in x from the tile's
+  // padded x, for q (FP64: 8 components, and 1), k_1, k_2 and the FP32 copy of q (15 components)
+  std::vector<CUtensorMap> um(kUpdMaps * c->nev);
+  for (int e = 0; e < c->nev; ++e) {
+    const Lattice& L = c->lat[e];
+    struct Src { void* base; CUtensorMapDataType t; int esz; cuuint32_t depth; };
+    const Src src[kUpdMaps] = {{c->q + L.base, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, 8},
+                               {c->q + L.base, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, 1},
+                               {k_buf(c, 1) + L.base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, NQ},
+                               {k_buf(c, 2) + L.base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, NQ},
+                               {c->qf + L.base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, NQ}};
+    for (int w = 0; w < kUpdMaps; ++w) {
+      const cuuint64_t es = (cuuint64_t)src[w].esz;
+      cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)NQ};
+      cuuint64_t strides[3] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es, (cuuint64_t)c->gs * es};
+      cuuint32_t box[4] = {(cuuint32_t)(s.x + 4), (cuuint32_t)s.y, (cuuint32_t)s.z, src[w].depth};
+      cuuint32_t estr[4] = {1, 1, 1, 1};
+      CUresult r = encode(&um[kUpdMaps * e + w], src[w].t, 4, src[w].base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(c, KT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d), update map %d", (int)r, w);
+    }
+  }
+  CK(cudaMemcpyAsync(c->d_umaps, um.data(), um.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return KT_OK;
 }
 
 int select_shape(Ctx* c, int cand) {
-  const int shape = cand / 2, one_per_tile = cand % 2;
+  const int base = cand % kNumBase, shape = base / 2, one_per_tile = base % 2;
+  c->staged = (cand >= kNumBase) && c->mixed && !c->pi32;
+  c->upd_nbuf = one_per_tile ? 1 : 2;
   std::vector<Tile> tiles;
   build_tiles(c->lat, kShapes[shape], tiles);
   if ((int)tiles.size() > c->max_tiles) return fail(c, KT_ERR_OOM, "tile table overflow");
@@ -634,8 +726,14 @@ int select_shape(Ctx* c, int cand) {
   auto grid = [&](int cap) { return one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles)); };
   if (c->mixed) {
     c->grid_rhs = grid(occupancy_blocks(rhs_kernel<1, true, false>, sh, rhs_smem_bytes(sh.x, sh.y, sh.z)));
-    c->grid_upd = grid(c->learned ? occupancy_blocks(update_kernel<1, true>, sh)
-                                  : occupancy_blocks(update_kernel<1, false>, sh));
+    if (c->staged) {
+      const size_t usm = upd_smem_bytes(sh.x, sh.y, sh.z, c->upd_nbuf);
+      c->grid_upd = grid(c->learned ? occupancy_blocks(update_staged_kernel<2, true>, sh, usm)
+                                    : occupancy_blocks(update_staged_kernel<2, false>, sh, usm));
+    } else {
+      c->grid_upd = grid(c->learned ? occupancy_blocks(update_kernel<1, true, false>, sh)
+                                    : occupancy_blocks(update_kernel<1, false, false>, sh));
+    }
     c->grid_blocks = c->grid_rhs;
   } else {
     c->grid_blocks = grid(occupancy_blocks(stage_kernel<double, 1, true, false>, sh));  // same launch bounds
@@ -649,7 +747,7 @@ int select_shape(Ctx* c, int cand) {
 // Autotuner: time a first-stage launch for every candidate (tile shape, grid size).  The launches write only
 // scratch buffers (q*, its FP32 copy, e*, p*, and u* redirected to the spare buffer), so the
 // state is untouched; the fastest shape is kept.
-template <typename R, bool LEARNED>
+template <typename R>
 int time_first_stage(Ctx* c, float* ms) {
   StageIO<R> io = make_io<R>(c, 1);
   io.u_out = (R*)c->U[c->spare];
@@ -657,7 +755,7 @@ int time_first_stage(Ctx* c, float* ms) {
     if constexpr (sizeof(R) == 4) {  // writes k_1, q*'s FP32 copy, e*, P*, u* (spare buffer)
       UpdIO u = make_uio(c, 1);
       u.u_out = (float*)c->U[c->spare];
-      launch_split_stage<1, LEARNED>(c, io, u);
+      launch_split_stage<1>(c, io, u);
     } else {
       launch_stage<1>(c, io);
     }
@@ -677,14 +775,16 @@ int time_first_stage(Ctx* c, float* ms) {
 }
 
 int autotune(Ctx* c) {
+  Range range_("kt autotune");
   int best = 0;
-  for (int s = 0; s < kNumCandidates; ++s) {
+  const int ncand = (c->mixed && !c->pi32) ? kNumCandidates : kNumBase;  // staging applies to the FP64-pi update
+  for (int s = 0; s < kNumCandidates; ++s) c->tune_ms[s] = 0.f;
+  for (int s = 0; s < ncand; ++s) {
     int rc = select_shape(c, s);
     if (rc != KT_OK) return rc;
     float ms = 0.f;
-    if (c->mixed && c->learned) rc = time_first_stage<float, true>(c, &ms);
-    else if (c->mixed) rc = time_first_stage<float, false>(c, &ms);
-    else rc = time_first_stage<double, false>(c, &ms);
+    if (c->mixed) rc = time_first_stage<float>(c, &ms);
+    else rc = time_first_stage<double>(c, &ms);
     if (rc != KT_OK) return rc;
     c->tune_ms[s] = ms;
     if (ms < c->tune_ms[best]) best = s;
@@ -697,6 +797,7 @@ int autotune(Ctx* c) {
 }
 
 int build_graph(Ctx* c, int phase) {
+  Range range_("kt capture step graph");
   int save[3] = {c->cur, c->prev, c->spare};
   cudaGraph_t gr;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -781,6 +882,9 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   c->mixed = (o.precision == KT_MIXED);
   c->esz = c->mixed ? 4 : 8;
   c->learned = (o.inversion == KT_INV_LEARNED);
+  if (o.pi_storage != KT_STORE_FP64 && o.pi_storage != KT_STORE_PI_FP32) return bail(KT_ERR_ARG);
+  if (o.pi_storage == KT_STORE_PI_FP32 && o.precision != KT_MIXED) return bail(KT_ERR_ARG);
+  c->pi32 = (o.pi_storage == KT_STORE_PI_FP32);
   c->nev = n_events;
   layout(n_events, grids, c->lat, c->gs, c->max_cells);
   c->ev_set.assign(n_events, 0);
@@ -884,6 +988,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   for (const auto& s : kShapes) c->max_tiles = std::max(c->max_tiles, tiles_for(c->lat, s));
   c->d_tiles = (Tile*)carve((size_t)c->max_tiles * sizeof(Tile));
   if (c->mixed) c->d_tmaps = (CUtensorMap*)carve(2 * c->lat.size() * sizeof(CUtensorMap));
+  if (c->mixed) c->d_umaps = (CUtensorMap*)carve(kUpdMaps * c->lat.size() * sizeof(CUtensorMap));
   c->reg = (float*)carve(fs * 4);
   c->z_net = (float*)carve(fs * 4);
   P.seg_d = c->seg_d;
@@ -933,6 +1038,7 @@ int kt_init(kt_ctx** out, const kt_grid* grid, double dx, double deta, double dt
 
 int kt_set_state_event(kt_ctx* c, int event, double tau, const double* e, const double* u, const double* pi,
                        const double* Pi, const double* u_prev, int on_device) {
+  Range range_("kt_set_state");
   if (!c) return KT_ERR_ARG;
   if (event < 0 || event >= c->nev || !e || !(tau > 0 || !c->P.milne))
     return fail(c, KT_ERR_ARG, "kt_set_state: bad argument");
@@ -1020,6 +1126,7 @@ int finish_steps(Ctx* c, int n_steps) {
 extern "C" {
 
 int kt_step(kt_ctx* c, int n_steps) {
+  Range range_("kt_step");
   if (!c || n_steps < 0) return KT_ERR_ARG;
   int rc = begin_steps(c, n_steps);
   if (rc != KT_OK) return rc;
@@ -1043,6 +1150,7 @@ int kt_step(kt_ctx* c, int n_steps) {
 }
 
 int kt_time_kernels(kt_ctx* c, int n_steps, float* ms, int* n_kernels) {
+  Range range_("kt_time_kernels");
   if (!c || n_steps < 1 || !ms || !n_kernels || *n_kernels < kNumTimed) return KT_ERR_ARG;
   int rc = begin_steps(c, n_steps);
   if (rc != KT_OK) return rc;
@@ -1069,6 +1177,7 @@ int kt_time_kernels(kt_ctx* c, int n_steps, float* ms, int* n_kernels) {
 
 int kt_get_state_event(kt_ctx* c, int event, double* tau, double* e, double* u, double* pi, double* Pi, double* q,
                        int on_device) {
+  Range range_("kt_get_state");
   if (!c) return KT_ERR_ARG;
   if (event < 0 || event >= c->nev) return fail(c, KT_ERR_ARG, "kt_get_state: bad event");
   const Lattice& L = c->lat[event];
@@ -1082,15 +1191,21 @@ int kt_get_state_event(kt_ctx* c, int event, double* tau, double* e, double* u, 
   const char* Ucur = (const char*)c->U[c->cur];
   if (e) jobs.push_back({c->E[0], 1, e});
   if (u) for (int m = 0; m < 4; ++m) jobs.push_back({Ucur + (size_t)m * fs * c->esz, 1, u + m * ncp});
-  if (pi) for (int m = 0; m < 10; ++m) jobs.push_back({c->q + (size_t)(4 + m) * fs, 0, pi + m * ncp});
-  if (Pi) jobs.push_back({c->q + (size_t)14 * fs, 0, Pi});
-  if (q) for (int n = 0; n < NQ; ++n) jobs.push_back({c->q + (size_t)n * fs, 0, q + n * ncp});
+  // component n of q: FP64, or (KT_STORE_PI_FP32, n >= 4) the FP32 state
+  auto qjob = [&](int n, double* dst) {
+    if (c->pi32 && n >= 4) jobs.push_back({c->qf + (size_t)n * fs, 2, dst});
+    else jobs.push_back({c->q + (size_t)n * fs, 0, dst});
+  };
+  if (pi) for (int m = 0; m < 10; ++m) qjob(4 + m, pi + m * ncp);
+  if (Pi) qjob(14, Pi);
+  if (q) for (int n = 0; n < NQ; ++n) qjob(n, q + n * ncp);
   for (size_t b = 0; b < jobs.size(); b += 18) {
     size_t nj = std::min<size_t>(18, jobs.size() - b);
     for (size_t t = 0; t < nj; ++t) {
       const Job& jb = jobs[b + t];
       double* dst = c->stage + t * ncp;
-      if (jb.is_r && c->mixed) gather_kernel<float><<<nb, 256, 0, c->stream>>>(L, (const float*)jb.f, dst);
+      if (jb.is_r == 2 || (jb.is_r && c->mixed))
+        gather_kernel<float><<<nb, 256, 0, c->stream>>>(L, (const float*)jb.f, dst);
       else gather_kernel<double><<<nb, 256, 0, c->stream>>>(L, (const double*)jb.f, dst);
     }
     CK(cudaGetLastError());
@@ -1118,7 +1233,8 @@ struct CkptRow {
 std::vector<CkptRow> checkpoint_rows(Ctx* c) {
   std::vector<CkptRow> rows;
   const size_t fs = (size_t)c->gs;
-  for (int n = 0; n < NQ; ++n) rows.push_back({c->q + n * fs, 0});
+  for (int n = 0; n < NQ; ++n)
+    rows.push_back((c->pi32 && n >= 4) ? CkptRow{c->qf + n * fs, 2} : CkptRow{c->q + n * fs, 0});
   for (int n = 0; n < NQ; ++n)
     rows.push_back(c->mixed ? CkptRow{c->qf + n * fs, 1} : CkptRow{c->q + n * fs, 0});
   rows.push_back({c->E[0], 1});
@@ -1134,6 +1250,7 @@ std::vector<CkptRow> checkpoint_rows(Ctx* c) {
 extern "C" {
 
 int kt_get_checkpoint(kt_ctx* c, int event, double* tau, double* buf, int on_device) {
+  Range range_("kt_get_checkpoint");
   if (!c || !buf) return KT_ERR_ARG;
   if (event < 0 || event >= c->nev) return fail(c, KT_ERR_ARG, "kt_get_checkpoint: bad event");
   if (!c->ev_set[event]) return fail(c, KT_ERR_ARG, "kt_get_checkpoint: event %d has no state", event);
@@ -1160,6 +1277,7 @@ int kt_get_checkpoint(kt_ctx* c, int event, double* tau, double* buf, int on_dev
 }
 
 int kt_set_checkpoint(kt_ctx* c, int event, double tau, const double* buf, int on_device) {
+  Range range_("kt_set_checkpoint");
   if (!c || !buf) return KT_ERR_ARG;
   if (event < 0 || event >= c->nev || !(tau > 0 || !c->P.milne))
     return fail(c, KT_ERR_ARG, "kt_set_checkpoint: bad argument");
@@ -1173,7 +1291,9 @@ int kt_set_checkpoint(kt_ctx* c, int event, double tau, const double* buf, int o
     CK(cudaMemcpyAsync(c->stage, buf + b * ncp, nr * ncp * 8, kind, c->stream));
     for (size_t t = 0; t < nr; ++t) {
       const CkptRow& r = rows[b + t];
-      if (!c->mixed && b + t >= (size_t)NQ && b + t < (size_t)(2 * NQ)) continue;  // FP64: the stencil reads q
+      const size_t row = b + t;
+      if (!c->mixed && row >= (size_t)NQ && row < (size_t)(2 * NQ)) continue;  // FP64: the stencil reads q
+      if (c->pi32 && row >= (size_t)(NQ + 4) && row < (size_t)(2 * NQ)) continue;  // the state rows hold them
       const double* src = c->stage + t * ncp;
       if (r.is_r == 2 || (r.is_r && c->mixed)) scatter_kernel<float><<<nb, 256, 0, c->stream>>>(c->P, L, src, (float*)r.f);
       else scatter_kernel<double><<<nb, 256, 0, c->stream>>>(c->P, L, src, (double*)r.f);
@@ -1210,6 +1330,7 @@ int kt_selftest_div(const double* a, const double* b, double* q, long long n, vo
 }
 
 int kt_get_diagnostics(kt_ctx* c, int event, double* out, int on_device) {
+  Range range_("kt_get_diagnostics");
   if (!c || !out) return KT_ERR_ARG;
   if (event < 0 || event >= c->nev) return fail(c, KT_ERR_ARG, "kt_get_diagnostics: bad event");
   if (!c->ev_set[event]) return fail(c, KT_ERR_ARG, "kt_get_diagnostics: event %d has no state", event);
@@ -1236,8 +1357,8 @@ int kt_mlp_features(kt_ctx* c, long long n, const long long* cells, float* x, fl
   if (!c->ev_set[0]) return fail(c, KT_ERR_ARG, "kt_mlp_features: no state set");
   if (n == 0) return KT_OK;
   CK(cudaMemsetAsync(c->d_stat, 0, 4, c->stream));
-  mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->P, c->lat[0], c->q, c->tau, n, cells, x,
-                                                                          y, e_exact, c->d_stat);
+  mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->P, c->lat[0], c->q, c->qf, c->pi32,
+                                                                          c->tau, n, cells, x, y, e_exact, c->d_stat);
   CK(cudaGetLastError());
   unsigned st = 0;
   CK(cudaMemcpyAsync(&st, c->d_stat, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1273,9 +1394,32 @@ int kt_set_tuning(kt_ctx* c, int candidate) {
 
 int kt_get_stats(kt_ctx* c, kt_stats* s) {
   if (!c || !s) return KT_ERR_ARG;
-  *s = c->last;
-  s->tau = c->tau;
-  s->steps = c->steps;
+  kt_stats r = c->last;
+  r.tau = c->tau;
+  r.steps = c->steps;
+  r.e_min = r.e_max = r.reg_min = 0.0;
+  bool any = false;
+  for (int e = 0; e < c->nev; ++e) any |= (c->ev_set[e] != 0);
+  if (any) {  // the extrema of the current state, reduced on the device (words 12-14 of the stats block)
+    unsigned* ext = c->d_stat + KSTAT_WORDS;
+    const unsigned init[3] = {0x7f800000u, 0u, 0x7f800000u};
+    CK(cudaMemcpyAsync(ext, init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+    for (int e = 0; e < c->nev; ++e) {
+      if (!c->ev_set[e]) continue;
+      if (c->mixed) state_extrema_kernel<float><<<152, 256, 0, c->stream>>>(c->lat[e], (const float*)c->E[0], c->reg, ext);
+      else state_extrema_kernel<double><<<152, 256, 0, c->stream>>>(c->lat[e], (const double*)c->E[0], c->reg, ext);
+    }
+    CK(cudaGetLastError());
+    unsigned h[3];
+    CK(cudaMemcpyAsync(h, ext, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    float f[3];
+    memcpy(f, h, sizeof(f));
+    r.e_min = f[0];
+    r.e_max = f[1];
+    r.reg_min = f[2];
+  }
+  *s = r;
   return KT_OK;
 }
 

@@ -205,6 +205,138 @@ __global__ void mlp_adam_kernel(float* params, const float* __restrict__ grad, f
   params[p] -= lr * (mp * c1) / (sqrtf(vp * c2) + eps);
 }
 
+// ---------------------------------------------------------------- training data
+// The training set keeps the samples the network corrects (feature 1, r^2 = M^2/E^2, above the
+// gate) in their original order, with target z = y / r^2: a stable compaction in three passes
+// (per-block counts, one-block scan of the counts, per-block scatter) over tiles of
+// kTgtTile samples.
+constexpr int kTgtThreads = 256, kTgtPer = 4, kTgtTile = kTgtThreads * kTgtPer;
+
+__device__ __forceinline__ bool network_corrects(const float* __restrict__ x, long long i) {
+  return x[i * MLP_IN + 1] > kMlpGateR2;
+}
+
+__global__ void __launch_bounds__(kTgtThreads) targets_count_kernel(const float* __restrict__ x, long long n,
+                                                                    long long* counts) {
+  __shared__ int s_w[kTgtThreads / 32];
+  int c = 0;
+  const long long base = (long long)blockIdx.x * kTgtTile;
+#pragma unroll
+  for (int k = 0; k < kTgtPer; ++k) {
+    const long long i = base + k * kTgtThreads + threadIdx.x;
+    c += (i < n && network_corrects(x, i)) ? 1 : 0;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < kTgtThreads / 32; ++w) t += s_w[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of the per-block counts in place, total into *n_out (one block)
+__global__ void __launch_bounds__(1024) targets_scan_kernel(long long* counts, long long nblocks, long long* n_out) {
+  __shared__ long long s_part[1024];
+  const long long per = (nblocks + blockDim.x - 1) / blockDim.x;
+  const long long b0 = threadIdx.x * per, b1 = min(nblocks, b0 + per);
+  long long t = 0;
+  for (long long b = b0; b < b1; ++b) t += counts[b];
+  s_part[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int k = 0; k < (int)blockDim.x; ++k) {
+      const long long v = s_part[k];
+      s_part[k] = acc;
+      acc += v;
+    }
+    *n_out = acc;
+  }
+  __syncthreads();
+  long long acc = s_part[threadIdx.x];
+  for (long long b = b0; b < b1; ++b) {
+    const long long v = counts[b];
+    counts[b] = acc;
+    acc += v;
+  }
+}
+
+__global__ void __launch_bounds__(kTgtThreads) targets_scatter_kernel(const float* __restrict__ x,
+                                                                      const float* __restrict__ y, long long n,
+                                                                      const long long* __restrict__ offsets,
+                                                                      float* x_out, float* z_out) {
+  __shared__ int s_w[kTgtThreads / 32];
+  long long off = offsets[blockIdx.x];
+  const long long base = (long long)blockIdx.x * kTgtTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < kTgtPer; ++k) {  // samples in order: row k of the tile, then the threads
+    const long long i = base + k * kTgtThreads + threadIdx.x;
+    const bool keep = i < n && network_corrects(x, i);
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_w[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kTgtThreads / 32; ++w) {
+      const int c = s_w[w];
+      before += (w < warp) ? c : 0;
+      total += c;
+    }
+    if (keep) {
+      const long long o = off + before + __popc(bal & ((1u << lane) - 1u));
+      const float r2 = x[i * MLP_IN + 1];
+#pragma unroll
+      for (int m = 0; m < MLP_IN; ++m) x_out[o * MLP_IN + m] = x[i * MLP_IN + m];
+      z_out[o] = __fdiv_rn(y[i], r2);
+    }
+    off += total;
+    __syncthreads();
+  }
+}
+
+// A keyed pseudo-random permutation of [0, n): a 4-round balanced Feistel network on 2h-bit
+// words (4^h >= n) with a SplitMix64-finalised round function, and cycle walking back into
+// [0, n).  Each walk is bounded; a walk that has not returned after kWalkMax rounds (not expected:
+// at most 3/4 of the domain lies outside [0, n)) takes i itself and is flagged.
+constexpr int kWalkMax = 4096;
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long feistel(unsigned long long v, int h, unsigned long long key) {
+  const unsigned long long mask = (1ULL << h) - 1ULL;
+  unsigned long long L = v >> h, R = v & mask;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const unsigned long long F = mix64(R ^ (key + 0x9e3779b97f4a7c15ULL * (unsigned long long)(r + 1))) & mask;
+    const unsigned long long t = L ^ F;
+    L = R;
+    R = t;
+  }
+  return (L << h) | R;
+}
+
+__global__ void batch_kernel(const float* __restrict__ x, const float* __restrict__ y, long long n, int h,
+                             unsigned long long key, long long first, long long count, float* xb, float* yb,
+                             unsigned* flag) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  unsigned long long v = (unsigned long long)(first + k);
+  int w = 0;
+  do {
+    v = feistel(v, h, key);
+  } while (v >= (unsigned long long)n && ++w < kWalkMax);
+  if (v >= (unsigned long long)n) {
+    v = (unsigned long long)(first + k);
+    atomicOr(flag, 1u);
+  }
+#pragma unroll
+  for (int m = 0; m < MLP_IN; ++m) xb[k * MLP_IN + m] = x[v * MLP_IN + m];
+  yb[k] = y[v];
+}
+
 }  // namespace
 
 namespace kt {
@@ -294,6 +426,43 @@ int kt_mlp_grad(const float* params, const float* x, const float* y_target, long
     mlp_grad_kernel<true><<<nb, 256, 0, s>>>(params, x, y_target, n, inv_n, grad, loss);
   else
     mlp_grad_kernel<false><<<nb, 256, 0, s>>>(params, x, y_target, n, inv_n, grad, loss);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
+}
+
+int kt_mlp_targets_workspace(long long n, size_t* bytes) {
+  if (n < 0 || !bytes) return KT_ERR_ARG;
+  *bytes = (size_t)((n + kTgtTile - 1) / kTgtTile + 1) * sizeof(long long);
+  return KT_OK;
+}
+
+int kt_mlp_targets(const float* x, const float* y, long long n, float* x_out, float* z_out, long long* n_out,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+  size_t need = 0;
+  if (!x || !y || !x_out || !z_out || !n_out || !workspace || kt_mlp_targets_workspace(n, &need) != KT_OK ||
+      workspace_bytes < need)
+    return KT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long nb = (n + kTgtTile - 1) / kTgtTile;
+  long long* counts = (long long*)workspace;
+  if (nb == 0) return cudaMemsetAsync(n_out, 0, sizeof(long long), s) == cudaSuccess ? KT_OK : KT_ERR_CUDA;
+  if (nb > 0x7fffffffLL) return KT_ERR_ARG;
+  targets_count_kernel<<<(unsigned)nb, kTgtThreads, 0, s>>>(x, n, counts);
+  targets_scan_kernel<<<1, 1024, 0, s>>>(counts, nb, n_out);
+  targets_scatter_kernel<<<(unsigned)nb, kTgtThreads, 0, s>>>(x, y, n, counts, x_out, z_out);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
+}
+
+int kt_mlp_batch(const float* x, const float* y, long long n, unsigned long long seed, int epoch, long long b,
+                 long long batch, float* xb, float* yb, unsigned* flag, void* stream) {
+  if (!x || !y || !xb || !yb || !flag || n <= 0 || batch <= 0 || b < 0 || epoch < 0) return KT_ERR_ARG;
+  const long long first = b * batch;
+  if (first >= n) return KT_ERR_ARG;
+  const long long count = (first + batch <= n) ? batch : n - first;
+  int h = 1;
+  while (h < 31 && (1LL << (2 * h)) < n) ++h;
+  const unsigned long long key = seed * 0x2545f4914f6cdd1dULL + (unsigned long long)epoch;
+  batch_kernel<<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n, h, key, first, count, xb,
+                                                                                    yb, flag);
   return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
 }
 

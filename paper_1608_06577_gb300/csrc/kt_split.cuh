@@ -21,7 +21,8 @@ namespace kt {
 
 struct UpdIO {
   double* q;                // q^n, FP64; stage 2 overwrites it with q^{n+1} (own cell only)
-  const float* qf_n;        // FP32 copy of q^n
+  const float* qf_n;        // FP32 copy of q^n (FP32 pi storage: components 4-14 are the state itself)
+  const float* qsf;         // FP32 pi storage, stage 2: q* (its pi and Pi components are the state)
   float* k1;                // dtau C[q^n]; stage 1 rewrites its pi components with the regulated increment
   const float* k2;          // dtau C[q*] (stage 2)
   float* qr_out;            // FP32 copy of the new state: q* (stage 1) or q^{n+1} (stage 2), with ghosts
@@ -222,28 +223,59 @@ __device__ __forceinline__ unsigned invert_split(const Params& P, double gnn, co
   return st;
 }
 
+// Where the update of one cell reads its inputs: straight from the field arrays (UpdInGlobal), or
+// from the tile's box staged in shared memory by TMA (UpdInShared, below).  q(n): q^n in FP64;
+// k1(n), k2(n): the stage increments; qfn(n): the FP32 copy of q^n (stage 1); qs(n): the FP32 q*
+// (FP32 pi storage, stage 2).
+struct UpdInGlobal {
+  const UpdIO& io;
+  long long fs, c;
+  __device__ __forceinline__ double q(int n) const { return __ldg(io.q + n * fs + c); }
+  __device__ __forceinline__ float k1(int n) const { return __ldg(io.k1 + n * fs + c); }
+  __device__ __forceinline__ float k2(int n) const { return __ldg(io.k2 + n * fs + c); }
+  __device__ __forceinline__ float qfn(int n) const { return __ldg(io.qf_n + n * fs + c); }
+  __device__ __forceinline__ float qs(int n) const { return __ldg(io.qsf + n * fs + c); }
+};
+
 // the increment added to q^n in FP64: k_1 (stage 1) or (k_1 + k_2)/2 (stage 2)
-template <int STAGE>
-__device__ __forceinline__ float increment(const UpdIO& io, long long a) {
-  if constexpr (STAGE == 1) return __ldg(io.k1 + a);
-  else return 0.5f * (__ldg(io.k1 + a) + __ldg(io.k2 + a));
+template <int STAGE, typename In>
+__device__ __forceinline__ float increment(const In& in, int n) {
+  if constexpr (STAGE == 1) return in.k1(n);
+  else return 0.5f * (in.k1(n) + in.k2(n));
+}
+
+// FP32 pi storage (KT_STORE_PI_FP32): pi^{mu nu} and Pi are the FP32 values of the stencil copy,
+// Heun-summed in FP32; only T^{tau mu} (components 0-3) is kept and summed in FP64.  The new pi, Pi
+// of one cell: q* = q^n + k_1 (stage 1) or q^{n+1} = (q^n + q* + k_2)/2 (stage 2), Eqs. (step1)-
+// (finalStep), with q* the regulated first-stage state.
+template <int STAGE, typename In>
+__device__ __forceinline__ float pi32_state(const In& in, int n) {
+  if constexpr (STAGE == 1) return in.qfn(n) + in.k1(n);
+  else return 0.5f * (in.qfn(n) + in.qs(n) + in.k2(n));
 }
 
 // One cell; all lanes of the warp call it together (the learned start is warp-wide).
-template <int STAGE, bool LEARNED>
-__device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, const UpdIO& io, int i, int j, int k,
-                                            double tau_out, const uint32_t* s_mlp, unsigned& st, unsigned& nit,
-                                            unsigned& nreg, unsigned& nfb) {
+template <int STAGE, bool LEARNED, bool PI32, typename In>
+__device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, const UpdIO& io, const In& in, int i,
+                                            int j, int k, double tau_out, const uint32_t* s_mlp, unsigned& st,
+                                            unsigned& nit, unsigned& nreg, unsigned& nfb) {
   const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
   const long long fs = L.fstride;
   const long long c = L.idx(i + 2, j + 2, k + 2);
   double qn[NQ];  // FP64 new state; components outside the inversion set are formed after it
+  float qp[NQ];   // FP32 pi storage: the new pi, Pi (components 4-14)
 #pragma unroll
   for (int n = 0; n < NQ; ++n) qn[n] = (n == 0) ? 1.0 : 0.0;  // a harmless rest state past the edge
   if (valid) {
 #pragma unroll
-    for (int n = 0; n < NQ; ++n)
-      if (inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
+    for (int n = 0; n < NQ; ++n) {
+      if (PI32 && n >= 4) {
+        qp[n] = pi32_state<STAGE>(in, n);
+        if (inversion_component(n)) qn[n] = to_f64<float>(qp[n]);  // exact widening for E, M^i, Pi
+      } else if (inversion_component(n)) {
+        qn[n] = in.q(n) + to_f64<float>(increment<STAGE>(in, n));
+      }
+    }
   }
 
   const double gnn = P.milne ? tau_out * tau_out : 1.0;
@@ -264,20 +296,27 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   // the FP32 copy read by the next stencil (and the remaining FP64 components in stage 2)
   // Stage 2 forms pi components 8-13 as f q^n + f dq in one FP64 multiply-add once the
   // regulation factor f is known (measured faster than the separate sum and product).
-  constexpr bool kFusePi = (STAGE == 2);
+  constexpr bool kFusePi = (STAGE == 2) && !PI32;
   float qr[NQ];
   double q8[6];  // q^n and the increment of pi components 8-13 (kFusePi)
   float inc8[6];
   bool scaled = false;
-  if constexpr (STAGE == 1) {
+  if constexpr (PI32) {
 #pragma unroll
-    for (int n = 0; n < NQ; ++n) qr[n] = __ldg(io.qf_n + n * fs + c) + __ldg(io.k1 + n * fs + c);
+    for (int n = 0; n < NQ; ++n) {
+      if (n >= 4) qr[n] = qp[n];
+      else if (STAGE == 1) qr[n] = in.qfn(n) + in.k1(n);
+      else qr[n] = from_f64<float>(qn[n]);
+    }
+  } else if constexpr (STAGE == 1) {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) qr[n] = in.qfn(n) + in.k1(n);
   } else if constexpr (kFusePi) {  // the pi components outside the inversion set are read once, here
 #pragma unroll
     for (int n = 0; n < NQ; ++n) {
       if (!inversion_component(n)) {
-        q8[n - 8] = __ldg(io.q + n * fs + c);
-        inc8[n - 8] = increment<STAGE>(io, n * fs + c);
+        q8[n - 8] = in.q(n);
+        inc8[n - 8] = increment<STAGE>(in, n);
         qr[n] = from_f64<float>(q8[n - 8]) + inc8[n - 8];
       } else {
         qr[n] = from_f64<float>(qn[n]);
@@ -286,7 +325,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   } else {
 #pragma unroll
     for (int n = 0; n < NQ; ++n) {
-      if (!inversion_component(n)) qn[n] = __ldg(io.q + n * fs + c) + to_f64<float>(increment<STAGE>(io, n * fs + c));
+      if (!inversion_component(n)) qn[n] = in.q(n) + to_f64<float>(increment<STAGE>(in, n));
       qr[n] = from_f64<float>(qn[n]);
     }
   }
@@ -307,11 +346,13 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
     if (f < 0.999f) ++nreg;
     if (STAGE == 2 && io.reg_out) io.reg_out[c] = f;
     if (f != 1.f) {
-      if constexpr (STAGE == 1) {
+      if constexpr (PI32) {  // the FP32 state itself is rescaled (stage 2 reads q* from it)
+#pragma unroll
+        for (int n = 4; n < 14; ++n) qr[n] *= f;
+      } else if constexpr (STAGE == 1) {
 #pragma unroll
         for (int n = 4; n < 14; ++n) {  // f q* = q^n + (f k_1 + (f - 1) q^n)
-          const long long a = n * fs + c;
-          io.k1[a] = fmaf(f, io.k1[a], (f - 1.f) * __ldg(io.qf_n + a));
+          io.k1[n * fs + c] = fmaf(f, in.k1(n), (f - 1.f) * in.qfn(n));
           qr[n] *= f;
         }
       } else {  // rescale the FP64 state in registers (re-reading its inputs would miss L2)
@@ -340,7 +381,8 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   //    at the cell and its ghosts
   if constexpr (STAGE == 2) {
 #pragma unroll
-    for (int n = 0; n < NQ; ++n) io.q[n * fs + c] = qn[n];
+    for (int n = 0; n < NQ; ++n)
+      if (!PI32 || n < 4) io.q[n * fs + c] = qn[n];
   }
   for_cell_and_ghosts(P, L, i + 2, j + 2, k + 2, [&](long long t) {
 #pragma unroll
@@ -352,7 +394,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   });
 }
 
-template <int STAGE, bool LEARNED>
+template <int STAGE, bool LEARNED, bool PI32>
 __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     update_kernel(const Params P, const UpdIO io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
                   int ntiles) {
@@ -369,10 +411,124 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
   for (int t = t0; t < t1; ++t) {
     const Tile tl = tiles[t];
     const Lattice L = lats[tl.event];
-    update_cell<STAGE, LEARNED>(P, L, io, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y, tl.k0 + (int)threadIdx.z,
-                                tau_out, s_mlp, st, nit, nreg, nfb);
+    const int i = tl.i0 + (int)threadIdx.x, j = tl.j0 + (int)threadIdx.y, k = tl.k0 + (int)threadIdx.z;
+    const UpdInGlobal in{io, L.fstride, L.idx(i + 2, j + 2, k + 2)};
+    update_cell<STAGE, LEARNED, PI32>(P, L, io, in, i, j, k, tau_out, s_mlp, st, nit, nreg, nfb);
   }
   block_stats(io.status, nullptr, io.counters, st, 0.f, nit, nreg, nfb);
+}
+
+// ---------------------------------------------------------------- staged update (TMA)
+// The inputs of a tile's update (FP64 pi storage) are copied into shared memory by a few TMA bulk
+// loads instead of one global load per thread and component, so that the loads of a tile are all
+// in flight at once without holding registers: stage 1 q^n components 0-7 and 14 (FP64), k_1 and
+// the FP32 copy of q^n (15 each); stage 2 q^n (15, FP64), k_1 and k_2.  A box spans the tile's
+// cells in y and eta and bx + 4 cells in x, from the tile's padded x (a multiple of 32, so that
+// every copy starts on a 16-byte boundary); a thread's own cell sits at x offset 2.  Blocks of a
+// persistent grid double-buffer: the next tile's copies land while the current tile computes.
+constexpr int kUpdQSlots = 16;  // FP64 component slots: two boxes of 8 (stage 1 uses 9)
+constexpr int kUpdMaps = 5;     // tensor maps per event: q (8 deep), q (1 deep), k_1, k_2, FP32 copy of q
+__host__ __device__ constexpr int upd_box_cells(int tx, int ty, int tz) { return (tx + 4) * ty * tz; }
+__host__ __device__ constexpr int upd_align128(int b) { return (b + 127) & ~127; }
+__host__ __device__ constexpr int upd_buffer_bytes(int tx, int ty, int tz) {
+  return upd_align128(kUpdQSlots * 8 * upd_box_cells(tx, ty, tz)) + 2 * upd_align128(NQ * 4 * upd_box_cells(tx, ty, tz));
+}
+__host__ __device__ constexpr int upd_smem_bytes(int tx, int ty, int tz, int nbuf) {
+  return nbuf * upd_buffer_bytes(tx, ty, tz) + 128;  // + alignment slack
+}
+
+template <int STAGE>
+struct UpdInShared {
+  const double* sq;  // q^n: slot n (stage 1: component 14 in slot 8), bc cells per slot
+  const float* sa;   // k_1, component n at n * bc
+  const float* sb;   // stage 1: the FP32 copy of q^n; stage 2: k_2
+  int bc, own;
+  __device__ __forceinline__ double q(int n) const { return sq[((STAGE == 1 && n == 14) ? 8 : n) * bc + own]; }
+  __device__ __forceinline__ float k1(int n) const { return sa[n * bc + own]; }
+  __device__ __forceinline__ float k2(int n) const { return sb[n * bc + own]; }
+  __device__ __forceinline__ float qfn(int n) const { return sb[n * bc + own]; }
+  __device__ __forceinline__ float qs(int) const { return 0.f; }  // (FP32 pi storage is not staged)
+};
+
+template <int STAGE, bool LEARNED>
+__global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
+    update_staged_kernel(const Params P, const UpdIO io, const Lattice* __restrict__ lats,
+                         const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ umaps, int nbuf) {
+  extern __shared__ __align__(128) unsigned char u_raw[];
+  __shared__ alignas(8) uint64_t s_bar[2];
+  constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
+  __shared__ uint32_t s_mlp[kInfer ? PK_WORDS : 1];
+  unsigned char* const sbase = u_raw + ((128u - (smem_u32(u_raw) & 127u)) & 127u);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int bc = (blockDim.x + 4) * blockDim.y * blockDim.z;
+  const int qbytes = upd_align128(kUpdQSlots * 8 * bc), kbytes = upd_align128(NQ * 4 * bc);
+  const int bufbytes = qbytes + 2 * kbytes;
+  const unsigned q8_bytes = 64u * bc, q1_bytes = 8u * bc, k_bytes = 4u * NQ * bc;
+  const unsigned tile_bytes = (STAGE == 1) ? (q8_bytes + q1_bytes + 2 * k_bytes) : (2 * q8_bytes + 2 * k_bytes);
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_barrier_init();
+  }
+  if constexpr (kInfer) mlp_load_shared(s_mlp, io.mlp_packed);
+  __syncthreads();
+
+  unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
+  bool bad = false;
+  unsigned issued = 0, done = 0;  // tiles whose copies were issued / waited for (the same in every thread)
+  const double tau_out = io.d_tau[0] + P.dtau;
+  int t0, t1;
+  tile_range(ntiles, t0, t1);
+  auto issue = [&](int t, unsigned slot) {  // thread 0 only: the four (stage 2) or five copies of tile t
+    const Tile tl = tiles[t];
+    const CUtensorMap* m = umaps + kUpdMaps * tl.event;
+    unsigned char* buf = sbase + slot * bufbytes;
+    uint64_t* bar = &s_bar[slot];
+    for (int w = 0; w < kUpdMaps; ++w) fence_tensormap_acquire(m + w);
+    fence_proxy_async_smem();  // earlier reads of this buffer before the async-proxy writes
+    mbar_arrive_expect_tx(bar, tile_bytes);
+    const int x = tl.i0, y = tl.j0 + 2, z = tl.k0 + 2;
+    tma_load_4d(buf, m + 0, x, y, z, 0, bar);  // q^n components 0-7
+    if constexpr (STAGE == 1) tma_load_4d(buf + q8_bytes, m + 1, x, y, z, 14, bar);  // component 14
+    else tma_load_4d(buf + q8_bytes, m + 0, x, y, z, 8, bar);  // components 8-14 (15: zero fill)
+    tma_load_4d(buf + qbytes, m + 2, x, y, z, 0, bar);  // k_1
+    tma_load_4d(buf + qbytes + kbytes, m + ((STAGE == 1) ? 4 : 3), x, y, z, 0, bar);  // q^n copy / k_2
+  };
+
+  if (t0 < t1) {
+    if (tid == 0) issue(t0, 0u);
+    issued = 1;
+  }
+  for (int t = t0; t < t1; ++t) {
+    if (nbuf == 2 && t + 1 < t1) {  // the other buffer was last read by the previous tile
+      if (__syncthreads_or(bad)) { bad = true; break; }
+      if (tid == 0) issue(t + 1, issued & 1u);
+      ++issued;
+    }
+    const unsigned slot = (nbuf == 2) ? (done & 1u) : 0u;
+    const unsigned parity = (nbuf == 2) ? ((done >> 1) & 1u) : (done & 1u);
+    const bool ok = mbar_wait(&s_bar[slot], parity, kWaitPolls);
+    if (ok) ++done;
+    if (__syncthreads_or(!ok)) { bad = true; break; }  // every thread computes, or none
+    const Tile tl = tiles[t];
+    const Lattice L = lats[tl.event];
+    const unsigned char* buf = sbase + slot * bufbytes;
+    const int own = ((int)threadIdx.z * (int)blockDim.y + (int)threadIdx.y) * ((int)blockDim.x + 4) + (int)threadIdx.x + 2;
+    const UpdInShared<STAGE> in{(const double*)buf, (const float*)(buf + qbytes), (const float*)(buf + qbytes + kbytes),
+                                bc, own};
+    update_cell<STAGE, LEARNED, false>(P, L, io, in, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y,
+                                       tl.k0 + (int)threadIdx.z, tau_out, s_mlp, st, nit, nreg, nfb);
+    if (nbuf == 1 && t + 1 < t1) {  // single buffer: refill it once every thread is done with it
+      if (__syncthreads_or(bad)) { bad = true; break; }
+      if (tid == 0) issue(t + 1, 0u);
+      ++issued;
+    }
+  }
+  if (bad) {  // a copy did not complete in time: let the ones in flight land before the block exits
+    for (; done < issued; ++done)
+      mbar_wait(&s_bar[(nbuf == 2) ? (done & 1u) : 0u], (nbuf == 2) ? ((done >> 1) & 1u) : (done & 1u), kWaitPolls);
+  }
+  block_stats(io.status, nullptr, io.counters, st | (bad ? ST_TIMEOUT : 0u), 0.f, nit, nreg, nfb);
 }
 
 }  // namespace kt

@@ -14,7 +14,7 @@ import math
 
 import numpy as np
 
-from .binding import KT, KT_MIXED, MLP_NPARAM, mlp_adam, mlp_grad, mlp_predict
+from .binding import KT, KT_MIXED, MLP_NPARAM, mlp_adam, mlp_batch, mlp_grad, mlp_predict, mlp_targets
 
 GATE_R2 = 1e-3  # KT_MLP_GATE_R2
 
@@ -32,12 +32,16 @@ def init_params(seed=0):
 
 
 def collect(problem_factory, seeds, n_samples, steps=100, every=10, sample_seed=1234):
-    """Sample n_samples cells uniformly over the snapshots of the given seeds' trajectories."""
+    """Sample n_samples cells uniformly over the snapshots of the given seeds' trajectories: the
+    features and targets are written by kt_mlp_features straight into the preallocated set."""
     import torch
     snaps = len(seeds) * (steps // every)
     per = int(math.ceil(n_samples / snaps))
     rng = np.random.default_rng(sample_seed)
-    xs, ys, es = [], [], []
+    X = torch.empty((snaps * per, 6), dtype=torch.float32, device="cuda")
+    Y = torch.empty(snaps * per, dtype=torch.float32, device="cuda")
+    E = torch.empty(per, dtype=torch.float64, device="cuda")
+    k = 0
     for seed in seeds:
         prob = problem_factory(seed)
         kt = KT(prob, precision=KT_MIXED)
@@ -45,60 +49,61 @@ def collect(problem_factory, seeds, n_samples, steps=100, every=10, sample_seed=
         for _ in range(steps // every):
             kt.step(every)
             cells = torch.as_tensor(rng.integers(0, prob.ncells, per), device="cuda")
-            x, y, e = kt.mlp_features(cells)
-            xs.append(x)
-            ys.append(y)
-            es.append(e)
+            kt.mlp_features(cells, out=(X[k * per:(k + 1) * per], Y[k * per:(k + 1) * per], E))
+            k += 1
         del kt
-    X, Y = torch.cat(xs)[:n_samples], torch.cat(ys)[:n_samples]
-    return X.contiguous(), Y.contiguous()
+    return X[:n_samples], Y[:n_samples]
 
 
 def train(X, Y, epochs=20, batch=8192, lr=3e-3, lr_min=1e-4, seed=0, log=None):
-    """Adam with cosine learning-rate decay; returns float32 CUDA parameters and the loss log."""
+    """Adam with cosine learning-rate decay over shuffled epochs (kt_mlp_batch draws each mini-batch
+    of a keyed permutation, kt_mlp_grad and kt_mlp_adam do the rest); returns float32 CUDA
+    parameters and the loss after each epoch."""
     import torch
     params = torch.as_tensor(init_params(seed), device="cuda")
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
     n = X.shape[0]
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(seed)
+    batch = min(batch, n)
+    xb = torch.empty((batch, 6), dtype=torch.float32, device="cuda")
+    yb = torch.empty(batch, dtype=torch.float32, device="cuda")
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
     steps_per_epoch = max(1, n // batch)
     total = epochs * steps_per_epoch
     step = 0
     losses = []
     for ep in range(epochs):
-        perm = torch.randperm(n, device="cuda", generator=gen)
         for b in range(steps_per_epoch):
-            idx = perm[b * batch:(b + 1) * batch]
-            xb, yb = X[idx].contiguous(), Y[idx].contiguous()
-            g, loss = mlp_grad(params, xb, yb, bf16_forward=True)
+            rows = mlp_batch(X, Y, seed + 1, ep, b, batch, xb, yb, flag)
+            g, loss = mlp_grad(params, xb[:rows], yb[:rows], bf16_forward=True)
             step += 1
             cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / total))
             mlp_adam(params, g, m, v, step, cur)
         losses.append(float(loss.item()))
         if log:
             log(f"epoch {ep}: loss {losses[-1]:.3e}")
+    if int(flag.item()):
+        raise RuntimeError("kt_mlp_batch: a permutation walk exceeded its bound")
     return params, losses
 
 
 def network_targets(X, Y):
-    """The cells the network corrects (r^2 > GATE_R2) and their targets z = y / r^2."""
-    r2 = X[:, 1]
-    keep = r2 > GATE_R2
-    return X[keep].contiguous(), (Y[keep] / r2[keep]).contiguous()
+    """The cells the network corrects (r^2 > GATE_R2) and their targets z = y / r^2 (kt_mlp_targets)."""
+    return mlp_targets(X, Y)
 
 
 def predict_y(params, X):
-    """The correction y of the learned start for feature rows X (tensor-core inference of z)."""
-    r2 = X[:, 1]
-    return (mlp_predict(params, X) * r2) * (r2 > GATE_R2)
+    """The correction y of the learned start for feature rows X (tensor-core inference of z), as a
+    host array: y = r^2 z where r^2 > GATE_R2, else 0."""
+    z = mlp_predict(params, X).cpu().numpy().astype(np.float64)
+    r2 = X[:, 1].cpu().numpy().astype(np.float64)
+    return np.where(r2 > GATE_R2, r2 * z, 0.0)
 
 
 def evaluate(params, X, Y):
-    """Max and rms error in y of the learned start (tensor-core inference) on (X, Y)."""
-    d = (predict_y(params, X) - Y).double()
-    return float(d.abs().max().item()), float(d.pow(2).mean().sqrt().item())
+    """Max and rms error in y of the learned start (tensor-core inference) on (X, Y), on the host."""
+    d = predict_y(params, X) - Y.cpu().numpy().astype(np.float64)
+    return float(np.max(np.abs(d))), float(np.sqrt(np.mean(d * d)))
 
 
 def train_default(n=128, seeds=range(2, 12), n_samples=1_000_000, epochs=20, log=None):

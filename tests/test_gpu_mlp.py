@@ -102,6 +102,45 @@ def test_adam_step_formula():
     np.testing.assert_allclose(P.cpu().numpy(), ref, rtol=1e-5, atol=1e-6)
 
 
+def test_training_targets_and_shuffled_batches():
+    """kt_mlp_targets keeps, in order, the rows whose feature 1 (r^2) exceeds the gate, with
+    z = y / r^2 (IEEE division: bit-equal to numpy's float32 division); kt_mlp_batch's batches of
+    an epoch cover every row exactly once, differ between epochs, and repeat for the same key."""
+    torch = _torch()
+    from paper_1608_06577_gb300.binding import mlp_batch, mlp_targets
+    from paper_1608_06577_gb300.learned import GATE_R2
+    rng = np.random.default_rng(3)
+    for n in (1, 1023, 1024, 1025, 70001):
+        X = rng.standard_normal((n, 6)).astype(np.float32)
+        X[:, 1] = rng.uniform(0.0, 2e-3, n).astype(np.float32)
+        Y = rng.standard_normal(n).astype(np.float32)
+        xo, zo = mlp_targets(torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda"))
+        keep = X[:, 1] > np.float32(GATE_R2)
+        assert np.array_equal(xo.cpu().numpy(), X[keep])
+        assert np.array_equal(zo.cpu().numpy(), Y[keep] / X[keep, 1])
+    for n, batch in ((1, 1), (1000, 128), (4097, 1000), (100000, 8192)):
+        X = np.repeat(np.arange(n, dtype=np.float32)[:, None], 6, axis=1)
+        Y = np.arange(n, dtype=np.float32)
+        tX, tY = torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")
+        xb = torch.empty((batch, 6), dtype=torch.float32, device="cuda")
+        yb = torch.empty(batch, dtype=torch.float32, device="cuda")
+        flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+        orders = []
+        for ep in (0, 1, 0):
+            seen = []
+            for b in range((n + batch - 1) // batch):
+                rows = mlp_batch(tX, tY, 7, ep, b, batch, xb, yb, flag)
+                seen.append(yb[:rows].cpu().numpy().copy())
+                assert np.array_equal(xb[:rows, 3].cpu().numpy(), seen[-1])
+            order = np.concatenate(seen)
+            assert np.array_equal(np.sort(order), Y)  # a permutation: every row exactly once
+            orders.append(order)
+        assert np.array_equal(orders[0], orders[2])
+        if n > 10:
+            assert not np.array_equal(orders[0], orders[1]) and not np.array_equal(orders[0], Y)
+        assert int(flag.item()) == 0
+
+
 @pytest.fixture(scope="module")
 def trained():
     from paper_1608_06577_gb300 import learned
@@ -148,12 +187,12 @@ def test_learned_inversion_accuracy_and_gain(trained):
     what the trained network gains: Newton steps per cell-stage against the same method with the
     network switched off (the conformal start e_conf alone) and against the plain root-find.
 
-    Measured result: the trained network does not beat its own conformal start here.  The
-    learned path accepts a root at |f| <= 1e-10 E, which one Newton step from any start within
-    ~1e-5 of the root reaches; e_conf is already that close in most cells (M^2/E^2 is small in
-    this workload), and a BF16 network cannot bring a start within 1e-10, so both need one step
-    in nearly every cell.  The test therefore asserts only that the network costs at most 5% more
-    steps than the conformal start, while both beat the plain root-find by a wide margin."""
+    Measured: 1.08 Newton steps per cell-stage with the trained network, 1.45 with the conformal
+    start alone, 3.16 with the plain root-find.  The learned path accepts a root at |f| <= 1e-10 E,
+    which one Newton step reaches from any start within ~1e-5 of the root; e_conf is that close
+    where M^2/E^2 is small, the network's correction brings the moving cells there too, and no
+    BF16 start is within 1e-10 of the root, so one step per cell is the floor.  Asserted: the
+    network saves at least 10% of the conformal start's steps, and both halve the plain count."""
     params, _, _, _ = trained
     p = _small(4)
     c = _newton_counts(p, params.cpu().numpy(), 40)
@@ -166,15 +205,16 @@ def test_learned_inversion_accuracy_and_gain(trained):
     assert rel < 1e-4
     assert fb < 0.02
     assert it_l < 0.5 * it_p and it_off < 0.5 * it_p
-    assert it_l <= 1.05 * it_off
+    assert it_l <= 0.9 * it_off
 
 
 def test_learned_start_near_tc_on_the_lattice_eos():
     """Where a start matters more: the paper's lattice EOS (Sec. 2.3), whose c_s^2 dips far below
     1/3 near T_c so that e_conf is a worse start, with eta/s = 0.2 and the zeta/s of Eq. (zetas).
     The network is trained on that EOS's own trajectories (other seeds) and compared with the
-    conformal start and the plain root-find on a held-out event; the counts are printed and the
-    same bounds as on the workload EOS are asserted."""
+    conformal start and the plain root-find on a held-out event.  Measured: 1.01 Newton steps per
+    cell-stage trained, 1.50 conformal start, 3.11 plain; the same bounds as on the workload EOS
+    are asserted."""
     from paper_1608_06577_gb300 import learned
     from workload.eos import lattice_table
     tab = lattice_table()
@@ -190,4 +230,4 @@ def test_learned_start_near_tc_on_the_lattice_eos():
           f"plain {it_p:.3f}")
     assert fb < 0.02
     assert it_l < 0.5 * it_p
-    assert it_l <= 1.05 * it_off
+    assert it_l <= 0.9 * it_off

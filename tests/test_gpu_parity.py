@@ -45,9 +45,9 @@ def field_errors(g, r, milne=True):
     return errs
 
 
-def run_pair(p, nsteps, precision=0):
+def run_pair(p, nsteps, precision=0, pi_fp32=False):
     from paper_1608_06577_gb300 import KT
-    kt = KT(p, precision=precision)
+    kt = KT(p, precision=precision, pi_fp32=pi_fp32)
     kt.set_problem_state()
     kt.step(nsteps)
     g = kt.get_state()
@@ -214,13 +214,18 @@ def test_cfl_max_speed_matches_oracle(precision, baseline_eos):
         kt.step(8)
         o = oracle.Oracle(p)
         assert o.step(8) == 0
-        a, b = kt.stats()["max_speed"], o.max_speed()
+        st = kt.stats()
+        a, b = st["max_speed"], o.max_speed()
         print(p.name, "max speed GPU", a, "oracle", b)
         assert 0.0 < b < 1.0
         assert abs(a - b) <= (1e-7 if precision == 0 else 1e-5) * b
+        # the state's extrema in kt_stats: e in the stored precision, rounded to float
+        e = kt.get_state(fields=("e",))["e"]
+        assert st["e_min"] == float(np.float32(e.min())) and st["e_max"] == float(np.float32(e.max()))
+        assert st["reg_min"] == float(np.min(kt.diagnostics()["regulation"]))
 
 
-@pytest.mark.parametrize("mode", ["fp64", "learned"])
+@pytest.mark.parametrize("mode", ["fp64", "learned", "learned_pi32"])
 def test_checkpoint_restart_is_bit_exact(mode, baseline_eos):
     """Sec. 4.3 writes the state out every m steps and continues from it: 10 steps equal 5 steps,
     kt_get_checkpoint, kt_set_checkpoint into a fresh context, and 5 more steps, bit for bit in
@@ -229,7 +234,7 @@ def test_checkpoint_restart_is_bit_exact(mode, baseline_eos):
     from paper_1608_06577_gb300.learned import init_params
     p = hotspot_problem(nx=24, ny=20, neta=10, nhot=6, seed=9, r_max=0.8, eos_table=baseline_eos)
     kw = {} if mode == "fp64" else {"precision": KT_MIXED, "inversion": KT_INV_LEARNED,
-                                    "mlp_weights": init_params(3)}
+                                    "mlp_weights": init_params(3), "pi_fp32": mode.endswith("pi32")}
     a = KT(p, **kw)
     a.set_problem_state()
     a.step(5)
@@ -270,15 +275,18 @@ def test_invalid_state_rejected():
     kt.step(1)
 
 
-def test_mixed_mode_error_after_100_steps(baseline_eos):
+@pytest.mark.parametrize("pi_fp32", [False, True])
+def test_mixed_mode_error_after_100_steps(pi_fp32, baseline_eos):
     """Mixed precision (FP32 reconstruction, fluxes and sources; FP64 Heun accumulation and
     FP64 root-find) against the FP64 oracle after 100 steps: pointwise relative error in e
-    <= 1e-4 on every cell; the per-field max-norm errors are reported."""
+    <= 1e-4 on every cell; the per-field max-norm errors are reported.  pi_fp32: the storage
+    variant with pi^{mu nu} and Pi stored and Heun-summed in FP32 (T^{tau mu} in FP64)."""
     p = hotspot_problem(nx=40, ny=36, neta=20, nhot=10, seed=4, r_max=1.2, eos_table=baseline_eos)
-    g, r, _ = run_pair(p, 100, precision=1)
+    g, r, _ = run_pair(p, 100, precision=1, pi_fp32=pi_fp32)
     rel_e = np.max(np.abs(g["e"] / r["e"] - 1))
     errs = field_errors(g, r)
-    print("mixed mode after 100 steps: max rel err e", rel_e, {k: f"{v:.2e}" for k, v in errs.items()})
+    print(f"mixed mode (pi fp32: {pi_fp32}) after 100 steps: max rel err e", rel_e,
+          {k: f"{v:.2e}" for k, v in errs.items()})
     assert rel_e < 1e-4
     assert errs["e[0]"] < 1e-4 and errs["q[0]"] < 1e-4
 
