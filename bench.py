@@ -57,6 +57,13 @@ SLOT_BYTES = {
     "mixed": {"stage1_rhs": 160, "stage1_update": 320, "stage2_rhs": 160, "stage2_update": 448},
     "learned": {"stage1_rhs": 160, "stage1_update": 320, "stage2_rhs": 160, "stage2_update": 448},
 }
+# The fused launch per stage: stage 1 reads qf 60,
+# u 16, u_prev 16, e, p 8, q (T, pi^{tau mu}, Pi) 72, qf at the cell 60 and writes k1 60, qsf 60, u
+# 16, e, p 8 = 376 (+ network output 4, learned); stage 2 reads qsf 60, u 16, u_prev 16, e, p 8,
+# q 120, k1 60 and writes q 120, qf 60, u 16, e, p 8 = 484 (+ 4, learned): 868 B per step, k never
+# leaves the SM within a stage.
+FUSED_SLOT_BYTES = {"stage1_rhs": 380, "stage2_rhs": 488}
+FUSED_FIRST_CANDIDATE = 24  # tuning candidates 24-35 are the fused launches (chosen only explicitly)
 SLOT_KERNEL = {"stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel", "stage1_update": "update_kernel",
                "stage2_update": "update_kernel", "tau_advance": "advance_tau_kernel"}
 LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
@@ -323,25 +330,56 @@ def run_ours(args, world, rank, local):
             tu = kt.tuning()
             best = min(range(len(tu["candidate_ms"])), key=lambda i: tu["candidate_ms"][i] or float("inf"))
             results[mode]["tuning"] = {"tile": list(tu["block"]), "grid_blocks": tu["grid_blocks"],
-                                       "candidate": best, "one_block_per_tile": bool(best % 2),
-                                       "update_inputs_staged_by_tma": best >= 12}
+                                       "candidate": best, "one_block_per_tile": bool(best % 2)}
         del kt
         torch.cuda.empty_cache()
 
+    # Measured alternatives of the mixed-precision layout on the autotuned tile shape and grid (the
+    # autotuner times only the split launches with direct reads): the update's inputs staged in
+    # shared memory by TMA, and one fused launch per stage
+    variants = None
+    if args.mode != "fp64" and not args.only_main:
+        variants = {}
+        base = results[args.mode]["tuning"]["candidate"]
+        for name, v in (("split_update_staged_by_tma", 1), ("fused_stage", 2)):
+            kt = make_kt(prob, args.mode, weights, stream)
+            kt.set_tuning(12 * v + base)
+            kt.set_problem_state()
+            kt.step(args.warmup)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            runs = []
+            for _ in range(REPEATS):
+                barrier(world)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                kt.step(args.steps)
+                ev1.record(stream)
+                ev1.synchronize()
+                runs.append(max_over_ranks(ev0.elapsed_time(ev1), world) / args.steps)
+            variants[name] = {"candidate": 12 * v + base, "ms_per_step": statistics.median(runs),
+                              "runs_ms_per_step": runs, "slots_ms": kt.time_kernels(3)}
+            del kt
+            torch.cuda.empty_cache()
+
     main = results[args.mode]
     ms_step = main["ms_per_step"]
-    bpc = BYTES_PER_CELL[args.mode]
+    fused = args.mode != "fp64" and main.get("tuning", {}).get("candidate", 0) >= FUSED_FIRST_CANDIDATE
+    slot_bytes = FUSED_SLOT_BYTES if fused else SLOT_BYTES[args.mode]
+    bpc = sum(slot_bytes.values())
     alg = ALG_BYTES_PER_CELL[args.mode]
     # per kernel: launches per step, average launch time, algorithmic bytes per launch, GB/s
     kernels = {}
     for slot, t in main["slots_ms"].items():
-        if t <= 0.0:
+        if t <= 0.0 or (fused and slot.endswith("update")):  # (fused: the update slots are empty)
             continue
-        k = kernels.setdefault("stage_kernel" if args.mode == "fp64" and slot.endswith("rhs") else SLOT_KERNEL[slot],
-                               {"launches_per_step": 0, "ms_per_step": 0.0, "bytes_per_step": 0.0})
+        name = SLOT_KERNEL[slot]
+        if slot.endswith("rhs") and (args.mode == "fp64" or fused):
+            name = "stage_kernel" if args.mode == "fp64" else "fused_kernel"
+        k = kernels.setdefault(name, {"launches_per_step": 0, "ms_per_step": 0.0, "bytes_per_step": 0.0})
         k["launches_per_step"] += 1
         k["ms_per_step"] += t
-        k["bytes_per_step"] += cells * SLOT_BYTES[args.mode].get(slot, 8.0 / cells)
+        k["bytes_per_step"] += cells * slot_bytes.get(slot, 8.0 / cells)
     for k in kernels.values():
         k["avg_launch_ms"] = k["ms_per_step"] / k["launches_per_step"]
         k["gbs"] = k["bytes_per_step"] / (k["ms_per_step"] * 1e-3) / 1e9
@@ -351,7 +389,8 @@ def run_ours(args, world, rank, local):
     dom = max(kernels, key=lambda n: kernels[n]["ms_per_step"])
     traffic_k = None if args.large else MEASURED_TRAFFIC.get((args.mode, n))
     traffic = None
-    if traffic_k:  # DRAM bytes per step: every kernel's recorded traffic per launch times its launches
+    if traffic_k and all(k in traffic_k for k in kernels if k != "advance_tau_kernel"):
+        # DRAM bytes per step: every kernel's recorded traffic per launch times its launches
         traffic = sum(traffic_k[k] * v["launches_per_step"] for k, v in kernels.items() if k in traffic_k)
     achieved = cells * alg / (ms_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -446,10 +485,10 @@ def run_ours(args, world, rank, local):
                               "newton_iters_per_cell_stage": r["stats"]["newton_iters"] / ncs(r),
                               "fallbacks_per_cell_stage": r["stats"]["fallbacks"] / ncs(r)}
                           for m, r in results.items()},
-                "fp64_pipe": fp64_pipe,
+                "fp64_pipe": fp64_pipe, "layout_variants": variants,
                 "learned_training": train_info,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": LAUNCHES_PER_STEP["fp64" if args.mode == "fp64" else "mixed"] * main["steps"]}
+                "gpu_launches": (3 if (args.mode == "fp64" or fused) else 5) * main["steps"]}
         print(json.dumps(line), flush=True)
 
 

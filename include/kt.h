@@ -247,12 +247,16 @@ int kt_get_state_event(kt_ctx* ctx, int event, double* tau, double* e, double* u
                        int on_device);
 /* The tile shape in use (threads per block x, y, z), the grid size in blocks and, after
  * autotuning, the measured first-stage time in ms of each candidate (up to *n_candidates
- * entries; *n_candidates is set to the number of candidates, 24; candidates that do not apply
- * to the context report 0).  Candidate 12 v + 2 s + g is tile shape s of (32,4,2), (32,8,1),
- * (32,2,4), (32,1,8), (32,4,1), (32,2,2) with g = 0 a persistent grid (as many blocks as are
- * resident at once, each walking the tile table) or g = 1 one block per tile, and v = 1 (KT_MIXED
- * with FP64 pi storage only) the update kernels' inputs staged in shared memory by TMA bulk copies
- * of each tile (double-buffered on a persistent grid) instead of read by each thread. */
+ * entries; *n_candidates is set to the number of candidates, 36; candidates not timed report 0).
+ * Candidate 12 v + 2 s + g is tile shape s of (32,4,2), (32,8,1), (32,2,4), (32,1,8), (32,4,1),
+ * (32,2,2) with g = 0 a persistent grid (as many blocks as are resident at once, each walking the
+ * tile table) or g = 1 one block per tile, and, for KT_MIXED with FP64 pi storage, the variant v:
+ * 0 a right-hand-side and an update launch per stage; 1 the same with the update kernels' inputs
+ * staged in shared memory by TMA bulk copies of each tile (double-buffered on a persistent grid);
+ * 2 (face velocities by reconstruction) one fused launch per stage, right-hand side and update.
+ * The autotuner times the candidates with v = 0 only (the other variants measured slower over a
+ * whole step); kt_set_tuning selects any.  The FP64 mode and other KT_MIXED options use v = 0
+ * whatever v is asked for. */
 int kt_get_tuning(kt_ctx* ctx, int* block_xyz, int* grid_blocks, float* candidate_ms, int* n_candidates);
 /* Use candidate `candidate` (numbered as above) from now on, without autotuning; KT_ERR_ARG if it
  * is out of range.  The results do not depend on the candidate: every candidate runs the same

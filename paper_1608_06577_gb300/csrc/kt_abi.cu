@@ -32,9 +32,13 @@ struct Shape {
 constexpr Shape kShapes[] = {{32, 4, 2}, {32, 8, 1}, {32, 2, 4}, {32, 1, 8}, {32, 4, 1}, {32, 2, 2}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 // candidates: every shape with a persistent grid (blocks resident at once) and with one block per tile,
-// each (mixed precision) with the update kernel reading its inputs directly or staged by TMA
+// each (mixed precision) as a right-hand-side and an update launch per stage, the update reading
+// its inputs directly or staged by TMA, or as one fused launch per stage.  The autotuner times the
+// first 12 (two launches per stage, direct reads): the other two variants measured slower over a
+// whole step and are selected only by kt_set_tuning.
+constexpr int kNumTuned = 2 * kNumShapes;
 constexpr int kNumBase = 2 * kNumShapes;
-constexpr int kNumCandidates = 2 * kNumBase;
+constexpr int kNumCandidates = 3 * kNumBase;
 
 struct Ctx {
   kt_options opt;
@@ -71,6 +75,7 @@ struct Ctx {
   CUtensorMap* d_tmaps = nullptr;  // mixed precision: per event, the 4-d maps of qf (first nev) and qsf
   CUtensorMap* d_umaps = nullptr;  // mixed precision: per event, the kUpdMaps maps of the staged update
   int staged = 0;                  // the update kernels read their inputs staged by TMA
+  int fused = 0;                   // one fused launch per stage (right-hand side + update)
   int upd_nbuf = 1;                // staged update: buffers per block (2 on a persistent grid)
   float* reg = nullptr;            // regulation factor of the last step, per cell (diagnostics)
   float* z_net = nullptr;          // learned start: the network's output per cell within a step
@@ -551,6 +556,14 @@ int allow_rhs_smem(Ctx* c) {
   set((const void*)rhs_kernel<2, false, false>);
   set((const void*)rhs_kernel<2, true, true>);
   set((const void*)rhs_kernel<2, false, true>);
+  set((const void*)fused_kernel<1, true, false, true>);
+  set((const void*)fused_kernel<1, true, false, false>);
+  set((const void*)fused_kernel<1, false, false, true>);
+  set((const void*)fused_kernel<1, false, false, false>);
+  set((const void*)fused_kernel<2, true, false, true>);
+  set((const void*)fused_kernel<2, true, false, false>);
+  set((const void*)fused_kernel<2, false, false, true>);
+  set((const void*)fused_kernel<2, false, false, false>);
   if (e != cudaSuccess) return fail(c, KT_ERR_CUDA, "rhs shared memory: %s", cudaGetErrorString(e));
   bytes = 0;
   for (const auto& sh : kShapes) bytes = std::max(bytes, upd_smem_bytes(sh.x, sh.y, sh.z, 2));
@@ -587,8 +600,34 @@ void launch_update(Ctx* c, const UpdIO& uio) {
     update_kernel<STAGE, false, false><<<c->grid_upd, blk, 0, c->stream>>>(c->P, uio, c->d_lat, c->d_tiles, c->ntiles);
 }
 
+// the fused stage kernel (right-hand side and update in one launch)
+template <int STAGE>
+void launch_fused(Ctx* c, const StageIO<float>& io, const UpdIO& uio) {
+  const Shape& s = kShapes[c->shape];
+  const dim3 blk(s.x, s.y, s.z);
+  const CUtensorMap* maps = c->d_tmaps + (STAGE == 1 ? 0 : c->nev);
+  const size_t sm = rhs_smem_bytes(s.x, s.y, s.z);
+  const bool t1 = (c->P.theta == 1.0);
+  if (t1 && c->learned)
+    fused_kernel<STAGE, true, false, true><<<c->grid_rhs, blk, sm, c->stream>>>(c->P, io, uio, c->d_lat, c->d_tiles,
+                                                                               c->ntiles, maps);
+  else if (t1)
+    fused_kernel<STAGE, true, false, false><<<c->grid_rhs, blk, sm, c->stream>>>(c->P, io, uio, c->d_lat, c->d_tiles,
+                                                                                c->ntiles, maps);
+  else if (c->learned)
+    fused_kernel<STAGE, false, false, true><<<c->grid_rhs, blk, sm, c->stream>>>(c->P, io, uio, c->d_lat, c->d_tiles,
+                                                                                c->ntiles, maps);
+  else
+    fused_kernel<STAGE, false, false, false><<<c->grid_rhs, blk, sm, c->stream>>>(c->P, io, uio, c->d_lat, c->d_tiles,
+                                                                                 c->ntiles, maps);
+}
+
 template <int STAGE>
 void launch_split_stage(Ctx* c, const StageIO<float>& io, const UpdIO& uio) {
+  if (c->fused) {
+    launch_fused<STAGE>(c, io, uio);
+    return;
+  }
   launch_rhs<STAGE>(c, io);
   launch_update<STAGE>(c, uio);
 }
@@ -604,6 +643,16 @@ void mark(Ctx* c, cudaEvent_t* ev, int i) {
 template <typename R>
 void launch_step_stages(Ctx* c, cudaEvent_t* ev) {
   if constexpr (sizeof(R) == 4) {
+    if (c->fused) {  // the fused launches take the right-hand-side slots; the update slots stay empty
+      mark(c, ev, 0);
+      launch_fused<1>(c, make_io<float>(c, 1), make_uio(c, 1));
+      mark(c, ev, 1);
+      mark(c, ev, 2);
+      launch_fused<2>(c, make_io<float>(c, 2), make_uio(c, 2));
+      mark(c, ev, 3);
+      mark(c, ev, 4);
+      return;
+    }
     mark(c, ev, 0);
     launch_rhs<1>(c, make_io<float>(c, 1));
     mark(c, ev, 1);
@@ -708,8 +757,10 @@ int encode_tensor_maps(Ctx* c) {
 }
 
 int select_shape(Ctx* c, int cand) {
-  const int base = cand % kNumBase, shape = base / 2, one_per_tile = base % 2;
-  c->staged = (cand >= kNumBase) && c->mixed && !c->pi32;
+  const int base = cand % kNumBase, shape = base / 2, one_per_tile = base % 2, variant = cand / kNumBase;
+  const bool fusable = c->mixed && !c->pi32 && !c->P.iface_invert;
+  c->staged = (variant == 1) && c->mixed && !c->pi32;
+  c->fused = (variant == 2) && fusable;
   c->upd_nbuf = one_per_tile ? 1 : 2;
   std::vector<Tile> tiles;
   build_tiles(c->lat, kShapes[shape], tiles);
@@ -725,7 +776,9 @@ int select_shape(Ctx* c, int cand) {
   const Shape& sh = kShapes[shape];
   auto grid = [&](int cap) { return one_per_tile ? c->ntiles : std::max(1, std::min(cap, c->ntiles)); };
   if (c->mixed) {
-    c->grid_rhs = grid(occupancy_blocks(rhs_kernel<1, true, false>, sh, rhs_smem_bytes(sh.x, sh.y, sh.z)));
+    const size_t rsm = rhs_smem_bytes(sh.x, sh.y, sh.z);
+    c->grid_rhs = grid(c->fused ? occupancy_blocks(fused_kernel<1, true, false, true>, sh, rsm)
+                                : occupancy_blocks(rhs_kernel<1, true, false>, sh, rsm));
     if (c->staged) {
       const size_t usm = upd_smem_bytes(sh.x, sh.y, sh.z, c->upd_nbuf);
       c->grid_upd = grid(c->learned ? occupancy_blocks(update_staged_kernel<2, true>, sh, usm)
@@ -777,9 +830,8 @@ int time_first_stage(Ctx* c, float* ms) {
 int autotune(Ctx* c) {
   Range range_("kt autotune");
   int best = 0;
-  const int ncand = (c->mixed && !c->pi32) ? kNumCandidates : kNumBase;  // staging applies to the FP64-pi update
   for (int s = 0; s < kNumCandidates; ++s) c->tune_ms[s] = 0.f;
-  for (int s = 0; s < ncand; ++s) {
+  for (int s = 0; s < kNumTuned; ++s) {
     int rc = select_shape(c, s);
     if (rc != KT_OK) return rc;
     float ms = 0.f;

@@ -199,9 +199,9 @@ __device__ __forceinline__ unsigned invert_split(const Params& P, double gnn, co
     }
     P0 = e * (1.0 / 3.0);
   } else if (LEARNED) {
-    st = rootfind_learned(P, E, E + Pi, M2, d2f_bits(M2), start, e, P0, iters, fallbacks);
+    st = rootfind_learned(P, E, E + Pi, M2, d2f_trunc(M2), start, e, P0, iters, fallbacks);
   } else {
-    st = rootfind_plain(P, E, E + Pi, M2, d2f_bits(M2), start, e, P0, iters);
+    st = rootfind_plain(P, E, E + Pi, M2, d2f_trunc(M2), start, e, P0, iters);
   }
   if (st) {
     uo[0] = 1.f;
@@ -254,8 +254,10 @@ __device__ __forceinline__ float pi32_state(const In& in, int n) {
   else return 0.5f * (in.qfn(n) + in.qs(n) + in.k2(n));
 }
 
-// One cell; all lanes of the warp call it together (the learned start is warp-wide).
-template <int STAGE, bool LEARNED, bool PI32, typename In>
+// One cell; all lanes of the warp call it together (the learned start is warp-wide).  STORE_K1
+// (stage 1 of the fused stage kernel, whose k_1 exists only in shared memory): write all of k_1
+// to the field array for the second stage, its pi components carrying the regulator's rescaling.
+template <int STAGE, bool LEARNED, bool PI32, typename In, bool STORE_K1 = false>
 __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, const UpdIO& io, const In& in, int i,
                                             int j, int k, double tau_out, const uint32_t* s_mlp, unsigned& st,
                                             unsigned& nit, unsigned& nreg, unsigned& nfb) {
@@ -332,6 +334,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   const float eR = from_f64<float>(e), P0R = from_f64<float>(P0);
 
   // e) regulator (Eq. regPimunu), after the root-find, on pi only
+  bool k1_pi_written = false;  // STORE_K1: the pi components of k_1 were written rescaled
   if (P.regulate) {
     const float go = P.milne ? from_f64<float>(tau_out * tau_out) : 1.f;
     float pm[4][4];
@@ -355,6 +358,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
           io.k1[n * fs + c] = fmaf(f, in.k1(n), (f - 1.f) * in.qfn(n));
           qr[n] *= f;
         }
+        k1_pi_written = true;
       } else {  // rescale the FP64 state in registers (re-reading its inputs would miss L2)
         const double fd = to_f64<float>(f);
 #pragma unroll
@@ -372,6 +376,11 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
 #pragma unroll
       for (int n = 8; n < 14; ++n) qn[n] = q8[n - 8] + to_f64<float>(inc8[n - 8]);
     }
+  }
+  if constexpr (STORE_K1 && STAGE == 1 && !PI32) {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n)
+      if (n < 4 || n > 13 || !k1_pi_written) io.k1[n * fs + c] = in.k1(n);
   }
 #pragma unroll
   for (int n = 0; n < NQ; ++n)
@@ -529,6 +538,133 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
       mbar_wait(&s_bar[(nbuf == 2) ? (done & 1u) : 0u], (nbuf == 2) ? ((done >> 1) & 1u) : (done & 1u), kWaitPolls);
   }
   block_stats(io.status, nullptr, io.counters, st | (bad ? ST_TIMEOUT : 0u), 0.f, nit, nreg, nfb);
+}
+
+// ---------------------------------------------------------------- fused stage (one launch per stage)
+// The right-hand side and the update of a tile in one kernel: the FP32 stencil of rhs_kernel gives
+// k = dtau C[q] in registers, which goes to shared memory (the staging buffer the last-but-one
+// component group used, free by then) instead of a field array, and the update of update_kernel
+// reads it from there.  Each stage thus skips the write and read of its k (120 B per cell), and
+// blocks of an SM in different phases keep the FP32 pipes (stencil) and the FP64 pipe (Heun sums,
+// root-find) busy at the same time.  Stage 1 still writes k_1 for the second stage's Heun sum.
+template <int STAGE>
+struct UpdInFused {
+  const UpdIO& io;
+  long long fs, c;
+  const float* sk;  // this stage's k: component n at sk[n * kst]
+  int kst;
+  __device__ __forceinline__ double q(int n) const { return __ldg(io.q + n * fs + c); }
+  __device__ __forceinline__ float k1(int n) const {
+    if constexpr (STAGE == 1) return sk[n * kst];
+    else return __ldg(io.k1 + n * fs + c);
+  }
+  __device__ __forceinline__ float k2(int n) const { return sk[n * kst]; }
+  __device__ __forceinline__ float qfn(int n) const { return __ldg(io.qf_n + n * fs + c); }
+  __device__ __forceinline__ float qs(int) const { return 0.f; }  // (FP32 pi storage is not fused)
+};
+
+// 128 registers (16 warps of 128-thread tiles per SM): with the rhs kernel's 96 the two phases
+// spilled 500 bytes per thread and the launch ran 10% slower.
+template <int STAGE, bool TH1, bool IFACE, bool LEARNED>
+__global__ void __maxnreg__(128)
+    fused_kernel(const Params P, const StageIO<float> io, const UpdIO uio, const Lattice* __restrict__ lats,
+                 const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ tmaps) {
+  extern __shared__ __align__(128) float s_raw[];
+  __shared__ alignas(8) uint64_t s_bar[2];
+  constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
+  __shared__ uint32_t s_mlp[kInfer ? PK_WORDS : 1];
+  float* const s_q = s_raw + ((32u - ((smem_u32(s_raw) >> 2) & 31u)) & 31u);  // TMA wants 128-byte buffers
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int bx = blockDim.x + 4, by = blockDim.y + 4, bz = blockDim.z + 4;
+  const int vol = bx * by * bz;                  // floats per component in a buffer
+  const unsigned box_bytes = 4u * kCompPerBox * vol;
+  const int bfl = rhs_buffer_floats(blockDim.x, blockDim.y, blockDim.z);
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_barrier_init();
+  }
+  if constexpr (kInfer) mlp_load_shared(s_mlp, uio.mlp_packed);
+  __syncthreads();
+
+  float amax = 0.f;
+  bool bad = false;
+  unsigned issued = 0, done = 0;  // TMA copies issued and waited for (the same in every thread)
+  unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
+  const double tau_n = io.d_tau[0];
+  const double tau_out = tau_n + P.dtau;
+  const CellGeom<float> G = cell_geom<float>(P, (STAGE == 1) ? tau_n : tau_out);
+  const float th = pr<float>(P).theta;
+  const int sy = bx, sz = bx * by;
+  const int own = ((int)threadIdx.z + 2) * sz + ((int)threadIdx.y + 2) * sy + (int)threadIdx.x + 2;
+  auto stage_group = [&](const CUtensorMap* map, const Tile& tl, int g) {  // thread 0 only
+    const unsigned b = issued & 1u;
+    fence_proxy_async_smem();  // earlier accesses of this buffer before the async-proxy write
+    mbar_arrive_expect_tx(&s_bar[b], box_bytes);
+    tma_load_4d(s_q + b * bfl, map, tl.i0, tl.j0, tl.k0, kCompPerBox * g, &s_bar[b]);
+  };
+
+  int t0, t1;
+  tile_range(ntiles, t0, t1);
+  for (int t = t0; t < t1; ++t) {
+    const Tile tl = tiles[t];
+    const Lattice L = lats[tl.event];
+    const CUtensorMap* map = tmaps + tl.event;
+    if (__syncthreads_or(bad)) { bad = true; break; }  // every thread is done with both buffers
+    if (tid == 0) {
+      fence_tensormap_acquire(map);
+      stage_group(map, tl, 0);
+    }
+    ++issued;
+
+    const int i = tl.i0 + (int)threadIdx.x, j = tl.j0 + (int)threadIdx.y, k = tl.k0 + (int)threadIdx.z;
+    const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
+    const long long c = valid ? L.idx(i + 2, j + 2, k + 2) : 0;
+    // ---- the right-hand side (as rhs_kernel)
+    float dq[NQ], uc[4], du[4][4], dv = 0.f;
+    Faces<float> Fx, Fy, Fz;
+    if (valid) {
+      cell_faces<float, TH1, IFACE>(P, L, io, c, u_global(L, io, c), G, dq, uc, du, dv, amax, Fx, Fy, Fz);
+      cell_sources<float>(P, L, io, c, G, uc, du, dv, dq);
+    }
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+      if (g + 1 < kGroups) {
+        if (__syncthreads_or(bad)) { bad = true; break; }
+        if (tid == 0) stage_group(map, tl, g + 1);
+        ++issued;
+      }
+      const unsigned b = done & 1u;
+      if (!mbar_wait(&s_bar[b], (done >> 1) & 1u, kWaitPolls)) { bad = true; continue; }
+      ++done;
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < kCompPerBox; ++m)
+          if (kCompPerBox * g + m < NQ)
+            component_rhs<float, true, TH1>(P, kCompPerBox * g + m, s_q + b * bfl + m * vol + own, 1, sy, sz, th,
+                                            Fx, Fy, Fz, dq);
+      }
+    }
+    if (__syncthreads_or(bad)) { bad = true; break; }  // the update runs for every tile of every block, or none
+    // ---- k into the buffer the last-but-one group used (every thread has passed the barrier
+    //      that issued the last group, so it is free until the next tile's first copy)
+    float* const sk = s_q + (done & 1u) * bfl + tid;
+    if (valid) {
+      const float dt = pr<float>(P).dtau;
+#pragma unroll
+      for (int n = 0; n < NQ; ++n) sk[n * nthr] = dq[n] * dt;
+    }
+    // ---- the update (as update_kernel), reading k from shared memory
+    const UpdInFused<STAGE> in{uio, L.fstride, L.idx(i + 2, j + 2, k + 2), sk, nthr};
+    update_cell<STAGE, LEARNED, false, UpdInFused<STAGE>, true>(P, L, uio, in, i, j, k, tau_out, s_mlp, st, nit,
+                                                                  nreg, nfb);
+    fence_proxy_async_smem();  // this thread's generic accesses of the buffer before the next copy into it
+  }
+  if (bad) {  // a copy did not complete in time: let the ones in flight land before the block exits
+    for (; done < issued; ++done) mbar_wait(&s_bar[done & 1u], (done >> 1) & 1u, kWaitPolls);
+  }
+  block_stats(io.status, io.max_speed_bits, io.counters, st | (bad ? ST_TIMEOUT : 0u), amax, nit, nreg, nfb);
 }
 
 }  // namespace kt

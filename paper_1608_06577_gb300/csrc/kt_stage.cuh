@@ -320,7 +320,7 @@ __device__ __forceinline__ double clamp_pos(double x, double lo, double hi) {  /
 __device__ __forceinline__ int eos_interval_pos(const Params& P, double e) {
   const EosSeg<double>* seg = P.seg_d;
   const int n1 = P.eos_n - 2;
-  const float g = (__logf(d2f_bits(e)) - P.lne0) * P.inv_h;
+  const float g = (__logf(d2f_trunc(e)) - P.lne0) * P.inv_h;
   int i = (g > 0.f) ? (int)g : 0;  // NaN compares false -> 0
   i = min(i, n1);
   const long long b = obits(e);
@@ -350,9 +350,9 @@ __device__ __forceinline__ Resid residual(const Params& P, double e, double E, d
   const double em = e - E;
   r.g = fma(em, r.A, M2);
   const EosSeg<float>& sf = P.seg_f[i];
-  const float df = d2f_bits(d);
+  const float df = d2f_trunc(d);
   const float c2 = fmaf(df, fmaf(df, 3.f * sf.a3, 2.f * sf.a2), sf.a1);
-  const float Af = d2f_bits(r.A);
+  const float Af = d2f_trunc(r.A);
   r.gp = Af - __fdividef(M2f * c2, Af);
   return r;
 }
@@ -416,7 +416,7 @@ __device__ __forceinline__ unsigned invert_fp64(const Params& P, double tau, con
     if (e < P.e_min) e = P.e_min;
     P0 = e * (1.0 / 3.0);
   } else {
-    st = rootfind_plain(P, E, E + Pi, M2, d2f_bits(M2), guess, e, P0, iters);
+    st = rootfind_plain(P, E, E + Pi, M2, d2f_trunc(M2), guess, e, P0, iters);
   }
   if (st) {
     uo[0] = 1.0; uo[1] = uo[2] = uo[3] = 0.0;
@@ -738,16 +738,16 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
 // gives z, which is returned in z_io (a warp whose cells all have r^2 <= kMlpGateR2 skips it);
 // otherwise (the second stage, whose state differs by O(dtau)) z_io holds that z on entry.  All
 // 32 lanes of the warp call it together.  E, M^2 in single precision from the FP64 components
-// (they only feed the features).
+// (they only feed the features and the start).
 template <bool INFER>
 __device__ __forceinline__ double learned_start(const Params& P, double gnn, const double (&qn)[NQ],
                                                 const uint32_t* s_mlp, float& z_io) {
-  const float Ef = d2f_bits(qn[0]) - d2f_bits(qn[4]);
-  const float Mx = d2f_bits(qn[1]) - d2f_bits(qn[5]), My = d2f_bits(qn[2]) - d2f_bits(qn[6]),
-              Mn = d2f_bits(qn[3]) - d2f_bits(qn[7]);
-  const float M2f = fmaf(Mx, Mx, fmaf(My, My, d2f_bits(gnn) * Mn * Mn));
+  const float Ef = d2f_trunc(qn[0]) - d2f_trunc(qn[4]);
+  const float Mx = d2f_trunc(qn[1]) - d2f_trunc(qn[5]), My = d2f_trunc(qn[2]) - d2f_trunc(qn[6]),
+              Mn = d2f_trunc(qn[3]) - d2f_trunc(qn[7]);
+  const float M2f = fmaf(Mx, Mx, fmaf(My, My, d2f_trunc(gnn) * Mn * Mn));
   float x[MLP_IN], ecE;
-  mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_bits(qn[14]), x, ecE);
+  mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_trunc(qn[14]), x, ecE);
   if constexpr (INFER) z_io = __any_sync(0xffffffffu, x[1] > kMlpGateR2) ? mlp_warp_infer(s_mlp, x) : 0.f;
   const float y = (x[1] > kMlpGateR2) ? x[1] * z_io : 0.f;
   return f2d_bits(Ef * ecE * __expf(0.1f * y));

@@ -65,9 +65,9 @@ def test_autotuner_reports_and_picks_fastest():
     t = k.tuning()
     ms = [m for m in t["candidate_ms"] if m > 0]
     shapes = [(32, 4, 2), (32, 8, 1), (32, 2, 4), (32, 1, 8), (32, 4, 1), (32, 2, 2)]
-    # 2 grid variants per shape, each with the update reading its inputs directly or staged by TMA
-    assert len(ms) == len(t["candidate_ms"]) == 4 * len(shapes)
-    assert t["block"] == shapes[(int(np.argmin(t["candidate_ms"])) % (2 * len(shapes))) // 2]
+    # 2 grid variants per shape are timed (the staged and fused variants are selected explicitly)
+    assert len(t["candidate_ms"]) == 6 * len(shapes) and len(ms) == 2 * len(shapes)
+    assert t["block"] == shapes[int(np.argmin(ms)) // 2]
     assert t["grid_blocks"] >= 1
 
 
@@ -75,14 +75,14 @@ def test_autotuner_reports_and_picks_fastest():
 def test_grid_variants_are_bit_identical(learned):
     """Every autotuner candidate runs the same arithmetic on the same tiles: every tile shape, with a
     persistent grid or one block per tile, with the update's inputs read directly or staged in
-    shared memory by TMA, gives the same state, bit for bit."""
+    shared memory by TMA, as split or fused launches, gives the same state, bit for bit."""
     from paper_1608_06577_gb300 import KT, learned as lm
     p = hotspot_problem(nx=72, ny=56, neta=20, nhot=12, r_max=2.0)
     kw = dict(inversion=1, mlp_weights=lm.init_params(3)) if learned else {}
     shapes = [(32, 4, 2), (32, 8, 1), (32, 2, 4), (32, 1, 8), (32, 4, 1), (32, 2, 2)]
     ref = None
-    # shapes (32,4,2), (32,8,1) per tile, (32,4,1), (32,2,2) per tile; then the same staged
-    for cand in (0, 3, 8, 11, 12, 15, 20, 23):
+    # shapes (32,4,2), (32,8,1) per tile, (32,4,1), (32,2,2) per tile; then the same staged, fused
+    for cand in (0, 3, 8, 11, 12, 15, 20, 23, 24, 27, 32, 35):
         k = KT(p, precision=1, **kw)
         k.set_tuning(cand)
         k.set_problem_state()
