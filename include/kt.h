@@ -226,6 +226,13 @@ int kt_selftest_wait(kt_ctx* ctx, unsigned polls);
  * double; other b take the IEEE division.  KT_ERR_ARG for null pointers or n < 0. */
 int kt_selftest_div(const double* a, const double* b, double* q, long long n, void* stream);
 
+/* Self-test of the double -> float conversions the mixed-precision kernels do with integer
+ * instructions (the paper has no counterpart): for n device-resident x, rn[i] is x[i] rounded to
+ * nearest even (the stored FP32 copies), rz[i] x[i] with its mantissa truncated (values that only
+ * steer a computation).  Both flush magnitudes below 2^-126 to zero; rn gives infinity for
+ * overflow, infinity and NaN; rz assumes |x| < 2^128.  KT_ERR_ARG for null pointers or n < 0. */
+int kt_selftest_cvt(const double* x, float* rn, float* rz, long long n, void* stream);
+
 int kt_get_stats(kt_ctx* ctx, kt_stats* stats);
 const char* kt_last_error(const kt_ctx* ctx);
 void kt_free(kt_ctx* ctx);

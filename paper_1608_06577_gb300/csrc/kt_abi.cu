@@ -370,6 +370,15 @@ __global__ void state_extrema_kernel(const Lattice L, const R* __restrict__ e, c
   }
 }
 
+// self-test of the integer-pipe double -> float conversions (rounded and truncating)
+__global__ void cvt_selftest_kernel(const double* __restrict__ x, float* rn, float* rz, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    rn[i] = d2f_bits(x[i]);
+    rz[i] = d2f_trunc(x[i]);
+  }
+}
+
 // self-test of the FP64 division of the stencil (vdiv) on caller-given operands
 __global__ void div_selftest_kernel(const double* __restrict__ a, const double* __restrict__ b, double* q,
                                     long long n) {
@@ -1372,6 +1381,13 @@ int kt_selftest_wait(kt_ctx* c, unsigned polls) {
   CK(cudaStreamSynchronize(c->stream));
   if (st & ST_TIMEOUT) return fail(c, KT_ERR_TIMEOUT, "kt_selftest_wait: the wait gave up after %u polls", polls);
   return KT_OK;
+}
+
+int kt_selftest_cvt(const double* x, float* rn, float* rz, long long n, void* stream) {
+  if (!x || !rn || !rz || n < 0) return KT_ERR_ARG;
+  if (n == 0) return KT_OK;
+  cvt_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, rn, rz, n);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ERR_CUDA;
 }
 
 int kt_selftest_div(const double* a, const double* b, double* q, long long n, void* stream) {

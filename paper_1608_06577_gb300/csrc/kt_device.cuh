@@ -296,7 +296,7 @@ __device__ __forceinline__ R ln_zeta_over_s(const Params& P, R T) {
 // instructions issue on the FP64 pipe, which has 1/64 of the FP32 rate; these bit-level
 // versions leave it free.  float -> double is exact (subnormal floats flush to zero);
 // double -> float rounds to nearest even (results below the smallest normal float flush to
-// zero, overflow gives infinity, NaN stays NaN).
+// zero; overflow, infinity and NaN give infinity, so a non-finite input stays non-finite).
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned ex = (b >> 23) & 0xffu;
@@ -309,16 +309,17 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }
 
 __device__ __forceinline__ float d2f_bits(double d) {
+  // round to nearest even at bit 29 of the magnitude: adding 0x0fffffff plus the lowest kept bit
+  // carries into the kept bits exactly when the dropped ones exceed half an ulp, or equal it with
+  // an odd kept part; the exponent is rebiased by 896 in the same 64-bit addition
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const unsigned s = hi & 0x80000000u;
-  const int ex = (int)((hi >> 20) & 0x7ffu);
-  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned rest = lo & 0x1fffffffu;
-  unsigned bits = ((unsigned)(ex - 896) << 23) + m;
-  bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
-  if (ex - 896 <= 0) bits = 0u;
-  if (ex - 896 >= 255) bits = 0x7f800000u | ((ex == 0x7ff && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
-  return __uint_as_float(s | bits);
+  const unsigned ah = hi & 0x7fffffffu;
+  const unsigned long long r =
+      ((((unsigned long long)ah << 32) | lo) + (0x0fffffffull + ((lo >> 29) & 1u))) - (896ull << 52);
+  unsigned bits = (unsigned)(r >> 29);
+  bits = (ah < (897u << 20)) ? 0u : bits;              // below the smallest normal float
+  bits = (ah >= (1151u << 20)) ? 0x7f800000u : bits;   // overflow, infinity or NaN
+  return __uint_as_float((hi & 0x80000000u) | bits);
 }
 
 // double -> float by truncating the mantissa (rounding toward zero), for values that only steer a

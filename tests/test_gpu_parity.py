@@ -200,6 +200,49 @@ def test_fp64_division_within_one_ulp():
     assert np.array_equal(q[~fast], ref[~fast])
 
 
+def test_integer_pipe_conversions():
+    """The kernels' double -> float conversions done with integer instructions: the rounded one
+    (stored FP32 copies of q, e, P0, u) equals IEEE round-to-nearest-even (numpy's float32 cast)
+    over random doubles of the float range, exact halfway cases, values that round up into the
+    next binade and to infinity, with magnitudes below 2^-126 flushed to zero and non-finite
+    inputs giving infinity; the truncating one (features, Newton step lengths, interval guesses)
+    equals the mantissa cut to 23 bits."""
+    import ctypes as C
+    import torch
+    from paper_1608_06577_gb300 import binding
+    L = binding.load_library()
+    L.kt_selftest_cvt.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    x = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-126, 128, n)) * rng.choice([-1.0, 1.0], n)
+    f = rng.uniform(1.0, 2.0, 4096).astype(np.float32).astype(np.float64)
+    ulp = np.spacing(f.astype(np.float32)).astype(np.float64)
+    ties = np.concatenate([f + 0.5 * ulp, f - 0.5 * np.spacing(f.astype(np.float32) - ulp).astype(np.float64)])
+    edges = np.array([0.0, -0.0, 1.0, -1.0, 2.0 ** -126, np.nextafter(2.0 ** -126, 0.0), 2.0 ** -127, 1e-300,
+                      3.4028234663852886e38, 3.4028235677973366e38, 1e39, np.inf, -np.inf, np.nan,
+                      np.nextafter(2.0, 1.0), 1.9999999403953552, 1.99999997019767761230])
+    x = np.concatenate([x, ties, -ties, edges])
+    tx = torch.as_tensor(x, device="cuda")
+    rn = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    rz = torch.empty_like(rn)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.kt_selftest_cvt(C.c_void_p(tx.data_ptr()), C.c_void_p(rn.data_ptr()), C.c_void_p(rz.data_ptr()),
+                             x.size, st) == 0
+    rn, rz = rn.cpu().numpy(), rz.cpu().numpy()
+    with np.errstate(over="ignore", invalid="ignore"):
+        ref = x.astype(np.float32)
+    small = np.abs(x) < 2.0 ** -126
+    ref[small] = np.copysign(0.0, x[small]).astype(np.float32)
+    ref[~np.isfinite(x)] = np.copysign(np.inf, np.nan_to_num(x[~np.isfinite(x)], nan=1.0))
+    assert np.array_equal(rn.view(np.uint32), ref.view(np.uint32))
+    fin = np.isfinite(x) & (np.abs(x) < 2.0 ** 128)
+    b = x[fin].view(np.uint64)
+    tr = ((b >> 32) & np.uint64(0x80000000)) | np.where((b & np.uint64(0x7fffffffffffffff)) >= np.uint64(897 << 52),
+                                                          (((b & np.uint64(0x7fffffffffffffff)) - np.uint64(896 << 52))
+                                                           >> np.uint64(29)) & np.uint64(0x7fffffff), np.uint64(0))
+    assert np.array_equal(rz[fin].view(np.uint32), tr.astype(np.uint32))
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_cfl_max_speed_matches_oracle(precision, baseline_eos):
     """The CFL diagnostic kt_stats.max_speed (the largest local speed a of Eq. (ax) over all faces
