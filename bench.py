@@ -48,7 +48,7 @@ ALG_BYTES_PER_CELL = {"fp64": 856, "mixed": 728, "learned": 728}
 # FP64 add/multiply/FMA instructions per cell and RK2 step of the FP64 mode (ncu counts of the two
 # fused stage kernels), and GB300's FP64 rate: 2 FMA per SM and clock (152 SMs; 1.25 TFLOP/s at
 # 2.07 GHz nominal), taken at the SM clock sampled during the timed steps
-FP64_INST_PER_CELL_STEP = 2 * 1821
+FP64_INST_PER_CELL_STEP = 1800 + 1829
 FP64_FMA_PER_SM_CLK = 2
 N_SM = 152
 # per launch slot of kt_time_kernels (bytes per cell); FP64: the fused stage kernels
@@ -67,10 +67,10 @@ FUSED_FIRST_CANDIDATE = 24  # tuning candidates 24-35 are the fused launches (ch
 SLOT_KERNEL = {"stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel", "stage1_update": "update_kernel",
                "stage2_update": "update_kernel", "tau_advance": "advance_tau_kernel"}
 LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels from
-# one ncu capture of the 128^3 learned workload (average over the two stages of each kernel).  Only
-# that mode and size have a capture.
-MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 342.3e6, "update_kernel": 804.7e6}}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels: one-
+# kernel ncu captures of the 96^3 learned workload, per cell times the 128^3 cells (average over
+# the two stages of each kernel).  Only that mode has a capture.
+MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 327.5e6, "update_kernel": 753.2e6}}
 REPEATS = 3  # timed runs of K steps per mode; the median is reported
 
 
