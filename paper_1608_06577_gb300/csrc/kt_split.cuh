@@ -118,6 +118,7 @@ __global__ void __maxnreg__(96)
       cell_sources<float>(P, L, io, c, G, uc, du, dv, dq);
     }
 
+    const FacesXY Wxy = faces_xy(Fx, Fy);  // theta = 1: the x and y fluxes in paired instructions
 #pragma unroll  // unrolled: the component index, the rows it feeds and every branch become constants
     for (int g = 0; g < kGroups; ++g) {
       if (g + 1 < kGroups) {
@@ -131,9 +132,13 @@ __global__ void __maxnreg__(96)
       if (valid) {
 #pragma unroll
         for (int m = 0; m < kCompPerBox; ++m)
-          if (kCompPerBox * g + m < NQ)
-            component_rhs<float, true, TH1>(P, kCompPerBox * g + m, s_q + b * bfl + m * vol + own, 1, sy, sz, th,
-                                            Fx, Fy, Fz, dq);
+          if (kCompPerBox * g + m < NQ) {
+            if constexpr (TH1)
+              component_rhs_xy(P, kCompPerBox * g + m, s_q + b * bfl + m * vol + own, sy, sz, Wxy, Fx, Fy, Fz, dq);
+            else
+              component_rhs<float, true, TH1>(P, kCompPerBox * g + m, s_q + b * bfl + m * vol + own, 1, sy, sz, th,
+                                              Fx, Fy, Fz, dq);
+          }
       }
     }
     if (valid && !bad) {  // (a timed-out block leaves at the next tile's barrier)
@@ -628,6 +633,7 @@ __global__ void __maxnreg__(128)
       cell_faces<float, TH1, IFACE>(P, L, io, c, u_global(L, io, c), G, dq, uc, du, dv, amax, Fx, Fy, Fz);
       cell_sources<float>(P, L, io, c, G, uc, du, dv, dq);
     }
+    const FacesXY Wxy = faces_xy(Fx, Fy);
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) {
       if (g + 1 < kGroups) {
@@ -641,9 +647,13 @@ __global__ void __maxnreg__(128)
       if (valid) {
 #pragma unroll
         for (int m = 0; m < kCompPerBox; ++m)
-          if (kCompPerBox * g + m < NQ)
-            component_rhs<float, true, TH1>(P, kCompPerBox * g + m, s_q + b * bfl + m * vol + own, 1, sy, sz, th,
-                                            Fx, Fy, Fz, dq);
+          if (kCompPerBox * g + m < NQ) {
+            if constexpr (TH1)
+              component_rhs_xy(P, kCompPerBox * g + m, s_q + b * bfl + m * vol + own, sy, sz, Wxy, Fx, Fy, Fz, dq);
+            else
+              component_rhs<float, true, TH1>(P, kCompPerBox * g + m, s_q + b * bfl + m * vol + own, 1, sy, sz, th,
+                                              Fx, Fy, Fz, dq);
+          }
       }
     }
     if (__syncthreads_or(bad)) { bad = true; break; }  // the update runs for every tile of every block, or none

@@ -293,6 +293,82 @@ __device__ __forceinline__ void component_rhs(const Params& P, int n, const R* p
   }
 }
 
+// ---- paired FP32 arithmetic (the f32x2 instructions of the sm_100 family): two independent
+// single-precision operations, each rounded to nearest as its scalar form, in one instruction
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void up2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// The x and y face weights of a cell as (x, y) pairs for the paired flux of component_rhs_xy.
+struct FacesXY {
+  unsigned long long c0, wLm, dW, nwRp, wRp;
+};
+__device__ __forceinline__ FacesXY faces_xy(const Faces<float>& Fx, const Faces<float>& Fy) {
+  return FacesXY{pk2(Fx.c0, Fy.c0), pk2(Fx.wLm, Fy.wLm), pk2(Fx.dW, Fy.dW), pk2(-Fx.wRp, -Fy.wRp), pk2(Fx.wRp, Fy.wRp)};
+}
+
+// component_rhs for the FP32 stencil in shared memory with theta = 1, the x and y directions
+// computed as pairs: the differences, the slope combination and the seven multiply-adds of the
+// two directions share instructions; the limiter's min/max and the eta direction stay scalar.
+// The same arithmetic as component_rhs, summed x + y, then eta.
+__device__ __forceinline__ void component_rhs_xy(const Params& P, int n, const float* p, int sy, int sz,
+                                                 const FacesXY& W, const Faces<float>& Fx, const Faces<float>& Fy,
+                                                 const Faces<float>& Fz, float (&dq)[NQ]) {
+  const float a0 = p[0];
+  const float a2x = p[-2], a1x = p[-1], b1x = p[1], b2x = p[2];
+  const float a2y = p[-2 * sy], a1y = p[-sy], b1y = p[sy], b2y = p[2 * sy];
+  const unsigned long long A0 = pk2(a0, a0), A1 = pk2(a1x, a1y), B1 = pk2(b1x, b1y);
+  const unsigned long long D0 = sub2(A1, pk2(a2x, a2y)), D1 = sub2(A0, A1), D2 = sub2(B1, A0),
+                           D3 = sub2(pk2(b2x, b2y), B1);
+  float d0x, d0y, d1x, d1y, d2x, d2y, d3x, d3y, smx, smy, s0x, s0y, spx, spy;
+  up2(D0, d0x, d0y);
+  up2(D1, d1x, d1y);
+  up2(D2, d2x, d2y);
+  up2(D3, d3x, d3y);
+  three_slopes<float, true>(d0x, d1x, d2x, d3x, 1.f, smx, s0x, spx);
+  three_slopes<float, true>(d0y, d1y, d2y, d3y, 1.f, smy, s0y, spy);
+  const unsigned long long slopes = fma2(W.wLm, pk2(smx, smy), fma2(W.dW, pk2(s0x, s0y), mul2(W.nwRp, pk2(spx, spy))));
+  unsigned long long acc = mul2(W.c0, A0);
+  acc = fma2(W.wLm, A1, acc);
+  acc = fma2(W.wRp, B1, acc);
+  acc = fma2(pk2(0.5f, 0.5f), slopes, acc);
+  float accx, accy, a1z, b1z;
+  up2(acc, accx, accy);
+  const float accz = component_flux<float, true, true>(p, sz, a0, 1.f, Fz, a1z, b1z, accx + accy);
+  add_row(dq, n, accz);
+  if (n >= 4 && n <= 13) {  // pi components
+    const int r0 = cross_row<0>(n, true);
+    if (r0 >= 0)
+      add_row(dq, r0, (Fx.vpl_h * b1x - Fx.vmi_h * a1x) + (Fy.vpl_h * b1y - Fy.vmi_h * a1y) +
+                          (Fz.vpl_h * b1z - Fz.vmi_h * a1z));
+    const int rx = cross_row<0>(n, false), ry = cross_row<1>(n, false), rz = cross_row<2>(n, false);
+    const float* hinv = pr<float>(P).half_inv_d;
+    if (rx >= 0) add_row(dq, rx, -(b1x - a1x) * hinv[0]);
+    if (ry >= 0) add_row(dq, ry, -(b1y - a1y) * hinv[1]);
+    if (rz >= 0) add_row(dq, rz, -(b1z - a1z) * hinv[2]);
+  }
+}
+
 // All 15 components from global memory.  The component loop is not unrolled: one compact body
 // keeps the instruction stream of the whole kernel small.
 template <typename R, bool TH1 = false>
