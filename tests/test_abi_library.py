@@ -66,6 +66,17 @@ def test_invalid_arguments_rejected(libpath):
     z = binding.Coef(0, 0.0, 0.0, 1.0)
     assert L.kt_init(ctypes.byref(ctx), ctypes.byref(g), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
                      ctypes.byref(z), None) == -1
+    # options are validated before any device work: FP32 pi storage needs the mixed precision
+    o = binding.Options()
+    L.kt_options_default(ctypes.byref(o))
+    o.pi_storage = 1
+    g4 = binding.Grid(4, 4, 4)
+    assert L.kt_init(ctypes.byref(ctx), ctypes.byref(g4), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
+                     ctypes.byref(z), ctypes.byref(o)) == -1
+    o.pi_storage = 7
+    o.precision = 1
+    assert L.kt_init(ctypes.byref(ctx), ctypes.byref(g4), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
+                     ctypes.byref(z), ctypes.byref(o)) == -1
     nb = ctypes.c_size_t()
     assert L.kt_state_bytes(ctypes.byref(binding.Grid(128, 128, 128)), None, None, ctypes.byref(nb)) == 0
     assert nb.value > 30 * 132 * 132 * 132 * 8
