@@ -66,6 +66,7 @@ struct Ctx {
   double* stage = nullptr;  // staging: 18 packed fields of the largest event
   EosSeg<double>* seg_d = nullptr;
   EosSeg<float>* seg_f = nullptr;
+  RootSeg* seg_r = nullptr;
   double* d_tau = nullptr;
   unsigned* d_stat = nullptr;
   float* d_mlp = nullptr;
@@ -181,6 +182,7 @@ size_t state_bytes(const std::vector<Lattice>& lat, long long gs, size_t max_cel
   b += align_up(18 * max_cells * 8, 256);      // staging
   b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(EosSeg<double>), 256);
   b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(EosSeg<float>), 256);
+  b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(RootSeg), 256);
   b += 256;                                    // tau
   b += 256;                                    // stats
   b += align_up(KT_MLP_NPARAM * 4, 256);       // MLP weights
@@ -248,6 +250,28 @@ void build_segments(const kt_eos* eos, std::vector<EosSeg<R>>& out) {
   }
   out[n - 1] = out[n - 2];
   out[n - 1].e0 = (R)eos->e[n - 1];  // sentinel: only its e0 is read by the interval search
+}
+
+// The root-find's records (RootSeg) from the FP64 and FP32 segments.
+void build_root_segments(const std::vector<EosSeg<double>>& sd, const std::vector<EosSeg<float>>& sf,
+                         std::vector<RootSeg>& out) {
+  const int n = (int)sd.size();
+  out.resize(n);
+  for (int i = 0; i < n; ++i) {
+    RootSeg r;
+    r.e0 = sd[i].e0;
+    r.e1 = (i + 2 < n) ? sd[i + 1].e0 : INFINITY;  // the last interval (n - 2) and the sentinel are open
+    r.P0 = sd[i].P0;
+    r.a1 = sd[i].a1;
+    r.a2 = sd[i].a2;
+    r.a3 = sd[i].a3;
+    const float two = 2.f, three = 3.f;
+    r.b1 = sf[i].a1;
+    r.b2 = two * sf[i].a2;
+    r.b3 = three * sf[i].a3;
+    r.unused = 0.f;
+    out[i] = r;
+  }
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -1041,6 +1065,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   int nseg = P.eos_n > 0 ? P.eos_n : 1;
   c->seg_d = (EosSeg<double>*)carve(nseg * sizeof(EosSeg<double>));
   c->seg_f = (EosSeg<float>*)carve(nseg * sizeof(EosSeg<float>));
+  c->seg_r = (RootSeg*)carve(nseg * sizeof(RootSeg));
   c->d_tau = (double*)carve(256);
   c->d_stat = (unsigned*)carve(256);
   c->d_mlp = (float*)carve(KT_MLP_NPARAM * 4);
@@ -1054,6 +1079,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   c->z_net = (float*)carve(fs * 4);
   P.seg_d = c->seg_d;
   P.seg_f = c->seg_f;
+  P.seg_r = c->seg_r;
 
   CK(cudaMemsetAsync(qq, 0, 30 * fs * 8, c->stream));
   CK(cudaMemsetAsync(ep, 0, 4 * fs * c->esz, c->stream));
@@ -1074,8 +1100,11 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
     std::vector<EosSeg<float>> sf;
     build_segments<double>(eos, sd);
     build_segments<float>(eos, sf);
+    std::vector<RootSeg> sr;
+    build_root_segments(sd, sf, sr);
     CK(cudaMemcpyAsync(c->seg_d, sd.data(), sd.size() * sizeof(sd[0]), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->seg_f, sf.data(), sf.size() * sizeof(sf[0]), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->seg_r, sr.data(), sr.size() * sizeof(sr[0]), cudaMemcpyHostToDevice, c->stream));
   }
   if (o.mlp_weights) {
     CK(cudaMemcpyAsync(c->d_mlp, o.mlp_weights, KT_MLP_NPARAM * 4, cudaMemcpyHostToDevice, c->stream));

@@ -53,6 +53,16 @@ struct EosSeg {
   R a1, a2, a3;         // the same P in d = e - e0: P = P0 + d (a1 + d (a2 + d a3)), c_s^2 = P'(d)
 };
 
+// The root-find's record of interval i of the table EOS, 64 bytes (two 32-byte sectors, fetched
+// by four vector loads in one round trip): its ends e0 <= e < e1 (e1 = +inf for the last
+// interval), so that the interval guess is checked with the coefficients already loaded; P in
+// d = e - e0 as in EosSeg (FP64); and c_s^2 = P'(d) = b1 + d (b2 + d b3) in single precision, with
+// b1, b2, b3 the FP32 table's a1, 2 a2, 3 a3 (the products rounded in single precision).
+struct alignas(64) RootSeg {
+  double e0, e1, P0, a1, a2, a3;
+  float b1, b2, b3, unused;
+};
+
 struct Coef {
   int kind;       // 0 const, 1 gauss
   double c0, c1, c2;
@@ -86,6 +96,7 @@ struct Params {
   float lne0, inv_h;  // index guess: (ln e - ln e_0) * inv_h
   const EosSeg<double>* seg_d;
   const EosSeg<float>* seg_f;
+  const RootSeg* seg_r;
   Coef eta, zeta;
   int shear_on, bulk_on;
   double tpp;         // tau_pipi / tau_pi (10/7 or 0)

@@ -392,19 +392,31 @@ __device__ __forceinline__ double clamp_pos(double x, double lo, double hi) {  /
   return (obits(x) < obits(lo)) ? lo : ((obits(x) <= obits(hi)) ? x : hi);
 }
 
-// interval of e > 0 in the FP64 table: the rule of eos_interval with integer comparisons
-__device__ __forceinline__ int eos_interval_pos(const Params& P, double e) {
-  const EosSeg<double>* seg = P.seg_d;
+// The interval of e > 0 in the FP64 table and its record: the single-precision log guess of
+// eos_interval, checked against both ends of the interval in the same load; only a guess that
+// misses (next to a node) searches as eos_interval does (integer comparisons of the bit patterns)
+// and loads again.  The same interval as eos_interval, with one dependent load instead of three.
+__device__ __forceinline__ RootSeg load_root_seg(const RootSeg* p) {
+  const double2* d = reinterpret_cast<const double2*>(p);
+  const double2 v0 = __ldg(d), v1 = __ldg(d + 1), v2 = __ldg(d + 2);
+  const float4 v3 = __ldg(reinterpret_cast<const float4*>(p) + 3);
+  return RootSeg{v0.x, v0.y, v1.x, v1.y, v2.x, v2.y, v3.x, v3.y, v3.z, v3.w};
+}
+__device__ __forceinline__ RootSeg root_seg(const Params& P, double e) {
+  const RootSeg* seg = P.seg_r;
   const int n1 = P.eos_n - 2;
   const float g = (__logf(d2f_trunc(e)) - P.lne0) * P.inv_h;
-  int i = (g > 0.f) ? (int)g : 0;  // NaN compares false -> 0
-  i = min(i, n1);
+  int i = min((g > 0.f) ? (int)g : 0, n1);  // NaN compares false -> 0
   const long long b = obits(e);
+  RootSeg s = load_root_seg(seg + i);
+  if ((i > 0 && b < obits(s.e0)) || b >= obits(s.e1)) {
 #pragma unroll 1
-  for (int it = 0; it < 64 && i > 0 && b < obits(seg[i].e0); ++it) --i;
+    for (int it = 0; it < 64 && i > 0 && b < obits(seg[i].e0); ++it) --i;
 #pragma unroll 1
-  for (int it = 0; it < 64 && i < n1 && b >= obits(seg[i + 1].e0); ++it) ++i;
-  return i;
+    for (int it = 0; it < 64 && i < n1 && b >= obits(seg[i].e1); ++it) ++i;
+    s = load_root_seg(seg + i);
+  }
+  return s;
 }
 
 // The residual in product form g(e) = (e - E) A(e) + M^2 = f(e) A(e), A = E + P0(e) + Pi > 0:
@@ -417,17 +429,15 @@ struct Resid {
   float gp;
 };
 __device__ __forceinline__ Resid residual(const Params& P, double e, double E, double EPi, double M2, float M2f) {
-  const int i = eos_interval_pos(P, e);
-  const EosSeg<double>& s = P.seg_d[i];
+  const RootSeg s = root_seg(P, e);
   const double d = e - s.e0;
   Resid r;
   r.p0 = fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
   r.A = EPi + r.p0;
   const double em = e - E;
   r.g = fma(em, r.A, M2);
-  const EosSeg<float>& sf = P.seg_f[i];
   const float df = d2f_trunc(d);
-  const float c2 = fmaf(df, fmaf(df, 3.f * sf.a3, 2.f * sf.a2), sf.a1);
+  const float c2 = fmaf(df, fmaf(df, s.b3, s.b2), s.b1);
   const float Af = d2f_trunc(r.A);
   r.gp = Af - __fdividef(M2f * c2, Af);
   return r;
@@ -440,7 +450,7 @@ __device__ __forceinline__ double newton_step(double e, const Resid& r) {
 
 // P0(e) on the FP64 table
 __device__ __forceinline__ double eos_P_pos(const Params& P, double e) {
-  const EosSeg<double>& s = P.seg_d[eos_interval_pos(P, e)];
+  const RootSeg s = root_seg(P, e);
   const double d = e - s.e0;
   return fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
 }
