@@ -70,7 +70,13 @@ LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels: one-
 # kernel ncu captures of the 96^3 learned workload, per cell times the 128^3 cells (average over
 # the two stages of each kernel).  Only that mode has a capture.
-MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 327.5e6, "update_kernel": 753.2e6}}
+MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 765.2e6}}
+# Warp instructions per 32 cells of each launch slot (ncu smsp__inst_executed.sum over the warps of
+# one-kernel captures of the 96^3 learned workload, current kernels), for each kernel's fraction of
+# the SMs' issue rate: one warp instruction per scheduler and clock, 4 schedulers per SM.  The
+# kernels are bound by instruction issue and latency rather than by HBM.
+INST_PER_WARP = {"learned": {"stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1834, "stage2_update": 1866}}
+ISSUE_PER_SM_CLK = 4
 REPEATS = 3  # timed runs of K steps per mode; the median is reported
 
 
@@ -380,8 +386,21 @@ def run_ours(args, world, rank, local):
         k["launches_per_step"] += 1
         k["ms_per_step"] += t
         k["bytes_per_step"] += cells * slot_bytes.get(slot, 8.0 / cells)
+    inst = INST_PER_WARP.get(args.mode) if not fused else None
+    sm_hz_k = ((clocks or {}).get("sm_mhz") or 2070.0) * 1e6
+    for slot, t in main["slots_ms"].items():
+        if inst and slot in inst and t > 0.0:
+            k = kernels[SLOT_KERNEL[slot]]
+            k.setdefault("warp_inst_per_step", 0.0)
+            k["warp_inst_per_step"] += inst[slot] * cells / 32
     for k in kernels.values():
         k["avg_launch_ms"] = k["ms_per_step"] / k["launches_per_step"]
+        if "warp_inst_per_step" in k:
+            ach = k["warp_inst_per_step"] / (k["ms_per_step"] * 1e-3)
+            peak = ISSUE_PER_SM_CLK * N_SM * sm_hz_k
+            k["issue"] = {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp instructions/s",
+                          "frac": ach / peak, "note": "ncu warp instructions per 32 cells (96^3 capture) x the "
+                          "launches' warps / CUDA-event time; peak 4 per SM and clock at the sampled SM clock"}
         k["gbs"] = k["bytes_per_step"] / (k["ms_per_step"] * 1e-3) / 1e9
         k["frac_of_hbm"] = k["gbs"] / hbm_peak
         k["share"] = k["ms_per_step"] / sum(v["ms_per_step"] for v in kernels.values())
