@@ -35,8 +35,8 @@ def _built():
     oracle.build()
 
 
-def snapshot(kt, p):
-    """The GPU state as CUDA float64 tensors shaped [comp, neta, ny, nx]."""
+def snapshot(kt, p, event=0):
+    """The GPU state of one event as CUDA float64 tensors shaped [comp, neta, ny, nx]."""
     import torch
     n = p.ncells
     t = {"e": torch.empty(n, dtype=torch.float64, device="cuda"),
@@ -44,7 +44,7 @@ def snapshot(kt, p):
          "pi": torch.empty((10, n), dtype=torch.float64, device="cuda"),
          "Pi": torch.empty(n, dtype=torch.float64, device="cuda"),
          "q": torch.empty((15, n), dtype=torch.float64, device="cuda")}
-    tau = kt.get_state_device(e=t["e"], u=t["u"], pi=t["pi"], Pi=t["Pi"], q=t["q"])
+    tau = kt.get_state_device(e=t["e"], u=t["u"], pi=t["pi"], Pi=t["Pi"], q=t["q"], event=event)
     shp = (p.neta, p.ny, p.nx)
     return tau, {k: v.reshape((-1,) + shp) if v.dim() == 2 else v.reshape((1,) + shp) for k, v in t.items()}
 
@@ -90,13 +90,24 @@ def check_sampled(kt, p, warm_steps, tol_field, tol_rel_e, seed):
     Errors per field as in the parity metric: |a - b| normalised by the field's max norm over the
     grid (u by max u^tau, pi by its tensor scale in an orthonormal frame).  tol_rel_e bounds the
     pointwise relative error in e on sampled cells with e > 1e-6 max e (mixed precision)."""
-    import torch
+    check_sampled_events(kt, {0: p}, warm_steps, tol_field, tol_rel_e, seed)
+
+
+def check_sampled_events(kt, probs, warm_steps, tol_field, tol_rel_e, seed):
+    """check_sampled for the events {event: problem} of one (batch) context, stepped together."""
     kt.step(warm_steps)
-    _, s_prev = snapshot(kt, p)
+    s_prev = {ev: snapshot(kt, p, ev)[1] for ev, p in probs.items()}
     kt.step(1)
-    tau, s_now = snapshot(kt, p)
+    s_now = {ev: snapshot(kt, p, ev) for ev, p in probs.items()}
     kt.step(1)
-    tau_next, s_next = snapshot(kt, p)
+    s_next = {ev: snapshot(kt, p, ev) for ev, p in probs.items()}
+    for ev, p in probs.items():
+        compare_sampled(kt, p, s_prev[ev], *s_now[ev], *s_next[ev], tol_field, tol_rel_e, seed + ev)
+    assert kt.stats()["status"] == 0
+
+
+def compare_sampled(kt, p, s_prev, tau, s_now, tau_next, s_next, tol_field, tol_rel_e, seed):
+    import torch
     cells = sample_cells(p, s_now, 10, seed)
     S_e = float(s_next["e"].abs().max().item())
     S_u = float(s_next["u"][0].abs().max().item())
@@ -122,7 +133,6 @@ def check_sampled(kt, p, warm_steps, tol_field, tol_rel_e, seed):
           "tuning", kt.tuning()["block"])
     assert worst["e"] <= tol_field and worst["u"] <= tol_field and worst["pi"] <= tol_field
     assert worst["rel_e"] <= tol_rel_e
-    assert kt.stats()["status"] == 0
 
 
 _W = {}
@@ -230,14 +240,33 @@ def test_fullsize_128_learned_sampled_parity(baseline_eos):
 
 def test_large_event_256x256x128(baseline_eos):
     """The 256 x 256 x 128 event (100 hotspots, eta/s = 0.2): mixed precision with the learned
-    start and plain FP64, each checked on sampled cells."""
+    start and plain FP64, each run for the configuration's 200 steps and checked on sampled cells
+    in the last one."""
     from paper_1608_06577_gb300 import KT, KT_INV_LEARNED, KT_MIXED
     p = hotspot_problem(nx=256, ny=256, neta=128, nhot=100, seed=7, eta_over_s=0.2, eos_table=baseline_eos)
     p.name = "large"
     kt = KT(p, precision=KT_MIXED, inversion=KT_INV_LEARNED, mlp_weights=_weights())
     kt.set_problem_state()
-    check_sampled(kt, p, 12, 1e-5, 1e-5, seed=13)
+    check_sampled(kt, p, 198, 1e-5, 1e-5, seed=13)
     del kt
     kt = KT(p, precision=0)
     kt.set_problem_state()
-    check_sampled(kt, p, 3, 1e-12, 1.0, seed=14)
+    check_sampled(kt, p, 198, 1e-12, 1.0, seed=14)
+
+
+def test_sixty_four_event_batch_sampled_parity(baseline_eos):
+    """The 64-event batch (per-event 64..160 cells across, 16..64 in eta, 20-100 hotspots, per-
+    event seeds), FP32 stencil + FP64 Heun and root-find with the learned start, one launch per
+    stage over the tile table, autotuned, CUDA graph: after 60 steps, sampled cells of the largest
+    and the smallest event and of events 0 and 63 against the oracle's step on their
+    neighbourhoods."""
+    from paper_1608_06577_gb300 import KT, KT_INV_LEARNED, KT_MIXED
+    from workload.problem import batch_problems
+    probs = batch_problems(n_events=64, eos_table=baseline_eos)
+    sizes = [p.ncells for p in probs]
+    pick = sorted({0, 63, int(np.argmax(sizes)), int(np.argmin(sizes))})
+    kt = KT(probs, precision=KT_MIXED, inversion=KT_INV_LEARNED, mlp_weights=_weights())
+    kt.set_problem_state()
+    for ev in pick:
+        probs[ev].name = f"batch event {ev}"
+    check_sampled_events(kt, {ev: probs[ev] for ev in pick}, 60, 1e-5, 1e-5, seed=21)
