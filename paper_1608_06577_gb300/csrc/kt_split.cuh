@@ -59,8 +59,9 @@ __host__ __device__ constexpr int rhs_smem_bytes(int tx, int ty, int tz) {  // t
 }
 
 // Register caps: 96 (rhs) lets 20 warps of 128-thread tiles share an SM; 72 (stage-1 update) 28
-// warps; 96 for the stage-2 update, which holds all 15 FP64 components; each measured faster than
-// the compiler's unconstrained choice and than the neighbouring caps (64 and 80 for stage 1).
+// warps; 96 for the stage-2 update, which holds all 15 FP64 components.  Each measured faster than
+// the compiler's unconstrained choice; for the update kernels, caps of 64-80 (stage 1) and 72-96
+// (stage 2) all measure within 0.5% of each other (latency-bound: more warps, more spills).
 template <int STAGE, bool TH1, bool IFACE>
 __global__ void __maxnreg__(96)
     rhs_kernel(const Params P, const StageIO<float> io, float* __restrict__ k_out, const Lattice* __restrict__ lats,
