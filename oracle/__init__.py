@@ -1,7 +1,7 @@
 """ctypes wrapper of the plain FP64 CPU oracle (oracle/kt_oracle.c).
 
 TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's CPU-baseline
-leg use it to judge the CUDA path.  It shares no code with the CUDA library.
+leg use it to check the CUDA path.  It shares no code with the CUDA library.
 """
 from __future__ import annotations
 

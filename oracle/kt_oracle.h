@@ -2,7 +2,7 @@
  * kt_oracle.h -- plain FP64 CPU oracle for the Kurganov-Tadmor (KT) + Heun step of
  * 3+1d relativistic viscous hydrodynamics (Bazow, Heinz, Strickland, arXiv:1608.06577).
  *
- * TEST INFRASTRUCTURE ONLY.  This library judges the CUDA path: only the test suite,
+ * TEST INFRASTRUCTURE ONLY.  This library checks the CUDA path: only the test suite,
  * the package's smoke check and the benchmark's CPU-baseline leg may load it.  It shares
  * no code, header, table generator or constant with the CUDA path.
  *
