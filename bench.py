@@ -237,9 +237,12 @@ def run_reference(args, world, rank):
 # ----------------------------------------------------------------------------- our arm
 # (precision, inversion); "network_off" is the learned mode with all-zero weights, i.e. started
 # from the conformal root alone: the ablation that shows what the trained network adds;
+# "conformal" the same start without the network (KT_INV_CONFORMAL: e_conf, no inference), so
+# that network_off - conformal is the inference's cost and network_off - learned its saving;
 # "learned_pi32" the learned mode with the FP32 storage of pi and Pi (KT_STORE_PI_FP32: only the
 # conserved T^{tau mu} kept and Heun-summed in FP64)
-MODES = {"learned": (1, 1), "mixed": (1, 0), "fp64": (0, 0), "network_off": (1, 1), "learned_pi32": (1, 1)}
+MODES = {"learned": (1, 1), "mixed": (1, 0), "fp64": (0, 0), "network_off": (1, 1), "conformal": (1, 2),
+         "learned_pi32": (1, 1)}
 
 
 def make_kt(prob, mode, weights, stream):
@@ -250,7 +253,7 @@ def make_kt(prob, mode, weights, stream):
     if mode == "network_off" and weights is not None:
         weights = np.zeros_like(weights)
     with torch.cuda.stream(stream):
-        return KT(prob, precision=prec, inversion=inv, mlp_weights=weights if inv else None,
+        return KT(prob, precision=prec, inversion=inv, mlp_weights=weights if inv == 1 else None,
                   pi_fp32=(mode == "learned_pi32"))
 
 

@@ -49,7 +49,7 @@ enum { KT_MILNE = 0, KT_CARTESIAN = 1 };              /* coordinates (Cartesian:
 enum { KT_BC_COPY = 0, KT_BC_PERIODIC = 1 };          /* ghost cells: Eqs. ghostCells_1/2 or periodic */
 enum { KT_FP64 = 0, KT_MIXED = 1 };                   /* precision mode */
 enum { KT_STORE_FP64 = 0, KT_STORE_PI_FP32 = 1 };     /* KT_MIXED storage of pi, Pi (kt_options.pi_storage) */
-enum { KT_INV_PLAIN = 0, KT_INV_LEARNED = 1 };        /* inversion start: previous e, or MLP */
+enum { KT_INV_PLAIN = 0, KT_INV_LEARNED = 1, KT_INV_CONFORMAL = 2 };  /* inversion start: previous e, MLP, conformal root */
 enum { KT_IFACE_RECON = 0, KT_IFACE_INVERT = 1 };     /* face velocities (see kt_options.iface) */
 enum { KT_EOS_CONFORMAL = 0, KT_EOS_TABLE = 1 };
 enum { KT_COEF_CONST = 0, KT_COEF_GAUSS = 1, KT_COEF_PAPER_ZETA = 2 };
@@ -87,7 +87,8 @@ typedef struct {
   int coords;            /* KT_MILNE (default) or KT_CARTESIAN */
   int bc;                /* KT_BC_COPY (default) or KT_BC_PERIODIC */
   int precision;         /* KT_FP64 (default) or KT_MIXED: FP32 stencil/sources, FP64 Heun + inversion */
-  int inversion;         /* KT_INV_PLAIN (default) or KT_INV_LEARNED */
+  int inversion;         /* KT_INV_PLAIN (default), KT_INV_LEARNED or KT_INV_CONFORMAL (both KT_MIXED
+                            only; see the learned root-find start below) */
   int tau_pipi_on;       /* 1 (default): tau_pipi/tau_pi = 10/7; 0: tau_pipi = 0 */
   int regulate;          /* 1 (default): Eq. (regPimunu) after every inversion */
   double rho_max, xi0;   /* regulator parameters of Eq. (rho); defaults 1 and 0.1 */
@@ -292,7 +293,11 @@ int kt_time_kernels(kt_ctx* ctx, int n_steps, float* ms, int* n_kernels);
  * Runge-Kutta stage; the second stage applies the same z to its own E, M^2 and Pi.
  * At most 2 FP64 Newton steps follow; a cell whose residual |f(e)|/E then exceeds 1e-10 falls
  * back to the plain root-find.  Parameters: KT_MLP_NPARAM floats, layout as documented above
- * KT_MLP_NPARAM.  All pointers below are device pointers; work goes to `stream`. */
+ * KT_MLP_NPARAM.  KT_INV_CONFORMAL is the same start without the network (y = 0: e = e_conf,
+ * the closed-form root of the conformal EOS, Sec. 2.4) and the same Newton steps and fallback:
+ * the ablation that shows what the network adds; it needs no weights.  (It gives the state of
+ * KT_INV_LEARNED with all-zero weights bit for bit, without the inference.)
+ * All pointers below are device pointers; work goes to `stream`. */
 #define KT_MLP_PACKED_BYTES 3396 /* scratch of kt_mlp_predict: packed BF16 weights + FP32 biases */
 #define KT_MLP_GATE_R2 1e-3      /* M^2/E^2 above which the network's correction is applied */
 

@@ -3,5 +3,5 @@
 The compute path is libkt.so (hand-written CUDA for sm_103a) behind the C ABI of
 include/kt.h; this package only marshals arguments to it.  There is no CPU fallback.
 """
-from .binding import (KT, KT_FP64, KT_INV_LEARNED, KT_INV_PLAIN, KT_MIXED, KTError, lib_path,  # noqa: F401
+from .binding import (KT, KT_FP64, KT_INV_CONFORMAL, KT_INV_LEARNED, KT_INV_PLAIN, KT_MIXED, KTError, lib_path,  # noqa: F401
                       load_library, mlp_adam, mlp_grad, mlp_predict)

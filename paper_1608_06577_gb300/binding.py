@@ -17,7 +17,7 @@ KT_OK = 0
 ERRORS = {-1: "KT_ERR_ARG", -2: "KT_ERR_CUDA", -3: "KT_ERR_OOM", -4: "KT_ERR_EOS", -5: "KT_ERR_STATE",
           -6: "KT_ERR_INVERSION", -7: "KT_ERR_NONFINITE", -8: "KT_ERR_TIMEOUT"}
 KT_FP64, KT_MIXED = 0, 1
-KT_INV_PLAIN, KT_INV_LEARNED = 0, 1
+KT_INV_PLAIN, KT_INV_LEARNED, KT_INV_CONFORMAL = 0, 1, 2
 KT_STORE_FP64, KT_STORE_PI_FP32 = 0, 1
 MLP_NPARAM = 32 * 6 + 32 + 32 * 32 + 32 + 32 + 1
 

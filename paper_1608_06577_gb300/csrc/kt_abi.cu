@@ -961,12 +961,14 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   if (!(o.theta_limiter >= 1.0 && o.theta_limiter <= 2.0)) return bail(KT_ERR_ARG);
   if (o.coords != KT_MILNE && o.coords != KT_CARTESIAN) return bail(KT_ERR_ARG);
   if (o.bc != KT_BC_COPY && o.bc != KT_BC_PERIODIC) return bail(KT_ERR_ARG);
-  if (o.inversion != KT_INV_PLAIN && o.inversion != KT_INV_LEARNED) return bail(KT_ERR_ARG);
-  // the learned start serves the mixed-precision path
+  if (o.inversion != KT_INV_PLAIN && o.inversion != KT_INV_LEARNED && o.inversion != KT_INV_CONFORMAL)
+    return bail(KT_ERR_ARG);
+  // the learned (and the conformal) start serves the mixed-precision path
   if (o.inversion == KT_INV_LEARNED && (!o.mlp_weights || o.precision != KT_MIXED)) return bail(KT_ERR_ARG);
+  if (o.inversion == KT_INV_CONFORMAL && o.precision != KT_MIXED) return bail(KT_ERR_ARG);
   c->mixed = (o.precision == KT_MIXED);
   c->esz = c->mixed ? 4 : 8;
-  c->learned = (o.inversion == KT_INV_LEARNED);
+  c->learned = (o.inversion == KT_INV_LEARNED || o.inversion == KT_INV_CONFORMAL);
   if (o.pi_storage != KT_STORE_FP64 && o.pi_storage != KT_STORE_PI_FP32) return bail(KT_ERR_ARG);
   if (o.pi_storage == KT_STORE_PI_FP32 && o.precision != KT_MIXED) return bail(KT_ERR_ARG);
   c->pi32 = (o.pi_storage == KT_STORE_PI_FP32);
@@ -1009,6 +1011,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   P.regulate = o.regulate;
   if (o.iface != KT_IFACE_RECON && o.iface != KT_IFACE_INVERT) return bail(KT_ERR_ARG);
   P.iface_invert = (o.iface == KT_IFACE_INVERT);
+  P.mlp_infer = (o.inversion == KT_INV_LEARNED);
   P.rho_max = o.rho_max;
   P.xi0 = o.xi0;
   P.e_min = o.e_min;

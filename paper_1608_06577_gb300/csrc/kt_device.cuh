@@ -102,6 +102,7 @@ struct Params {
   double tpp;         // tau_pipi / tau_pi (10/7 or 0)
   int regulate;
   int iface_invert;   // face velocities from root-finds of the extrapolated states (KT_IFACE_INVERT)
+  int mlp_infer;      // learned start: 1 runs the network (KT_INV_LEARNED), 0 starts from e_conf alone
   double rho_max, xi0;
   double e_min;
   double rate_max;    // 1 / tau_relax_min (or +inf)

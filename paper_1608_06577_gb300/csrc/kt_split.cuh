@@ -417,7 +417,7 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
   constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
   __shared__ uint32_t s_mlp[kInfer ? PK_WORDS : 1];
   if constexpr (kInfer) {
-    mlp_load_shared(s_mlp, io.mlp_packed);
+    if (P.mlp_infer) mlp_load_shared(s_mlp, io.mlp_packed);
     __syncthreads();
   }
   const double tau_out = io.d_tau[0] + P.dtau;
@@ -485,7 +485,7 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     mbar_init(&s_bar[1], 1);
     fence_barrier_init();
   }
-  if constexpr (kInfer) mlp_load_shared(s_mlp, io.mlp_packed);
+  if (kInfer && P.mlp_infer) mlp_load_shared(s_mlp, io.mlp_packed);
   __syncthreads();
 
   unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
@@ -591,7 +591,7 @@ __global__ void __maxnreg__(128)
     mbar_init(&s_bar[1], 1);
     fence_barrier_init();
   }
-  if constexpr (kInfer) mlp_load_shared(s_mlp, uio.mlp_packed);
+  if (kInfer && P.mlp_infer) mlp_load_shared(s_mlp, uio.mlp_packed);
   __syncthreads();
 
   float amax = 0.f;

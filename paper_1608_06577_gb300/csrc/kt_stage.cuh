@@ -834,7 +834,8 @@ __device__ __forceinline__ double learned_start(const Params& P, double gnn, con
   const float M2f = fmaf(Mx, Mx, fmaf(My, My, d2f_trunc(gnn) * Mn * Mn));
   float x[MLP_IN], ecE;
   mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_trunc(qn[14]), x, ecE);
-  if constexpr (INFER) z_io = __any_sync(0xffffffffu, x[1] > kMlpGateR2) ? mlp_warp_infer(s_mlp, x) : 0.f;
+  if constexpr (INFER)
+    z_io = (P.mlp_infer && __any_sync(0xffffffffu, x[1] > kMlpGateR2)) ? mlp_warp_infer(s_mlp, x) : 0.f;
   const float y = (x[1] > kMlpGateR2) ? x[1] * z_io : 0.f;
   return f2d_bits(Ef * ecE * __expf(0.1f * y));
 }

@@ -77,6 +77,15 @@ def test_invalid_arguments_rejected(libpath):
     o.precision = 1
     assert L.kt_init(ctypes.byref(ctx), ctypes.byref(g4), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
                      ctypes.byref(z), ctypes.byref(o)) == -1
+    # the conformal start (no network) serves the mixed precision only; unknown starts are rejected
+    L.kt_options_default(ctypes.byref(o))
+    o.inversion = binding.KT_INV_CONFORMAL
+    assert L.kt_init(ctypes.byref(ctx), ctypes.byref(g4), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
+                     ctypes.byref(z), ctypes.byref(o)) == -1
+    o.inversion = 3
+    o.precision = 1
+    assert L.kt_init(ctypes.byref(ctx), ctypes.byref(g4), 0.1, 0.1, 0.01, ctypes.byref(eos), ctypes.byref(z),
+                     ctypes.byref(z), ctypes.byref(o)) == -1
     nb = ctypes.c_size_t()
     assert L.kt_state_bytes(ctypes.byref(binding.Grid(128, 128, 128)), None, None, ctypes.byref(nb)) == 0
     assert nb.value > 30 * 132 * 132 * 132 * 8

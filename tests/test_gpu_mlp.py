@@ -208,6 +208,32 @@ def test_learned_inversion_accuracy_and_gain(trained):
     assert it_l <= 0.9 * it_off
 
 
+def test_conformal_start_equals_network_off_bitwise():
+    """KT_INV_CONFORMAL (the learned path's start without the network: e = e_conf, the same Newton
+    steps and fallback) gives the state and the Newton counts of KT_INV_LEARNED with all-zero
+    weights (whose output z is exactly 0) bit for bit, without running the inference; it needs
+    no weights, and the FP64 mode rejects it."""
+    from paper_1608_06577_gb300 import KT, KT_INV_CONFORMAL, KT_INV_LEARNED, KT_MIXED, KTError
+    from paper_1608_06577_gb300.binding import MLP_NPARAM
+    p = _small(4)
+    runs = {}
+    for name, kw in (("conformal", dict(inversion=KT_INV_CONFORMAL)),
+                     ("network_off", dict(inversion=KT_INV_LEARNED,
+                                          mlp_weights=np.zeros(MLP_NPARAM, dtype=np.float32)))):
+        kt = KT(p, precision=KT_MIXED, **kw)
+        kt.set_problem_state()
+        kt.step(12)
+        st = kt.stats()
+        runs[name] = (kt.get_state(fields=("e", "u", "pi", "Pi", "q")), st["newton_iters"], st["fallbacks"])
+        del kt
+    (a, ia, fa), (b, ib, fb) = runs["conformal"], runs["network_off"]
+    for f in ("e", "u", "pi", "Pi", "q"):
+        assert np.array_equal(a[f], b[f]), f
+    assert ia == ib and fa == fb
+    with pytest.raises(KTError):
+        KT(p, precision=0, inversion=KT_INV_CONFORMAL)
+
+
 def test_learned_start_near_tc_on_the_lattice_eos():
     """Where a start matters more: the paper's lattice EOS (Sec. 2.3), whose c_s^2 dips far below
     1/3 near T_c so that e_conf is a worse start, with eta/s = 0.2 and the zeta/s of Eq. (zetas).
