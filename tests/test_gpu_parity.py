@@ -126,6 +126,39 @@ def test_periodic_cartesian_viscous_parity_and_conservation(baseline_eos):
     assert kt2_q0 is not None
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "conformal"])
+def test_uniform_fluid_at_rest_is_stationary(mode, baseline_eos):
+    """The degenerate state: a uniform fluid at rest with pi = Pi = 0 on a periodic Cartesian grid
+    (ragged against the tiles) has every difference, face speed, flux and source equal to zero,
+    so C[q] = 0 and the Heun step leaves q unchanged: FP64 keeps every field bit for bit; mixed
+    precision keeps q bit for bit and pi = Pi = u^i = 0 exactly, with e and u^tau within an FP32
+    ulp or two (its root-find restarts from the FP32 copy of e and stops within its tolerance)."""
+    from paper_1608_06577_gb300 import KT, KT_INV_CONFORMAL, KT_MIXED
+    p = Problem(name="rest", nx=40, ny=13, neta=9, dx=0.1, dy=0.1, deta=0.1, dtau=0.01, tau0=1.0, nsteps=20,
+                coords="cartesian", bc="periodic", theta=1.0, eos=baseline_eos, eta_over_s=("const", 0.2, 0, 1),
+                zeta_over_s=("gauss", 0.1, 0.17 / HBARC, 0.03 / HBARC), tau_relax_min=0.01)
+    p.e = np.full(p.ncells, 5.0 / HBARC)
+    p.u = np.zeros((3, p.ncells))
+    p.pi = np.zeros((10, p.ncells))
+    p.Pi = np.zeros(p.ncells)
+    kw = {"fp64": {}, "mixed": {"precision": KT_MIXED},
+          "conformal": {"precision": KT_MIXED, "inversion": KT_INV_CONFORMAL}}[mode]
+    kt = KT(p, **kw)
+    kt.set_problem_state()
+    a = kt.get_state()
+    kt.step(20)
+    b = kt.get_state()
+    assert kt.stats()["status"] == 0
+    assert np.array_equal(a["q"], b["q"])
+    if mode == "fp64":
+        for f in ("e", "u", "pi", "Pi"):
+            assert np.array_equal(a[f], b[f]), f
+    else:
+        assert not np.any(b["pi"]) and not np.any(b["Pi"]) and not np.any(b["u"][1:])
+        assert np.max(np.abs(b["e"] / a["e"] - 1)) <= 2.4e-7
+        assert np.max(np.abs(b["u"][0] - 1)) <= 2.4e-7
+
+
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_sod_fp64_parity(axis):
     p = sod_problem(nx=64, dx=0.1, t_end=0.5, axis=axis)
