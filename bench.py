@@ -63,19 +63,21 @@ SLOT_BYTES = {
 # q 120, k1 60 and writes q 120, qf 60, u 16, e, p 8 = 484 (+ 4, learned): 868 B per step, k never
 # leaves the SM within a stage.
 FUSED_SLOT_BYTES = {"stage1_rhs": 380, "stage2_rhs": 488}
-FUSED_FIRST_CANDIDATE = 24  # tuning candidates 24-35 are the fused launches (chosen only explicitly)
+FUSED_FIRST_CANDIDATE = 24  # tuning candidates 24-35 are the fused launches (timed by the autotuner too)
 SLOT_KERNEL = {"stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel", "stage1_update": "update_kernel",
                "stage2_update": "update_kernel", "tau_advance": "advance_tau_kernel"}
 LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels: one-
 # kernel ncu captures of the 96^3 learned workload, per cell times the 128^3 cells (average over
-# the two stages of each kernel).  Only that mode has a capture.
-MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 765.2e6}}
+# the two stages of each kernel; the fused kernel captured on 32x2x2 tiles, one block per tile).
+# Only that mode has a capture.
+MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 762.8e6, "fused_kernel": 823.3e6}}
 # Warp instructions per 32 cells of each launch slot (ncu smsp__inst_executed.sum over the warps of
 # one-kernel captures of the 96^3 learned workload, current kernels), for each kernel's fraction of
 # the SMs' issue rate: one warp instruction per scheduler and clock, 4 schedulers per SM.  The
 # kernels are bound by instruction issue and latency rather than by HBM.
-INST_PER_WARP = {"learned": {"stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1834, "stage2_update": 1866}}
+INST_PER_WARP = {"learned": {"stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1721, "stage2_update": 1782}}
+INST_PER_WARP_FUSED = {"learned": {"stage1_rhs": 4650, "stage2_rhs": 4619}}  # the fused launches
 ISSUE_PER_SM_CLK = 4
 REPEATS = 3  # timed runs of K steps per mode; the median is reported
 
@@ -91,6 +93,8 @@ def parse():
     ap.add_argument("--train-samples", type=int, default=1_000_000)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--tuning", type=int, default=None,
+                    help="force autotuner candidate 12 v + 2 s + g of the timed mode (kt_set_tuning)")
     ap.add_argument("--large", action="store_true",
                     help="the large single event: 256x256x128, 100 hotspots, eta/s 0.2 (timing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -245,7 +249,7 @@ MODES = {"learned": (1, 1), "mixed": (1, 0), "fp64": (0, 0), "network_off": (1, 
          "learned_pi32": (1, 1)}
 
 
-def make_kt(prob, mode, weights, stream):
+def make_kt(prob, mode, weights, stream, tuning=None):
     import numpy as np
     import torch
     from paper_1608_06577_gb300 import KT
@@ -253,18 +257,21 @@ def make_kt(prob, mode, weights, stream):
     if mode == "network_off" and weights is not None:
         weights = np.zeros_like(weights)
     with torch.cuda.stream(stream):
-        return KT(prob, precision=prec, inversion=inv, mlp_weights=weights if inv == 1 else None,
-                  pi_fp32=(mode == "learned_pi32"))
+        kt = KT(prob, precision=prec, inversion=inv, mlp_weights=weights if inv == 1 else None,
+                pi_fp32=(mode == "learned_pi32"))
+        if tuning is not None:
+            kt.set_tuning(tuning)
+        return kt
 
 
-def time_mode(prob, mode, weights, steps, warmup, stream, world, profile_range=False):
+def time_mode(prob, mode, weights, steps, warmup, stream, world, profile_range=False, tuning=None):
     """Times REPEATS runs of exactly `steps` RK2 steps each (after `warmup` untimed steps) with CUDA
     events on the launching stream, each run bracketed by a barrier and a device synchronisation,
     max over ranks; returns the context and the per-run times in ms.  With profile_range the first
     timed run sits between cudaProfilerStart/Stop, so `ncu --profile-from-start off` lists exactly
     its launches."""
     import torch
-    kt = make_kt(prob, mode, weights, stream)
+    kt = make_kt(prob, mode, weights, stream, tuning)
     kt.set_problem_state()
     kt.step(warmup)
     torch.cuda.synchronize()
@@ -327,7 +334,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         if mode == args.mode:
             with ClockSampler(local) as cs:
-                kt, runs = time_mode(prob, mode, weights, steps, args.warmup, stream, world, profile_range=True)
+                kt, runs = time_mode(prob, mode, weights, steps, args.warmup, stream, world, profile_range=True,
+                                     tuning=args.tuning)
             clocks = cs.summary()
         else:
             kt, runs = time_mode(prob, mode, weights, steps, args.warmup, stream, world)
@@ -341,19 +349,25 @@ def run_ours(args, world, rank, local):
             results[mode]["slots_ms"] = kt.time_kernels(max(3, min(steps, 10)))
             tu = kt.tuning()
             best = min(range(len(tu["candidate_ms"])), key=lambda i: tu["candidate_ms"][i] or float("inf"))
+            if args.tuning is not None:
+                best = args.tuning
             results[mode]["tuning"] = {"tile": list(tu["block"]), "grid_blocks": tu["grid_blocks"],
-                                       "candidate": best, "one_block_per_tile": bool(best % 2)}
+                                       "candidate": best, "one_block_per_tile": bool(best % 2),
+                                       "layout": ("split", "split_update_staged_by_tma", "fused_stage")[best // 12]}
         del kt
         torch.cuda.empty_cache()
 
-    # Measured alternatives of the mixed-precision layout on the autotuned tile shape and grid (the
-    # autotuner times only the split launches with direct reads): the update's inputs staged in
-    # shared memory by TMA, and one fused launch per stage
+    # The other layouts of the mixed-precision stage on the autotuned tile shape and grid: split
+    # launches with direct reads, the update's inputs staged in shared memory by TMA, one fused
+    # launch per stage (the autotuner times the first and the last)
     variants = None
     if args.mode != "fp64" and not args.only_main:
         variants = {}
-        base = results[args.mode]["tuning"]["candidate"]
-        for name, v in (("split_update_staged_by_tma", 1), ("fused_stage", 2)):
+        picked = results[args.mode]["tuning"]["candidate"]
+        base = picked % 12
+        for name, v in (("split", 0), ("split_update_staged_by_tma", 1), ("fused_stage", 2)):
+            if 12 * v + base == picked:
+                continue
             kt = make_kt(prob, args.mode, weights, stream)
             kt.set_tuning(12 * v + base)
             kt.set_problem_state()
@@ -392,11 +406,11 @@ def run_ours(args, world, rank, local):
         k["launches_per_step"] += 1
         k["ms_per_step"] += t
         k["bytes_per_step"] += cells * slot_bytes.get(slot, 8.0 / cells)
-    inst = INST_PER_WARP.get(args.mode) if not fused else None
+    inst = (INST_PER_WARP_FUSED if fused else INST_PER_WARP).get(args.mode)
     sm_hz_k = ((clocks or {}).get("sm_mhz") or 2070.0) * 1e6
     for slot, t in main["slots_ms"].items():
         if inst and slot in inst and t > 0.0:
-            k = kernels[SLOT_KERNEL[slot]]
+            k = kernels["fused_kernel" if fused else SLOT_KERNEL[slot]]
             k.setdefault("warp_inst_per_step", 0.0)
             k["warp_inst_per_step"] += inst[slot] * cells / 32
     for k in kernels.values():

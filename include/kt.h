@@ -262,10 +262,10 @@ int kt_get_state_event(kt_ctx* ctx, int event, double* tau, double* e, double* u
  * 0 a right-hand-side and an update launch per stage; 1 the same with the update kernels' inputs
  * staged in shared memory by TMA bulk copies of each tile (double-buffered on a persistent grid);
  * 2 (face velocities by reconstruction) one fused launch per stage, right-hand side and update.
- * The autotuner times the candidates with v = 0 only (the other variants measured slower over a
- * whole step); kt_set_tuning selects any.  v = 1 applies to KT_MIXED with FP64 pi storage, v = 2
- * also needs KT_IFACE_RECON; elsewhere (the FP64 mode, FP32 pi storage) the v = 0 layout runs
- * whatever v is asked for. */
+ * The autotuner times the candidates with v = 0 and, where v = 2 applies, v = 2 (v = 1 measured
+ * slower over a whole step); kt_set_tuning selects any.  v = 1 applies to KT_MIXED with FP64 pi
+ * storage, v = 2 also needs KT_IFACE_RECON; elsewhere (the FP64 mode, FP32 pi storage) the v = 0
+ * layout runs whatever v is asked for. */
 int kt_get_tuning(kt_ctx* ctx, int* block_xyz, int* grid_blocks, float* candidate_ms, int* n_candidates);
 /* Use candidate `candidate` (numbered as above) from now on, without autotuning; KT_ERR_ARG if it
  * is out of range.  The results do not depend on the candidate: every candidate runs the same

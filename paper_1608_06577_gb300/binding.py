@@ -280,8 +280,8 @@ class KT:
         return {"block": tuple(blk), "grid_blocks": grid.value, "candidate_ms": list(ms)[:n.value]}
 
     def set_tuning(self, candidate: int) -> None:
-        """Use autotuner candidate `candidate` = 2 s + g (tile shape s, grid variant g) from now on
-        (kt_set_tuning)."""
+        """Use autotuner candidate `candidate` = 12 v + 2 s + g (layout v, tile shape s, grid variant
+        g) from now on (kt_set_tuning)."""
         self._check(self.L.kt_set_tuning(self.ctx, int(candidate)), "kt_set_tuning")
 
     KERNEL_SLOTS = ("stage1_rhs", "stage1_update", "stage2_rhs", "stage2_update", "tau_advance")

@@ -34,11 +34,12 @@ constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 // candidates: every shape with a persistent grid (blocks resident at once) and with one block per tile,
 // each (mixed precision) as a right-hand-side and an update launch per stage, the update reading
 // its inputs directly or staged by TMA, or as one fused launch per stage.  The autotuner times the
-// first 12 (two launches per stage, direct reads): the other two variants measured slower over a
-// whole step and are selected only by kt_set_tuning.
-constexpr int kNumTuned = 2 * kNumShapes;
+// split launches with direct reads (0-11) and, where the context can run them, the fused ones
+// (24-35); the TMA-staged update measured slower over a whole step and is selected only by
+// kt_set_tuning.
 constexpr int kNumBase = 2 * kNumShapes;
 constexpr int kNumCandidates = 3 * kNumBase;
+constexpr int kFusedFirst = 2 * kNumBase;
 
 struct Ctx {
   kt_options opt;
@@ -67,6 +68,7 @@ struct Ctx {
   EosSeg<double>* seg_d = nullptr;
   EosSeg<float>* seg_f = nullptr;
   RootSeg* seg_r = nullptr;
+  RootSegM* seg_m = nullptr;
   double* d_tau = nullptr;
   unsigned* d_stat = nullptr;
   float* d_mlp = nullptr;
@@ -183,6 +185,7 @@ size_t state_bytes(const std::vector<Lattice>& lat, long long gs, size_t max_cel
   b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(EosSeg<double>), 256);
   b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(EosSeg<float>), 256);
   b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(RootSeg), 256);
+  b += align_up((size_t)(eos_n > 0 ? eos_n : 1) * sizeof(RootSegM), 256);
   b += 256;                                    // tau
   b += 256;                                    // stats
   b += align_up(KT_MLP_NPARAM * 4, 256);       // MLP weights
@@ -271,6 +274,26 @@ void build_root_segments(const std::vector<EosSeg<double>>& sd, const std::vecto
     r.b3 = three * sf[i].a3;
     r.unused = 0.f;
     out[i] = r;
+  }
+}
+
+// The mixed-precision root-find's records: the FP64 ones with a2, a3 rounded to single precision.
+void build_mixed_root_segments(const std::vector<RootSeg>& sr, std::vector<RootSegM>& out) {
+  out.resize(sr.size());
+  for (size_t i = 0; i < sr.size(); ++i) {
+    const RootSeg& r = sr[i];
+    RootSegM m;
+    m.e0 = r.e0;
+    m.e1 = r.e1;
+    m.P0 = r.P0;
+    m.a1 = r.a1;
+    m.a2 = (float)r.a2;
+    m.a3 = (float)r.a3;
+    m.b1 = r.b1;
+    m.b2 = r.b2;
+    m.b3 = r.b3;
+    m.unused0 = m.unused1 = m.unused2 = 0.f;
+    out[i] = m;
   }
 }
 
@@ -864,7 +887,9 @@ int autotune(Ctx* c) {
   Range range_("kt autotune");
   int best = 0;
   for (int s = 0; s < kNumCandidates; ++s) c->tune_ms[s] = 0.f;
-  for (int s = 0; s < kNumTuned; ++s) {
+  const bool fusable = c->mixed && !c->pi32 && !c->P.iface_invert;
+  for (int s = 0; s < kNumCandidates; ++s) {
+    if (!(s < kNumBase || (fusable && s >= kFusedFirst))) continue;
     int rc = select_shape(c, s);
     if (rc != KT_OK) return rc;
     float ms = 0.f;
@@ -1069,6 +1094,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   c->seg_d = (EosSeg<double>*)carve(nseg * sizeof(EosSeg<double>));
   c->seg_f = (EosSeg<float>*)carve(nseg * sizeof(EosSeg<float>));
   c->seg_r = (RootSeg*)carve(nseg * sizeof(RootSeg));
+  c->seg_m = (RootSegM*)carve(nseg * sizeof(RootSegM));
   c->d_tau = (double*)carve(256);
   c->d_stat = (unsigned*)carve(256);
   c->d_mlp = (float*)carve(KT_MLP_NPARAM * 4);
@@ -1083,6 +1109,7 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   P.seg_d = c->seg_d;
   P.seg_f = c->seg_f;
   P.seg_r = c->seg_r;
+  P.seg_m = c->seg_m;
 
   CK(cudaMemsetAsync(qq, 0, 30 * fs * 8, c->stream));
   CK(cudaMemsetAsync(ep, 0, 4 * fs * c->esz, c->stream));
@@ -1105,9 +1132,12 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
     build_segments<float>(eos, sf);
     std::vector<RootSeg> sr;
     build_root_segments(sd, sf, sr);
+    std::vector<RootSegM> sm;
+    build_mixed_root_segments(sr, sm);
     CK(cudaMemcpyAsync(c->seg_d, sd.data(), sd.size() * sizeof(sd[0]), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->seg_f, sf.data(), sf.size() * sizeof(sf[0]), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->seg_r, sr.data(), sr.size() * sizeof(sr[0]), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->seg_m, sm.data(), sm.size() * sizeof(sm[0]), cudaMemcpyHostToDevice, c->stream));
   }
   if (o.mlp_weights) {
     CK(cudaMemcpyAsync(c->d_mlp, o.mlp_weights, KT_MLP_NPARAM * 4, cudaMemcpyHostToDevice, c->stream));

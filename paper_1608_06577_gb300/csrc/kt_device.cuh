@@ -63,6 +63,18 @@ struct alignas(64) RootSeg {
   float b1, b2, b3, unused;
 };
 
+// The mixed-precision root-find's record of the same interval: e0, e1, P0 and a1 in FP64, the
+// cubic's a2 and a3 rounded to single precision, b1-b3 as in RootSeg.  In d = e - e0 the
+// correction d (a2 + d a3) to a1 is below 1e-3 of a1 inside the table (intervals of ~1% in e,
+// c_s^2 varying by ~1e-4 across one), so forming it in single precision moves P0(e) by ~1e-12
+// of itself -- far inside the root-find's 1e-10 acceptance -- and takes one FP64 instruction
+// per residual off the slow FP64 pipe.
+struct alignas(64) RootSegM {
+  double e0, e1, P0, a1;
+  float a2, a3, b1, b2;
+  float b3, unused0, unused1, unused2;
+};
+
 struct Coef {
   int kind;       // 0 const, 1 gauss
   double c0, c1, c2;
@@ -97,6 +109,7 @@ struct Params {
   const EosSeg<double>* seg_d;
   const EosSeg<float>* seg_f;
   const RootSeg* seg_r;
+  const RootSegM* seg_m;  // the same intervals for the mixed-precision root-find
   Coef eta, zeta;
   int shear_on, bulk_on;
   double tpp;         // tau_pipi / tau_pi (10/7 or 0)

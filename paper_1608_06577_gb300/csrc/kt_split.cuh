@@ -157,41 +157,53 @@ __global__ void __maxnreg__(96)
 // ------------------------------------------------------------- d) the root-find (Sec. 2.4)
 // Learned start: from e_start at most two Newton steps; the root is accepted as soon as
 // |f(e)| <= 1e-10 E, i.e. |g| <= 1e-10 E A; otherwise the plain root-find continues from the
-// last iterate and the cell counts as a fallback.
-__device__ __forceinline__ unsigned rootfind_learned(const Params& P, double E, double EPi, double M2, float M2f,
-                                                     double e_start, double& e, double& P0, unsigned& iters,
-                                                     unsigned& fallbacks) {
+// last iterate and the cell counts as a fallback.  The test costs no FP64 instruction: the
+// threshold 0.99e-10 E A is formed in single precision from E and A truncated, and |g| is
+// compared with it on the upper 32 bits of both doubles (strictly below).  The 1% margin covers
+// the single-precision rounding of the threshold and the mixed records' P0 (g is evaluated with
+// P0 within ~2e-13 E A of the FP64 cubic's inside the table), so an accepted root satisfies
+// the exact test.
+__device__ __forceinline__ unsigned abs_hi(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+// upper 32 bits of the double equal to the positive normal float t (0 for a smaller or non-finite t)
+__device__ __forceinline__ unsigned thr_hi(float t) {
+  const unsigned b = __float_as_uint(t);
+  return (b >= 0x00800000u && b < 0x7f800000u) ? (b >> 3) + (896u << 20) : 0u;
+}
+__device__ __forceinline__ unsigned rootfind_learned(const Params& P, const InvIn& v, double EPi, double e_start,
+                                                     double& e, double& P0, unsigned& iters, unsigned& fallbacks) {
   const double lo = (P.e_min > 0.0) ? P.e_min : 1e-300;
-  const double tol = 1e-10 * E;
-  e = clamp_pos(e_start, lo, E);
+  const float tolf = 0.99e-10f * v.Ef;
+  e = clamp_pos(e_start, lo, v.E);
 #pragma unroll 1
   for (int kk = 0; kk < 3; ++kk) {
-    const Resid r = residual(P, e, E, EPi, M2, M2f);
-    if (abits(r.g) <= obits(tol * r.A)) {
+    const Resid r = residual<true>(P, e, v.E, EPi, v.M2, v.M2f);
+    if (abs_hi(r.g) < thr_hi(tolf * r.Af)) {
       P0 = r.p0;
       return 0u;
     }
     if (kk == 2) break;
-    e = clamp_pos(newton_step(e, r), lo, E);
+    e = clamp_pos(newton_step(e, r), lo, v.E);
     ++iters;
   }
   ++fallbacks;
-  return rootfind_plain(P, E, EPi, M2, M2f, e, e, P0, iters);
+  return rootfind_plain(P, v.E, EPi, v.M2, v.M2f, e, e, P0, iters);
 }
 
-// T^{tau mu} -> (e, P0, u^mu) at tau^{n+1} for the mixed path (Eqs. eInferred-uiInferred).  With
+// (E, M^i, Pi) -> (e, P0, u^mu) at tau^{n+1} for the mixed path (Eqs. eInferred-uiInferred).  With
 // the conformal EOS and no bulk pressure the closed form e = sqrt(4E^2 - 3M^2) - E is used.
+// M^2 < E^2 is decided in single precision, with a margin, where E and M^2 lie well inside its
+// range (M^2 < 0.998 E^2 in the truncated values makes it certain), else by the FP64 product.
 template <bool LEARNED>
-__device__ __forceinline__ unsigned invert_split(const Params& P, double gnn, const double (&qn)[NQ], double start,
-                                                 double& e, double& P0, float (&uo)[4], unsigned& iters,
-                                                 unsigned& fallbacks) {
-  const double E = qn[0] - qn[4];
-  const double Mx = qn[1] - qn[5], My = qn[2] - qn[6], Mn = qn[3] - qn[7];
-  const double Pi = qn[14];
-  const double M2 = fma(gnn * Mn, Mn, fma(My, My, Mx * Mx));
-  const long long bE = obits(E);
+__device__ __forceinline__ unsigned invert_split(const Params& P, const InvIn& v, double start, double& e,
+                                                 double& P0, float (&uo)[4], unsigned& iters, unsigned& fallbacks) {
+  const double E = v.E, M2 = v.M2, Pi = v.Pi;
+  const long long bE = obits(E), bM2 = obits(M2);
+  bool ok = bE > 0 && bE < 0x7ff0000000000000LL;  // E > 0 finite
+  if (ok && !(bE > 0x3c30000000000000LL && bE < 0x43b0000000000000LL && bM2 < 0x4770000000000000LL &&
+              v.M2f < 0.998f * v.Ef * v.Ef))  // 2^-60 < E < 2^60, M^2 < 2^120
+    ok = bM2 < obits(E * E);
   unsigned st = 0;
-  if (!(bE > 0 && bE < 0x7ff0000000000000LL) || !(obits(M2) < obits(E * E))) {  // E > 0 finite, M^2 < E^2
+  if (!ok) {
     st = ST_INVERSION;
     e = (P.e_min > 0.0) ? P.e_min : 1e-30;
     P0 = e * (1.0 / 3.0);
@@ -205,9 +217,9 @@ __device__ __forceinline__ unsigned invert_split(const Params& P, double gnn, co
     }
     P0 = e * (1.0 / 3.0);
   } else if (LEARNED) {
-    st = rootfind_learned(P, E, E + Pi, M2, d2f_trunc(M2), start, e, P0, iters, fallbacks);
+    st = rootfind_learned(P, v, E + Pi, start, e, P0, iters, fallbacks);
   } else {
-    st = rootfind_plain(P, E, E + Pi, M2, d2f_trunc(M2), start, e, P0, iters);
+    st = rootfind_plain(P, E, E + Pi, M2, v.M2f, start, e, P0, iters);
   }
   if (st) {
     uo[0] = 1.f;
@@ -219,9 +231,9 @@ __device__ __forceinline__ unsigned invert_split(const Params& P, double gnn, co
     const float ut = sqrtf(__fdividef(EPt, ePt));
     const float w = __fdividef(1.f, ePt * ut);
     uo[0] = ut;
-    uo[1] = d2f_bits(Mx) * w;
-    uo[2] = d2f_bits(My) * w;
-    uo[3] = d2f_bits(Mn) * w;
+    uo[1] = d2f_bits(v.Mx) * w;
+    uo[2] = d2f_bits(v.My) * w;
+    uo[3] = d2f_bits(v.Mn) * w;
   }
   if (!isfinite(uo[0]) || !isfinite(uo[1]) || !isfinite(uo[2]) || !isfinite(uo[3]) ||
       !((obits(e) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL))
@@ -274,23 +286,42 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   float qp[NQ];   // FP32 pi storage: the new pi, Pi (components 4-14)
 #pragma unroll
   for (int n = 0; n < NQ; ++n) qn[n] = (n == 0) ? 1.0 : 0.0;  // a harmless rest state past the edge
+  // Stage 1 with FP64 pi storage stores no FP64 state: the inversion's E = (T^tt - pi^tt) + the
+  // single-precision difference of their increments in k_1 (likewise M^i), two FP64 additions
+  // per pair instead of three; otherwise E, M^i are differences of the new FP64 components.
+  constexpr bool kDiff = (STAGE == 1) && !PI32;
+  double E = 1.0, Mx = 0.0, My = 0.0, Mn = 0.0, Pi = 0.0;
   if (valid) {
+    if constexpr (kDiff) {
+      E = (in.q(0) - in.q(4)) + to_f64<float>(in.k1(0) - in.k1(4));
+      Mx = (in.q(1) - in.q(5)) + to_f64<float>(in.k1(1) - in.k1(5));
+      My = (in.q(2) - in.q(6)) + to_f64<float>(in.k1(2) - in.k1(6));
+      Mn = (in.q(3) - in.q(7)) + to_f64<float>(in.k1(3) - in.k1(7));
+      Pi = in.q(14) + to_f64<float>(in.k1(14));
+    } else {
 #pragma unroll
-    for (int n = 0; n < NQ; ++n) {
-      if (PI32 && n >= 4) {
-        qp[n] = pi32_state<STAGE>(in, n);
-        if (inversion_component(n)) qn[n] = to_f64<float>(qp[n]);  // exact widening for E, M^i, Pi
-      } else if (inversion_component(n)) {
-        qn[n] = in.q(n) + to_f64<float>(increment<STAGE>(in, n));
+      for (int n = 0; n < NQ; ++n) {
+        if (PI32 && n >= 4) {
+          qp[n] = pi32_state<STAGE>(in, n);
+          if (inversion_component(n)) qn[n] = to_f64<float>(qp[n]);  // exact widening for E, M^i, Pi
+        } else if (inversion_component(n)) {
+          qn[n] = in.q(n) + to_f64<float>(increment<STAGE>(in, n));
+        }
       }
+      E = qn[0] - qn[4];
+      Mx = qn[1] - qn[5];
+      My = qn[2] - qn[6];
+      Mn = qn[3] - qn[7];
+      Pi = qn[14];
     }
   }
 
   const double gnn = P.milne ? tau_out * tau_out : 1.0;
+  const InvIn v = inv_in(gnn, E, Mx, My, Mn, Pi);
   double start;
   if constexpr (LEARNED) {
     float z = (STAGE == 2 && valid) ? __ldg(io.z_net + c) : 0.f;
-    start = learned_start<STAGE == 1>(P, gnn, qn, s_mlp, z);
+    start = learned_start<STAGE == 1>(P, v, s_mlp, z);
     if (STAGE == 1 && valid) io.z_net[c] = z;
   } else {
     start = valid ? to_f64<float>(__ldg(io.e_guess + c)) : 1.0;
@@ -299,7 +330,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   if (!valid) return;
   double e, P0;
   float uo[4];
-  st |= invert_split<LEARNED>(P, gnn, qn, start, e, P0, uo, nit, nfb);
+  st |= invert_split<LEARNED>(P, v, start, e, P0, uo, nit, nfb);
 
   // the FP32 copy read by the next stencil (and the remaining FP64 components in stage 2)
   // Stage 2 forms pi components 8-13 as f q^n + f dq in one FP64 multiply-add once the
@@ -415,7 +446,7 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
                   int ntiles) {
   unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
   constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
-  __shared__ uint32_t s_mlp[kInfer ? PK_WORDS : 1];
+  __shared__ alignas(16) uint32_t s_mlp[kInfer ? PK_WORDS : 1];
   if constexpr (kInfer) {
     if (P.mlp_infer) mlp_load_shared(s_mlp, io.mlp_packed);
     __syncthreads();
@@ -472,7 +503,7 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
   extern __shared__ __align__(128) unsigned char u_raw[];
   __shared__ alignas(8) uint64_t s_bar[2];
   constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
-  __shared__ uint32_t s_mlp[kInfer ? PK_WORDS : 1];
+  __shared__ alignas(16) uint32_t s_mlp[kInfer ? PK_WORDS : 1];
   unsigned char* const sbase = u_raw + ((128u - (smem_u32(u_raw) & 127u)) & 127u);
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int bc = (blockDim.x + 4) * blockDim.y * blockDim.z;
@@ -578,7 +609,7 @@ __global__ void __maxnreg__(128)
   extern __shared__ __align__(128) float s_raw[];
   __shared__ alignas(8) uint64_t s_bar[2];
   constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
-  __shared__ uint32_t s_mlp[kInfer ? PK_WORDS : 1];
+  __shared__ alignas(16) uint32_t s_mlp[kInfer ? PK_WORDS : 1];
   float* const s_q = s_raw + ((32u - ((smem_u32(s_raw) >> 2) & 31u)) & 31u);  // TMA wants 128-byte buffers
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);

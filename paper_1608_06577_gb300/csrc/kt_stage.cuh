@@ -396,19 +396,27 @@ __device__ __forceinline__ double clamp_pos(double x, double lo, double hi) {  /
 // eos_interval, checked against both ends of the interval in the same load; only a guess that
 // misses (next to a node) searches as eos_interval does (integer comparisons of the bit patterns)
 // and loads again.  The same interval as eos_interval, with one dependent load instead of three.
+// Seg is RootSeg (FP64 path) or RootSegM (mixed precision); both start with e0, e1.
 __device__ __forceinline__ RootSeg load_root_seg(const RootSeg* p) {
   const double2* d = reinterpret_cast<const double2*>(p);
   const double2 v0 = __ldg(d), v1 = __ldg(d + 1), v2 = __ldg(d + 2);
   const float4 v3 = __ldg(reinterpret_cast<const float4*>(p) + 3);
   return RootSeg{v0.x, v0.y, v1.x, v1.y, v2.x, v2.y, v3.x, v3.y, v3.z, v3.w};
 }
-__device__ __forceinline__ RootSeg root_seg(const Params& P, double e) {
-  const RootSeg* seg = P.seg_r;
+__device__ __forceinline__ RootSegM load_root_seg(const RootSegM* p) {
+  const double2* d = reinterpret_cast<const double2*>(p);
+  const double2 v0 = __ldg(d), v1 = __ldg(d + 1);
+  const float4 v2 = __ldg(reinterpret_cast<const float4*>(p) + 2);
+  const float b3 = __ldg(reinterpret_cast<const float*>(p) + 12);
+  return RootSegM{v0.x, v0.y, v1.x, v1.y, v2.x, v2.y, v2.z, v2.w, b3, 0.f, 0.f, 0.f};
+}
+template <typename Seg>
+__device__ __forceinline__ Seg root_seg(const Params& P, const Seg* seg, double e) {
   const int n1 = P.eos_n - 2;
   const float g = (__logf(d2f_trunc(e)) - P.lne0) * P.inv_h;
   int i = min((g > 0.f) ? (int)g : 0, n1);  // NaN compares false -> 0
   const long long b = obits(e);
-  RootSeg s = load_root_seg(seg + i);
+  Seg s = load_root_seg(seg + i);
   if ((i > 0 && b < obits(s.e0)) || b >= obits(s.e1)) {
 #pragma unroll 1
     for (int it = 0; it < 64 && i > 0 && b < obits(seg[i].e0); ++it) --i;
@@ -419,27 +427,49 @@ __device__ __forceinline__ RootSeg root_seg(const Params& P, double e) {
   return s;
 }
 
+// the interval's record for the FP64 path (RootSeg) or the mixed-precision one (RootSegM)
+template <bool MIXED>
+__device__ __forceinline__ auto path_seg(const Params& P, double e) {
+  if constexpr (MIXED) return root_seg(P, P.seg_m, e);
+  else return root_seg(P, P.seg_r, e);
+}
+
+// P0(e) in d = e - e0 on the interval's record: the cubic in FP64 (RootSeg), or (RootSegM) its
+// leading part in FP64 with the correction d (a2 + d a3) to a1 formed in single precision from
+// df, the single-precision d.
+__device__ __forceinline__ double seg_P(const RootSeg& s, double d, float) {
+  return fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
+}
+__device__ __forceinline__ double seg_P(const RootSegM& s, double d, float df) {
+  return fma(d, s.a1 + f2d_bits(df * fmaf(df, s.a3, s.a2)), s.P0);
+}
+
 // The residual in product form g(e) = (e - E) A(e) + M^2 = f(e) A(e), A = E + P0(e) + Pi > 0:
 // the root and the sign of f(e) = e - E + M^2 / A of Eq. (eInferred), without a reciprocal.
-// Also A, P0(e) and, in single precision, A f'(e) = A - M^2 c_s^2 / A: the Newton step on f,
-// e - f/f' = e - g/(A f'), then needs the FP64 product of g with a single-precision factor
-// (which only sets the step length; f is nearly linear in e where M is small, g is not).
+// Also A, P0(e) and, in single precision, A (truncated) and A f'(e) = A - M^2 c_s^2 / A: the
+// Newton step on f, e - f/f' = e - g/(A f'), then needs the FP64 product of g with a
+// single-precision factor (which only sets the step length; f is nearly linear in e where M is
+// small, g is not).  MIXED: P0 from the mixed-precision records (RootSegM), whose rounding of the
+// cubic's correction term (~1e-13 of P0, in steps as d crosses single-precision values) is far
+// below the learned start's 1e-10 acceptance but above the plain root-find's 2^-50 stop, so only
+// the learned start's Newton steps use it.
 struct Resid {
   double g, A, p0;
-  float gp;
+  float gp, Af;
 };
+template <bool MIXED>
 __device__ __forceinline__ Resid residual(const Params& P, double e, double E, double EPi, double M2, float M2f) {
-  const RootSeg s = root_seg(P, e);
+  const auto s = path_seg<MIXED>(P, e);
   const double d = e - s.e0;
+  const float df = d2f_trunc(d);
   Resid r;
-  r.p0 = fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
+  r.p0 = seg_P(s, d, df);
   r.A = EPi + r.p0;
   const double em = e - E;
   r.g = fma(em, r.A, M2);
-  const float df = d2f_trunc(d);
   const float c2 = fmaf(df, fmaf(df, s.b3, s.b2), s.b1);
-  const float Af = d2f_trunc(r.A);
-  r.gp = Af - __fdividef(M2f * c2, Af);
+  r.Af = d2f_trunc(r.A);
+  r.gp = r.Af - __fdividef(M2f * c2, r.Af);
   return r;
 }
 
@@ -450,22 +480,22 @@ __device__ __forceinline__ double newton_step(double e, const Resid& r) {
 
 // P0(e) on the FP64 table
 __device__ __forceinline__ double eos_P_pos(const Params& P, double e) {
-  const RootSeg s = root_seg(P, e);
-  const double d = e - s.e0;
-  return fma(d, fma(d, fma(d, s.a3, s.a2), s.a1), s.P0);
+  const RootSeg s = root_seg(P, P.seg_r, e);
+  return seg_P(s, e - s.e0, 0.f);
 }
 
 // Plain root-find: safeguarded Newton inside the bracket [e_min, E] (a step that leaves it
 // bisects), from `start` if it lies inside, else from E; stop at |de| <= 2^-50 E (g is known to
-// about one ulp of E A), at most 100 steps.  Table EOS only.
+// about one ulp of E A), at most 100 steps.  Table EOS only.  The stop's bit pattern is E's with
+// the exponent lowered by 50 (exact for E >= 2^-972; smaller E stops only at de = 0).
 __device__ __forceinline__ unsigned rootfind_plain(const Params& P, double E, double EPi, double M2, float M2f,
                                                    double start, double& e, double& P0, unsigned& iters) {
   double lo = (P.e_min > 0.0) ? P.e_min : 1e-300, hi = E;
   e = (obits(start) >= obits(lo) && obits(start) <= obits(hi)) ? start : hi;
-  const long long stop = obits(E * 0x1p-50);
+  const long long stop = max(obits(E) - (50LL << 52), 0LL);
   int it;
   for (it = 0; it < 100; ++it) {
-    const Resid r = residual(P, e, E, EPi, M2, M2f);
+    const Resid r = residual<false>(P, e, E, EPi, M2, M2f);
     if (abits(r.g) == 0) break;
     if (obits(r.g) < 0) lo = e; else hi = e;
     double en = newton_step(e, r);
@@ -816,28 +846,39 @@ __device__ __forceinline__ void cell_sources(const Params& P, const Lattice& L, 
   }
 }
 
-// The network's start for the root-find of the cell's new state qn (components 0-7 and 14 are
-// read): features in FP32, the network's output z, and the conformal root corrected by
-// y = r^2 z (r^2 = M^2/E^2, feature 1): e = E (e_conf/E) exp(y/10).  The correction vanishes at
-// rest, where e_conf = E is the root, and the network's BF16 error scales with it.  The network
-// runs once per cell and step: with INFER (the first stage) the warp-wide tensor-core inference
-// gives z, which is returned in z_io (a warp whose cells all have r^2 <= kMlpGateR2 skips it);
-// otherwise (the second stage, whose state differs by O(dtau)) z_io holds that z on entry.  All
-// 32 lanes of the warp call it together.  E, M^2 in single precision from the FP64 components
-// (they only feed the features and the start).
+// The inversion's inputs at one cell (Eqs. eInferred-uiInferred): E = T^tt - pi^tt,
+// M^i = T^ti - pi^ti, Pi and M^2 = M_x^2 + M_y^2 + g_nn M_n^2 in FP64; E and M^2 also truncated to
+// single precision for the network's features, the Newton step factor and the quick test of
+// M^2 < E^2.
+struct InvIn {
+  double E, Mx, My, Mn, Pi, M2;
+  float Ef, M2f;
+};
+__device__ __forceinline__ InvIn inv_in(double gnn, double E, double Mx, double My, double Mn, double Pi) {
+  InvIn v;
+  v.E = E; v.Mx = Mx; v.My = My; v.Mn = Mn; v.Pi = Pi;
+  v.M2 = fma(gnn * Mn, Mn, fma(My, My, Mx * Mx));
+  v.Ef = d2f_trunc(E);
+  v.M2f = d2f_trunc(v.M2);
+  return v;
+}
+
+// The network's start for the root-find of the inversion inputs v: features in FP32, the
+// network's output z, and the conformal root corrected by y = r^2 z (r^2 = M^2/E^2, feature 1):
+// e = E (e_conf/E) exp(y/10).  The correction vanishes at rest, where e_conf = E is the root, and
+// the network's BF16 error scales with it.  The network runs once per cell and step: with INFER
+// (the first stage) the warp-wide tensor-core inference gives z, which is returned in z_io (a warp
+// whose cells all have r^2 <= kMlpGateR2 skips it); otherwise (the second stage, whose state
+// differs by O(dtau)) z_io holds that z on entry.  All 32 lanes of the warp call it together.
 template <bool INFER>
-__device__ __forceinline__ double learned_start(const Params& P, double gnn, const double (&qn)[NQ],
-                                                const uint32_t* s_mlp, float& z_io) {
-  const float Ef = d2f_trunc(qn[0]) - d2f_trunc(qn[4]);
-  const float Mx = d2f_trunc(qn[1]) - d2f_trunc(qn[5]), My = d2f_trunc(qn[2]) - d2f_trunc(qn[6]),
-              Mn = d2f_trunc(qn[3]) - d2f_trunc(qn[7]);
-  const float M2f = fmaf(Mx, Mx, fmaf(My, My, d2f_trunc(gnn) * Mn * Mn));
+__device__ __forceinline__ double learned_start(const Params& P, const InvIn& v, const uint32_t* s_mlp,
+                                                float& z_io) {
   float x[MLP_IN], ecE;
-  mlp_features(fmaxf(Ef, 1e-30f), M2f, d2f_trunc(qn[14]), x, ecE);
+  mlp_features(fmaxf(v.Ef, 1e-30f), v.M2f, d2f_trunc(v.Pi), x, ecE);
   if constexpr (INFER)
     z_io = (P.mlp_infer && __any_sync(0xffffffffu, x[1] > kMlpGateR2)) ? mlp_warp_infer(s_mlp, x) : 0.f;
   const float y = (x[1] > kMlpGateR2) ? x[1] * z_io : 0.f;
-  return f2d_bits(Ef * ecE * __expf(0.1f * y));
+  return f2d_bits(v.Ef * ecE * __expf(0.1f * y));
 }
 
 // ---------------------------------------------------------------- one cell of a tile (FP64)

@@ -56,18 +56,23 @@ def test_batch_fp64_matches_oracle():
         assert not bad, (ev, bad)
 
 
-def test_autotuner_reports_and_picks_fastest():
+@pytest.mark.parametrize("pi_fp32", [False, True])
+def test_autotuner_reports_and_picks_fastest(pi_fp32):
+    """The autotuner times both grid variants of every tile shape as split launches and, where the
+    context can run them (FP64 pi storage), as fused launches, and keeps the fastest."""
     from paper_1608_06577_gb300 import KT
     p = hotspot_problem(nx=48, ny=40, neta=16, nhot=8, r_max=1.0)
-    k = KT(p, precision=1)
+    k = KT(p, precision=1, pi_fp32=pi_fp32)
     k.set_problem_state()
     k.step(3)
     t = k.tuning()
-    ms = [m for m in t["candidate_ms"] if m > 0]
+    ms = np.array(t["candidate_ms"])
     shapes = [(32, 4, 2), (32, 8, 1), (32, 2, 4), (32, 1, 8), (32, 4, 1), (32, 2, 2)]
-    # 2 grid variants per shape are timed (the staged and fused variants are selected explicitly)
-    assert len(t["candidate_ms"]) == 6 * len(shapes) and len(ms) == 2 * len(shapes)
-    assert t["block"] == shapes[int(np.argmin(ms)) // 2]
+    timed = np.flatnonzero(ms > 0)
+    expect = list(range(12)) + ([] if pi_fp32 else list(range(24, 36)))
+    assert len(ms) == 6 * len(shapes) and list(timed) == expect
+    best = int(timed[np.argmin(ms[timed])])
+    assert t["block"] == shapes[(best % 12) // 2]
     assert t["grid_blocks"] >= 1
 
 

@@ -72,17 +72,27 @@ def test_gradient_matches_fp64_backprop():
     assert np.max(np.abs(gb.cpu().numpy() - gr)) < 5e-2 * np.max(np.abs(gr))
 
 
-def test_tensor_core_inference_matches_reference():
+@pytest.mark.parametrize("seed", [1, 6, 11])
+def test_tensor_core_inference_matches_reference(seed):
+    """The tensor-core inference against the FP64 forward with the same BF16 rounding points.  Only
+    the accumulation differs (FP32 in the MMAs): a row agrees to ~1e-7 of the output scale unless a
+    hidden activation lies within that of a BF16 rounding boundary and rounds to the neighbouring
+    value on one side.  Over 40 weight draws (1000 rows each) every row agreed to 1.2e-7 of the
+    scale except at most one row per draw, whose error reached 1.6e-3 (seed 11), 1.5e-4 (seed 6).
+    So: at most 3 rows above 1e-6 of the scale, and every row within 4e-3."""
     torch = _torch()
     from paper_1608_06577_gb300.binding import mlp_predict
-    rng = np.random.default_rng(1)
+    rng = np.random.default_rng(seed)
     p = (rng.normal(size=omlp.NPARAM) * 0.3).astype(np.float32)
     X = rng.normal(size=(1000, 6)).astype(np.float32)  # not a multiple of 32: ragged last warp
     y = mlp_predict(torch.as_tensor(p, device="cuda"), torch.as_tensor(X, device="cuda")).cpu().numpy()
     yb, _ = omlp.forward(p, X, bf16=True)
     yf, _ = omlp.forward(p, X, bf16=False)
     scale = np.max(np.abs(yf))
-    assert np.max(np.abs(y - yb)) < 1e-2 * scale   # same rounding points, FP32 accumulation order
+    err = np.abs(y - yb) / scale
+    print(f"seed {seed}: max {err.max():.2e}, rows above 1e-6: {(err > 1e-6).sum()}")
+    assert (err > 1e-6).sum() <= 3      # FP32 accumulation order only
+    assert err.max() < 4e-3             # at most one activation on the other side of a BF16 rounding
     assert np.max(np.abs(y - yf)) < 5e-2 * scale   # BF16 weights and activations vs exact FP64
 
 
