@@ -69,15 +69,15 @@ SLOT_KERNEL = {"stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel", "stage1_u
 LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels: one-
 # kernel ncu captures of the 96^3 learned workload, per cell times the 128^3 cells (average over
-# the two stages of each kernel; the fused kernel captured on 32x2x2 tiles, one block per tile).
-# Only that mode has a capture.
-MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 762.8e6, "fused_kernel": 823.3e6}}
+# the two stages of each kernel; the update and fused kernels captured on 32x2x2 tiles, one block
+# per tile).  Only that mode (workload EOS) has a capture.
+MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 761.9e6, "fused_kernel": 826.7e6}}
 # Warp instructions per 32 cells of each launch slot (ncu smsp__inst_executed.sum over the warps of
 # one-kernel captures of the 96^3 learned workload, current kernels), for each kernel's fraction of
 # the SMs' issue rate: one warp instruction per scheduler and clock, 4 schedulers per SM.  The
 # kernels are bound by instruction issue and latency rather than by HBM.
-INST_PER_WARP = {"learned": {"stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1721, "stage2_update": 1782}}
-INST_PER_WARP_FUSED = {"learned": {"stage1_rhs": 4650, "stage2_rhs": 4619}}  # the fused launches
+INST_PER_WARP = {"learned": {"stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1906, "stage2_update": 1910}}
+INST_PER_WARP_FUSED = {"learned": {"stage1_rhs": 4615, "stage2_rhs": 4619}}  # the fused launches
 ISSUE_PER_SM_CLK = 4
 REPEATS = 3  # timed runs of K steps per mode; the median is reported
 
@@ -426,7 +426,7 @@ def run_ours(args, world, rank, local):
         k["share"] = k["ms_per_step"] / sum(v["ms_per_step"] for v in kernels.values())
         k["share_of_step_bytes"] = k["bytes_per_step"] / (cells * bpc)
     dom = max(kernels, key=lambda n: kernels[n]["ms_per_step"])
-    traffic_k = None if args.large else MEASURED_TRAFFIC.get((args.mode, n))
+    traffic_k = None if (args.large or args.eos != "workload") else MEASURED_TRAFFIC.get((args.mode, n))
     traffic = None
     if traffic_k and all(k in traffic_k for k in kernels if k != "advance_tau_kernel"):
         # DRAM bytes per step: every kernel's recorded traffic per launch times its launches

@@ -369,7 +369,7 @@ __global__ void mlp_pack_kernel(const float* __restrict__ params, uint32_t* pack
 // tensor-core inference over an array of feature rows
 __global__ void __launch_bounds__(256) mlp_predict_kernel(const uint32_t* __restrict__ packed,
                                                           const float* __restrict__ X, long long n, float* Y) {
-  __shared__ uint32_t sw[PK_WORDS];
+  __shared__ alignas(16) uint32_t sw[PK_WORDS];
   mlp_load_shared(sw, packed);
   __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

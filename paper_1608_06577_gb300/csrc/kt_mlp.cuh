@@ -45,6 +45,17 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
 }
+// ReLU and the rounding to BF16 in one conversion: max(x, 0) rounded to nearest (a negative x
+// gives zero); lo in the low half
+__device__ __forceinline__ uint32_t pack_relu_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// the biases of output columns 2t, 2t + 1 (one 8-byte shared-memory load; w is 16-byte aligned)
+__device__ __forceinline__ float2 bias_pair(const uint32_t* w, int off) {
+  return *reinterpret_cast<const float2*>(w + off);
+}
 
 __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                                uint32_t b0, uint32_t b1) {
@@ -56,7 +67,7 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint3
 }
 
 // Inference for the 32 cells of a warp (lane = cell); all 32 lanes must call it together.
-// w: packed weights (shared memory).  Fragment layouts are those of mma.m16n8k16: lane =
+// w: packed weights (shared memory, 16-byte aligned).  Fragment layouts are those of mma.m16n8k16: lane =
 // 4 g + t holds rows g, g+8 and columns 2t, 2t+1 (+8) of A and C, and B rows 2t, 2t+1 (+8),
 // column g.  The C fragments of one layer are the A fragments of the next.
 __device__ __forceinline__ float mlp_warp_infer(const uint32_t* __restrict__ w, const float (&x)[MLP_IN]) {
@@ -77,13 +88,13 @@ __device__ __forceinline__ float mlp_warp_infer(const uint32_t* __restrict__ w, 
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
     const uint32_t b0 = w[PK_W1 + (nt * 8 + g) * 4 + t];
-    const float bi0 = __uint_as_float(w[PK_B1 + nt * 8 + 2 * t]), bi1 = __uint_as_float(w[PK_B1 + nt * 8 + 2 * t + 1]);
+    const float2 bi = bias_pair(w, PK_B1 + nt * 8 + 2 * t);
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
-      float c[4] = {bi0, bi1, bi0, bi1};
+      float c[4] = {bi.x, bi.y, bi.x, bi.y};
       mma_bf16_16816(c, a1f[mt][0], a1f[mt][1], 0u, 0u, b0, 0u);
-      const uint32_t lo = pack_bf16x2(fmaxf(c[0], 0.f), fmaxf(c[1], 0.f));
-      const uint32_t hi = pack_bf16x2(fmaxf(c[2], 0.f), fmaxf(c[3], 0.f));
+      const uint32_t lo = pack_relu_bf16x2(c[0], c[1]);
+      const uint32_t hi = pack_relu_bf16x2(c[2], c[3]);
       const int ks = nt >> 1, half = nt & 1;
       a2f[mt][ks][half * 2 + 0] = lo;
       a2f[mt][ks][half * 2 + 1] = hi;
@@ -93,8 +104,8 @@ __device__ __forceinline__ float mlp_warp_infer(const uint32_t* __restrict__ w, 
   uint32_t a3f[2][2][4];
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
-    const float bi0 = __uint_as_float(w[PK_B2 + nt * 8 + 2 * t]), bi1 = __uint_as_float(w[PK_B2 + nt * 8 + 2 * t + 1]);
-    float c[2][4] = {{bi0, bi1, bi0, bi1}, {bi0, bi1, bi0, bi1}};
+    const float2 bi = bias_pair(w, PK_B2 + nt * 8 + 2 * t);
+    float c[2][4] = {{bi.x, bi.y, bi.x, bi.y}, {bi.x, bi.y, bi.x, bi.y}};
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
       const uint32_t b0 = w[PK_W2 + (nt * 8 + g) * PK_W2_STRIDE + ks * 8 + t];
@@ -106,8 +117,8 @@ __device__ __forceinline__ float mlp_warp_infer(const uint32_t* __restrict__ w, 
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
       const int ks = nt >> 1, half = nt & 1;
-      a3f[mt][ks][half * 2 + 0] = pack_bf16x2(fmaxf(c[mt][0], 0.f), fmaxf(c[mt][1], 0.f));
-      a3f[mt][ks][half * 2 + 1] = pack_bf16x2(fmaxf(c[mt][2], 0.f), fmaxf(c[mt][3], 0.f));
+      a3f[mt][ks][half * 2 + 0] = pack_relu_bf16x2(c[mt][0], c[mt][1]);
+      a3f[mt][ks][half * 2 + 1] = pack_relu_bf16x2(c[mt][2], c[mt][3]);
     }
   }
   // layer 3: [32 x 32] x [32 x 8 (column 0 used)] + b3
