@@ -292,7 +292,8 @@ int kt_time_kernels(kt_ctx* ctx, int n_steps, float* ms, int* n_kernels);
  * where e_conf = E is the root).  The network runs once per cell and step, in the first
  * Runge-Kutta stage; the second stage applies the same z to its own E, M^2 and Pi.
  * At most 2 FP64 Newton steps follow; a cell whose residual |f(e)|/E then exceeds 1e-10 falls
- * back to the plain root-find.  Parameters: KT_MLP_NPARAM floats, layout as documented above
+ * back to the plain root-find (the test uses 0.99e-10, formed in single precision, so that every
+ * accepted root meets 1e-10 exactly).  Parameters: KT_MLP_NPARAM floats, layout as documented above
  * KT_MLP_NPARAM.  KT_INV_CONFORMAL is the same start without the network (y = 0: e = e_conf,
  * the closed-form root of the conformal EOS, Sec. 2.4) and the same Newton steps and fallback:
  * the ablation that shows what the network adds; it needs no weights.  (It gives the state of
