@@ -172,7 +172,9 @@ __device__ __forceinline__ unsigned thr_hi(float t) {
 __device__ __forceinline__ unsigned rootfind_learned(const Params& P, const InvIn& v, double EPi, double e_start,
                                                      double& e, double& P0, unsigned& iters, unsigned& fallbacks) {
   const double lo = (P.e_min > 0.0) ? P.e_min : 1e-300;
-  const float tolf = 0.99e-10f * v.Ef;
+  // (E >= 2^120, beyond where the truncated E and A are valid single-precision values: no
+  // acceptance, the plain root-find decides)
+  const float tolf = (obits(v.E) < 0x4770000000000000LL) ? 0.99e-10f * v.Ef : 0.f;
   e = clamp_pos(e_start, lo, v.E);
 #pragma unroll 1
   for (int kk = 0; kk < 3; ++kk) {
