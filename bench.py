@@ -353,7 +353,8 @@ def run_ours(args, world, rank, local):
                 best = args.tuning
             results[mode]["tuning"] = {"tile": list(tu["block"]), "grid_blocks": tu["grid_blocks"],
                                        "candidate": best, "one_block_per_tile": bool(best % 2),
-                                       "layout": ("split", "split_update_staged_by_tma", "fused_stage")[best // 12]}
+                                       "layout": "fp64_stage" if mode == "fp64" else
+                                       ("split", "split_update_staged_by_tma", "fused_stage")[best // 12]}
         del kt
         torch.cuda.empty_cache()
 
@@ -568,6 +569,9 @@ def run_batch(args, world, rank, local):
     barrier(world)
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     slots = kt.time_kernels(max(3, min(args.steps, 10)))
+    tu = kt.tuning()
+    cand = min(range(len(tu["candidate_ms"])), key=lambda i: tu["candidate_ms"][i] or float("inf"))
+    fused = args.mode != "fp64" and cand >= FUSED_FIRST_CANDIDATE
     if rank == 0:
         line = {"metric": "cell updates/s per RK2 step, batch of events", "value": total_cells * args.steps / (ms * 1e-3),
                 "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -576,8 +580,11 @@ def run_batch(args, world, rank, local):
                 "config": {"workload": f"{args.batch} events, nx=ny in 64..160, neta in 16..64, 20-100 hotspots",
                            "cells_total": total_cells, "events_rank0": len(mine), "cells_rank0": cells,
                            "parallelism": f"events sharded over {world} ranks", "mode": args.mode,
-                           "tile": kt.tuning()["block"]},
-                "slots_ms": slots, "gpu_launches": LAUNCHES_PER_STEP["fp64" if args.mode == "fp64" else "mixed"] * args.steps}
+                           "tile": tu["block"], "candidate": cand,
+                           "layout": "fp64_stage" if args.mode == "fp64" else
+                           ("split", "split_update_staged_by_tma", "fused_stage")[cand // 12]},
+                "slots_ms": slots,
+                "gpu_launches": LAUNCHES_PER_STEP["fp64" if (args.mode == "fp64" or fused) else "mixed"] * args.steps}
         print(json.dumps(line), flush=True)
 
 
