@@ -71,13 +71,13 @@ LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
 # kernel ncu captures of the 96^3 learned workload, per cell times the 128^3 cells (average over
 # the two stages of each kernel; the update and fused kernels captured on 32x2x2 tiles, one block
 # per tile).  Only that mode (workload EOS) has a capture.
-MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 761.9e6, "fused_kernel": 826.7e6}}
+MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 762.5e6, "fused_kernel": 827.8e6}}
 # Warp instructions per 32 cells of each launch slot (ncu smsp__inst_executed.sum over the warps of
 # one-kernel captures of the 96^3 learned workload, current kernels), for each kernel's fraction of
 # the SMs' issue rate: one warp instruction per scheduler and clock, 4 schedulers per SM.  The
 # kernels are bound by instruction issue and latency rather than by HBM.
-INST_PER_WARP = {"learned": {"stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1906, "stage2_update": 1910}}
-INST_PER_WARP_FUSED = {"learned": {"stage1_rhs": 4615, "stage2_rhs": 4619}}  # the fused launches
+INST_PER_WARP = {"learned": {"stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1909, "stage2_update": 1913}}
+INST_PER_WARP_FUSED = {"learned": {"stage1_rhs": 4619, "stage2_rhs": 4622}}  # the fused launches
 ISSUE_PER_SM_CLK = 4
 REPEATS = 3  # timed runs of K steps per mode; the median is reported
 
