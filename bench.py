@@ -48,7 +48,7 @@ ALG_BYTES_PER_CELL = {"fp64": 856, "mixed": 728, "learned": 728}
 # FP64 add/multiply/FMA instructions per cell and RK2 step of the FP64 mode (ncu counts of the two
 # fused stage kernels), and GB300's FP64 rate: 2 FMA per SM and clock (152 SMs; 1.25 TFLOP/s at
 # 2.07 GHz nominal), taken at the SM clock sampled during the timed steps
-FP64_INST_PER_CELL_STEP = 1800 + 1829
+FP64_INST_PER_CELL_STEP = 1799 + 1828
 FP64_FMA_PER_SM_CLK = 2
 N_SM = 152
 # per launch slot of kt_time_kernels (bytes per cell); FP64: the fused stage kernels
