@@ -35,9 +35,10 @@ UNIT = "cell updates/s"
 #             + regulated k1 (pi) 40                                            = 320
 #   rhs 2:    qsf 60 + u 16 + u_prev 16 + e, p 8 -> k2 60                        = 160
 #   update 2: q 120 + k1 60 + k2 60 + e 4 -> q 120 + qf 60 + u 16 + e, p 8       = 448
-# = 1088 B (the learned start reads no previous e but writes, in stage 1, and reads, in stage 2,
-# the network's 4-byte output: also 1088 B).
-BYTES_PER_CELL = {"fp64": 856, "mixed": 1088, "learned": 1088}
+# = 1088 B (the learned start reads no previous e but, in both stages, the network's 4-byte
+# output instead: also 1088 B; the network's own launch reads 9 components of the FP32 copy of q^n
+# and writes z, 40 B per element of the padded arrays: 1128 B).
+BYTES_PER_CELL = {"fp64": 856, "mixed": 1088, "learned": 1128}
 # The algorithmic bytes of the method's step, independent of this design: per cell and RK2 step
 # every field is read and written once by a fused kernel per stage (stage 1 reads q^n (15), u^n,
 # u^{n-1} (4 + 4), e, p and writes q*, u*, e, p; stage 2 reads q*, u*, u^n, e, p, q^n and writes
@@ -55,29 +56,32 @@ N_SM = 152
 SLOT_BYTES = {
     "fp64": {"stage1_rhs": 368, "stage2_rhs": 488},
     "mixed": {"stage1_rhs": 160, "stage1_update": 320, "stage2_rhs": 160, "stage2_update": 448},
-    "learned": {"stage1_rhs": 160, "stage1_update": 320, "stage2_rhs": 160, "stage2_update": 448},
+    "learned": {"learned_start": 40, "stage1_rhs": 160, "stage1_update": 320, "stage2_rhs": 160,
+                "stage2_update": 448},
 }
 # The fused launch per stage: stage 1 reads qf 60,
 # u 16, u_prev 16, e, p 8, q (T, pi^{tau mu}, Pi) 72, qf at the cell 60 and writes k1 60, qsf 60, u
 # 16, e, p 8 = 376 (+ network output 4, learned); stage 2 reads qsf 60, u 16, u_prev 16, e, p 8,
 # q 120, k1 60 and writes q 120, qf 60, u 16, e, p 8 = 484 (+ 4, learned): 868 B per step, k never
-# leaves the SM within a stage.
-FUSED_SLOT_BYTES = {"stage1_rhs": 380, "stage2_rhs": 488}
+# leaves the SM within a stage (+ 40 for the network's launch, learned).
+FUSED_SLOT_BYTES = {"learned_start": 40, "stage1_rhs": 380, "stage2_rhs": 488}
 FUSED_FIRST_CANDIDATE = 24  # tuning candidates 24-35 are the fused launches (timed by the autotuner too)
-SLOT_KERNEL = {"stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel", "stage1_update": "update_kernel",
-               "stage2_update": "update_kernel", "tau_advance": "advance_tau_kernel"}
-LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance
+SLOT_KERNEL = {"learned_start": "mlp_start_kernel", "stage1_rhs": "rhs_kernel", "stage2_rhs": "rhs_kernel",
+               "stage1_update": "update_kernel", "stage2_update": "update_kernel", "tau_advance": "advance_tau_kernel"}
+LAUNCHES_PER_STEP = {"fp64": 3, "mixed": 5}  # + the tau advance (+ 1 for the network, learned start)
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels: one-
 # kernel ncu captures of the 96^3 learned workload, per cell times the 128^3 cells (average over
 # the two stages of each kernel; the update and fused kernels captured on 32x2x2 tiles, one block
 # per tile).  Only that mode (workload EOS) has a capture.
-MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 762.5e6, "fused_kernel": 827.8e6}}
+MEASURED_TRAFFIC = {("learned", 128): {"rhs_kernel": 311.2e6, "update_kernel": 756.7e6, "fused_kernel": 827.8e6,
+                                        "mlp_start_kernel": 85.4e6}}
 # Warp instructions per 32 cells of each launch slot (ncu smsp__inst_executed.sum over the warps of
 # one-kernel captures of the 96^3 learned workload, current kernels), for each kernel's fraction of
 # the SMs' issue rate: one warp instruction per scheduler and clock, 4 schedulers per SM.  The
 # kernels are bound by instruction issue and latency rather than by HBM.
-INST_PER_WARP = {"learned": {"stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1909, "stage2_update": 1913}}
-INST_PER_WARP_FUSED = {"learned": {"stage1_rhs": 4619, "stage2_rhs": 4622}}  # the fused launches
+INST_PER_WARP = {"learned": {"learned_start": 259, "stage1_rhs": 2811, "stage2_rhs": 2811, "stage1_update": 1621,
+                             "stage2_update": 1914}}
+INST_PER_WARP_FUSED = {"learned": {"learned_start": 259, "stage1_rhs": 4319, "stage2_rhs": 4622}}  # fused launches
 ISSUE_PER_SM_CLK = 4
 REPEATS = 3  # timed runs of K steps per mode; the median is reported
 
@@ -393,7 +397,7 @@ def run_ours(args, world, rank, local):
     ms_step = main["ms_per_step"]
     fused = args.mode != "fp64" and main.get("tuning", {}).get("candidate", 0) >= FUSED_FIRST_CANDIDATE
     slot_bytes = FUSED_SLOT_BYTES if fused else SLOT_BYTES[args.mode]
-    bpc = sum(slot_bytes.values())
+    bpc = sum(b for slot, b in slot_bytes.items() if main["slots_ms"].get(slot, 0.0) > 0.0)
     alg = ALG_BYTES_PER_CELL[args.mode]
     # per kernel: launches per step, average launch time, algorithmic bytes per launch, GB/s
     kernels = {}
@@ -411,7 +415,7 @@ def run_ours(args, world, rank, local):
     sm_hz_k = ((clocks or {}).get("sm_mhz") or 2070.0) * 1e6
     for slot, t in main["slots_ms"].items():
         if inst and slot in inst and t > 0.0:
-            k = kernels["fused_kernel" if fused else SLOT_KERNEL[slot]]
+            k = kernels["fused_kernel" if (fused and slot.endswith("rhs")) else SLOT_KERNEL[slot]]
             k.setdefault("warp_inst_per_step", 0.0)
             k["warp_inst_per_step"] += inst[slot] * cells / 32
     for k in kernels.values():
@@ -528,7 +532,8 @@ def run_ours(args, world, rank, local):
                 "fp64_pipe": fp64_pipe, "layout_variants": variants,
                 "learned_training": train_info,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": (3 if (args.mode == "fp64" or fused) else 5) * main["steps"]}
+                "gpu_launches": ((3 if (args.mode == "fp64" or fused) else 5)
+                                 + (1 if MODES[args.mode][1] == 1 else 0)) * main["steps"]}
         print(json.dumps(line), flush=True)
 
 
@@ -584,7 +589,8 @@ def run_batch(args, world, rank, local):
                            "layout": "fp64_stage" if args.mode == "fp64" else
                            ("split", "split_update_staged_by_tma", "fused_stage")[cand // 12]},
                 "slots_ms": slots,
-                "gpu_launches": LAUNCHES_PER_STEP["fp64" if (args.mode == "fp64" or fused) else "mixed"] * args.steps}
+                "gpu_launches": (LAUNCHES_PER_STEP["fp64" if (args.mode == "fp64" or fused) else "mixed"]
+                                 + (1 if MODES[args.mode][1] == 1 else 0)) * args.steps}
         print(json.dumps(line), flush=True)
 
 

@@ -274,12 +274,13 @@ int kt_set_tuning(kt_ctx* ctx, int candidate);
 
 /* Measurement (the paper has no counterpart): advance n_steps >= 1 steps exactly as kt_step does
  * but launch by launch, without the CUDA graph, with CUDA events on the context's stream between
- * the launches, and return in ms[0..4] the average duration per step of: the stage-1 right-hand-
- * side launch (FP64: the fused stage-1 launch), the stage-1 update launch (FP64: 0), the stage-2
- * right-hand-side launch (FP64: the fused stage-2 launch), the stage-2 update launch (FP64: 0)
- * and the tau advance.  *n_kernels must be >= 5 on entry and is set to 5.  The state, tau and
- * statistics advance as with kt_step; errors are those of kt_step.  The per-step event
- * synchronisation makes these steps slower in total than kt_step's. */
+ * the launches, and return in ms[0..5] the average duration per step of: the learned start's
+ * network launch (0 without KT_INV_LEARNED), the stage-1 right-hand-side launch (FP64, fused
+ * layout: the fused stage-1 launch), the stage-1 update launch (FP64, fused layout: 0), the
+ * stage-2 right-hand-side launch (FP64, fused layout: the fused stage-2 launch), the stage-2
+ * update launch (FP64, fused layout: 0) and the tau advance.  *n_kernels must be >= 6 on entry
+ * and is set to 6.  The state, tau and statistics advance as with kt_step; errors are those of
+ * kt_step.  The per-step event synchronisation makes these steps slower in total than kt_step's. */
 int kt_time_kernels(kt_ctx* ctx, int n_steps, float* ms, int* n_kernels);
 
 /* ------------------------------------------------------------------ learned root-find start
@@ -289,8 +290,9 @@ int kt_time_kernels(kt_ctx* ctx, int n_steps, float* ms, int* n_kernels);
  *   x = [(ln E - 1)/6, M^2/E^2, 5 Pi/E, ln(1 - M^2/E^2)/2, e_conf/E, |M|/E],
  * e_conf = sqrt(4E^2 - 3M^2) - E the conformal root; output z, start e = e_conf exp(y/10) with
  * y = (M^2/E^2) z where M^2/E^2 > KT_MLP_GATE_R2, else y = 0 (the correction vanishes at rest,
- * where e_conf = E is the root).  The network runs once per cell and step, in the first
- * Runge-Kutta stage; the second stage applies the same z to its own E, M^2 and Pi.
+ * where e_conf = E is the root).  The network runs once per cell and step, in a launch of its
+ * own before the first Runge-Kutta stage, on the state at the start of the step (its single-
+ * precision copy); both stages apply that z to their own E, M^2 and Pi.
  * At most 2 FP64 Newton steps follow; a cell whose residual |f(e)|/E then exceeds 1e-10 falls
  * back to the plain root-find (the test uses 0.99e-10, formed in single precision, so that every
  * accepted root meets 1e-10 exactly).  Parameters: KT_MLP_NPARAM floats, layout as documented above

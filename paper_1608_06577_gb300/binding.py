@@ -284,7 +284,7 @@ class KT:
         g) from now on (kt_set_tuning)."""
         self._check(self.L.kt_set_tuning(self.ctx, int(candidate)), "kt_set_tuning")
 
-    KERNEL_SLOTS = ("stage1_rhs", "stage1_update", "stage2_rhs", "stage2_update", "tau_advance")
+    KERNEL_SLOTS = ("learned_start", "stage1_rhs", "stage1_update", "stage2_rhs", "stage2_update", "tau_advance")
     DIAGNOSTICS = ("Kn_theta_pi", "Kn_theta_Pi", "Rinv_pi", "Rinv_Pi", "R2inv_pi", "R2inv_Pi", "regulation")
 
     def diagnostics(self, event=0) -> dict:
@@ -296,9 +296,10 @@ class KT:
     def time_kernels(self, n_steps: int) -> dict:
         """Advances n_steps steps launch by launch with CUDA events between the launches
         (kt_time_kernels) and returns the average ms per step of each launch slot; in FP64 mode
-        the rhs slots hold the fused stage kernels and the update slots are 0."""
-        ms = (C.c_float * 5)()
-        n = C.c_int(5)
+        and the fused layout the rhs slots hold the fused stage kernels and the update slots are
+        0; learned_start is the network's launch (0 without the learned start)."""
+        ms = (C.c_float * 6)()
+        n = C.c_int(6)
         self._check(self.L.kt_time_kernels(self.ctx, int(n_steps), ms, C.byref(n)), "kt_time_kernels")
         return dict(zip(self.KERNEL_SLOTS, list(ms)[:n.value]))
 

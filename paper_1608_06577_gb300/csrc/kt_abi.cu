@@ -81,7 +81,8 @@ struct Ctx {
   int fused = 0;                   // one fused launch per stage (right-hand side + update)
   int upd_nbuf = 1;                // staged update: buffers per block (2 on a persistent grid)
   float* reg = nullptr;            // regulation factor of the last step, per cell (diagnostics)
-  float* z_net = nullptr;          // learned start: the network's output per cell within a step
+  float* z_net = nullptr;          // learned start: the network's output per cell for the current step
+  int grid_mlp = 1;                // blocks of mlp_start_kernel
   int max_tiles = 0;
   // work decomposition
   int shape = 0;
@@ -556,7 +557,6 @@ UpdIO make_uio(Ctx* c, int stage) {
   u.d_tau = c->d_tau;
   u.status = c->d_stat;
   u.counters = (unsigned long long*)(c->d_stat + 4);
-  u.mlp_packed = c->learned ? c->d_mlp_packed : nullptr;
   u.reg_out = io.reg_out;
   u.z_net = c->z_net;
   return u;
@@ -689,43 +689,52 @@ void launch_split_stage(Ctx* c, const StageIO<float>& io, const UpdIO& uio) {
 }
 
 // ev (optional, kNumTimed + 1 events): recorded between the launches of one step, in the order
-// stage-1 rhs (or fused stage 1), stage-1 update, stage-2 rhs (or fused stage 2), stage-2 update,
-// tau advance; the FP64 path has no update launches, so their intervals are empty.
-constexpr int kNumTimed = 5;
+// learned start (the network's inference), stage-1 rhs (or fused stage 1), stage-1 update,
+// stage-2 rhs (or fused stage 2), stage-2 update, tau advance; intervals of launches a context
+// does not make (the network without the learned start, the update launches of the FP64 path and
+// of the fused layout) are empty.
+constexpr int kNumTimed = 6;
 void mark(Ctx* c, cudaEvent_t* ev, int i) {
   if (ev) cudaEventRecord(ev[i], c->stream);
 }
 
+// the learned start's network on the state at the start of the step (its FP32 copy)
+void launch_mlp_start(Ctx* c) {
+  kt::mlp_start_kernel<<<c->grid_mlp, 256, 0, c->stream>>>(c->qf, c->gs, c->d_tau, c->P.milne,
+                                                           c->d_mlp_packed, c->z_net);
+}
+
 template <typename R>
 void launch_step_stages(Ctx* c, cudaEvent_t* ev) {
+  mark(c, ev, 0);
   if constexpr (sizeof(R) == 4) {
+    if (c->learned && c->P.mlp_infer) launch_mlp_start(c);
+    mark(c, ev, 1);
     if (c->fused) {  // the fused launches take the right-hand-side slots; the update slots stay empty
-      mark(c, ev, 0);
       launch_fused<1>(c, make_io<float>(c, 1), make_uio(c, 1));
-      mark(c, ev, 1);
       mark(c, ev, 2);
-      launch_fused<2>(c, make_io<float>(c, 2), make_uio(c, 2));
       mark(c, ev, 3);
+      launch_fused<2>(c, make_io<float>(c, 2), make_uio(c, 2));
       mark(c, ev, 4);
+      mark(c, ev, 5);
       return;
     }
-    mark(c, ev, 0);
     launch_rhs<1>(c, make_io<float>(c, 1));
-    mark(c, ev, 1);
+    mark(c, ev, 2);
     launch_update<1>(c, make_uio(c, 1));
-    mark(c, ev, 2);
+    mark(c, ev, 3);
     launch_rhs<2>(c, make_io<float>(c, 2));
-    mark(c, ev, 3);
+    mark(c, ev, 4);
     launch_update<2>(c, make_uio(c, 2));
-    mark(c, ev, 4);
+    mark(c, ev, 5);
   } else {
-    mark(c, ev, 0);
-    launch_stage<1>(c, make_io<double>(c, 1));
     mark(c, ev, 1);
+    launch_stage<1>(c, make_io<double>(c, 1));
     mark(c, ev, 2);
-    launch_stage<2>(c, make_io<double>(c, 2));
     mark(c, ev, 3);
+    launch_stage<2>(c, make_io<double>(c, 2));
     mark(c, ev, 4);
+    mark(c, ev, 5);
   }
 }
 
@@ -734,7 +743,7 @@ int enqueue_step(Ctx* c, cudaEvent_t* ev = nullptr) {
   if (c->mixed) launch_step_stages<float>(c, ev);
   else launch_step_stages<double>(c, ev);
   advance_tau_kernel<<<1, 1, 0, c->stream>>>(c->d_tau, c->P.dtau);
-  mark(c, ev, 5);
+  mark(c, ev, 6);
   // u^{n-1} <- u^n, u^n <- u^{n+1}; the old u^{n-1} buffer (holding u^*) becomes the spare
   int ncur = c->spare, nprev = c->cur, nspare = c->prev;
   c->cur = ncur; c->prev = nprev; c->spare = nspare;
@@ -1110,6 +1119,14 @@ int kt_init_batch(kt_ctx** out, int n_events, const kt_grid* grids, double dx, d
   if (c->mixed) c->d_umaps = (CUtensorMap*)carve(kUpdMaps * c->lat.size() * sizeof(CUtensorMap));
   c->reg = (float*)carve(fs * 4);
   c->z_net = (float*)carve(fs * 4);
+  CK(cudaMemsetAsync(c->z_net, 0, fs * 4, c->stream));  // z = 0: the conformal start (no network)
+  {
+    int nb = 0, dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kt::mlp_start_kernel, 256, 0));
+    c->grid_mlp = (int)std::max(1LL, std::min((long long)std::max(1, nb) * sms, (long long)((fs + 255) / 256)));
+  }
   P.seg_d = c->seg_d;
   P.seg_f = c->seg_f;
   P.seg_r = c->seg_r;

@@ -1,9 +1,12 @@
-// kt_split.cuh -- the mixed-precision Runge-Kutta stage as two launches.
+// kt_split.cuh -- the mixed-precision Runge-Kutta stage as two launches (or one fused launch).
 //
 // rhs_kernel<S>:    k_S = dtau C[q] in FP32 (a, b of the stage: stencil, fluxes, sources; Sec. 3.1,
 //                   App. B).  No FP64 arithmetic, so it runs at the occupancy of the FP32 code.
-// update_kernel<S>: the FP64 Heun accumulation, the root-find (learned start on the tensor cores,
-//                   or the plain safeguarded Newton), the regulator and the stores (c-f).
+// update_kernel<S>: the FP64 Heun accumulation, the root-find (learned start from the network's
+//                   output of mlp_start_kernel, or the plain safeguarded Newton), the regulator and
+//                   the stores (c-f).
+// fused_kernel<S>:  both in one launch, k in shared memory.
+// mlp_start_kernel: the network's output z for every cell at the start of the step (tensor cores).
 //
 // Heun (Eqs. step1-finalStep) in increment form:
 //     q*      = q^n + k_1,            k_1 = dtau C[q^n]
@@ -33,9 +36,8 @@ struct UpdIO {
   const double* d_tau;      // tau^n
   unsigned* status;
   unsigned long long* counters;
-  const uint32_t* mlp_packed;
   float* reg_out;           // stage 2: the regulation factor applied at each cell, or null
-  float* z_net;             // learned start: the network's output z per cell (stage 1 writes, stage 2 reads)
+  const float* z_net;       // learned start: the network's output z per cell for the step (mlp_start_kernel)
 };
 
 // inversion inputs of q: T^{tau mu} (0-3), pi^{tau mu} (4-7), Pi (14)
@@ -279,7 +281,7 @@ __device__ __forceinline__ float pi32_state(const In& in, int n) {
 // to the field array for the second stage, its pi components carrying the regulator's rescaling.
 template <int STAGE, bool LEARNED, bool PI32, typename In, bool STORE_K1 = false>
 __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, const UpdIO& io, const In& in, int i,
-                                            int j, int k, double tau_out, const uint32_t* s_mlp, unsigned& st,
+                                            int j, int k, double tau_out, unsigned& st,
                                             unsigned& nit, unsigned& nreg, unsigned& nfb) {
   const bool valid = (i < L.nx) && (j < L.ny) && (k < L.nz);
   const long long fs = L.fstride;
@@ -322,9 +324,7 @@ __device__ __forceinline__ void update_cell(const Params& P, const Lattice& L, c
   const InvIn v = inv_in(gnn, E, Mx, My, Mn, Pi);
   double start;
   if constexpr (LEARNED) {
-    float z = (STAGE == 2 && valid) ? __ldg(io.z_net + c) : 0.f;
-    start = learned_start<STAGE == 1>(P, v, s_mlp, z);
-    if (STAGE == 1 && valid) io.z_net[c] = z;
+    start = learned_start(v, valid ? __ldg(io.z_net + c) : 0.f);
   } else {
     start = valid ? to_f64<float>(__ldg(io.e_guess + c)) : 1.0;
   }
@@ -447,12 +447,6 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     update_kernel(const Params P, const UpdIO io, const Lattice* __restrict__ lats, const Tile* __restrict__ tiles,
                   int ntiles) {
   unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
-  constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
-  __shared__ alignas(16) uint32_t s_mlp[kInfer ? PK_WORDS : 1];
-  if constexpr (kInfer) {
-    if (P.mlp_infer) mlp_load_shared(s_mlp, io.mlp_packed);
-    __syncthreads();
-  }
   const double tau_out = io.d_tau[0] + P.dtau;
   int t0, t1;
   tile_range(ntiles, t0, t1);
@@ -461,9 +455,45 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     const Lattice L = lats[tl.event];
     const int i = tl.i0 + (int)threadIdx.x, j = tl.j0 + (int)threadIdx.y, k = tl.k0 + (int)threadIdx.z;
     const UpdInGlobal in{io, L.fstride, L.idx(i + 2, j + 2, k + 2)};
-    update_cell<STAGE, LEARNED, PI32>(P, L, io, in, i, j, k, tau_out, s_mlp, st, nit, nreg, nfb);
+    update_cell<STAGE, LEARNED, PI32>(P, L, io, in, i, j, k, tau_out, st, nit, nreg, nfb);
   }
   block_stats(io.status, nullptr, io.counters, st, 0.f, nit, nreg, nfb);
+}
+
+// ---------------------------------------------------------------- the network, once per step
+// The learned start's network output z for every element of the field arrays (cells, their
+// ghosts and the padding between events) from the FP32 copy of the state q^n at tau^n, before the
+// first stage: one warp per 32 consecutive elements (coalesced loads of the 9 components the
+// features read), the warp-wide tensor-core inference where one of its elements has r^2 above
+// kMlpGateR2 (else z = 0).  Both stages of the step apply this z to their own E, M^2 and Pi, which
+// differ from q^n by O(dtau).  Run in a launch of its own, at full occupancy, the inference's
+// latency hides behind other warps; inside the register-capped update it could not.
+__global__ void __launch_bounds__(256) mlp_start_kernel(const float* __restrict__ qf, long long fs,
+                                                        const double* __restrict__ d_tau, int milne,
+                                                        const uint32_t* __restrict__ packed,
+                                                        float* __restrict__ z_net) {
+  __shared__ alignas(16) uint32_t sw[PK_WORDS];
+  mlp_load_shared(sw, packed);
+  __syncthreads();
+  const float tau = d2f_trunc(d_tau[0]);
+  const float gnn = milne ? tau * tau : 1.f;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < fs; base += stride) {  // block-uniform
+    const long long t = base + threadIdx.x;
+    const bool in = t < fs;
+    float E = 1.f, Mx = 0.f, My = 0.f, Mn = 0.f, Pi = 0.f;  // a rest state past the end
+    if (in) {
+      E = __ldg(qf + t) - __ldg(qf + 4 * fs + t);
+      Mx = __ldg(qf + fs + t) - __ldg(qf + 5 * fs + t);
+      My = __ldg(qf + 2 * fs + t) - __ldg(qf + 6 * fs + t);
+      Mn = __ldg(qf + 3 * fs + t) - __ldg(qf + 7 * fs + t);
+      Pi = __ldg(qf + 14 * fs + t);
+    }
+    float x[MLP_IN], ecE;
+    mlp_features(fmaxf(E, 1e-30f), fmaf(Mx, Mx, fmaf(My, My, gnn * Mn * Mn)), Pi, x, ecE);
+    const float z = __any_sync(0xffffffffu, x[1] > kMlpGateR2) ? mlp_warp_infer(sw, x) : 0.f;  // all lanes
+    if (in) z_net[t] = z;
+  }
 }
 
 // ---------------------------------------------------------------- staged update (TMA)
@@ -504,8 +534,6 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
                          const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ umaps, int nbuf) {
   extern __shared__ __align__(128) unsigned char u_raw[];
   __shared__ alignas(8) uint64_t s_bar[2];
-  constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
-  __shared__ alignas(16) uint32_t s_mlp[kInfer ? PK_WORDS : 1];
   unsigned char* const sbase = u_raw + ((128u - (smem_u32(u_raw) & 127u)) & 127u);
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int bc = (blockDim.x + 4) * blockDim.y * blockDim.z;
@@ -518,7 +546,6 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     mbar_init(&s_bar[1], 1);
     fence_barrier_init();
   }
-  if (kInfer && P.mlp_infer) mlp_load_shared(s_mlp, io.mlp_packed);
   __syncthreads();
 
   unsigned st = 0, nit = 0, nreg = 0, nfb = 0;
@@ -565,7 +592,7 @@ __global__ void __maxnreg__(STAGE == 1 ? 72 : 96)
     const UpdInShared<STAGE> in{(const double*)buf, (const float*)(buf + qbytes), (const float*)(buf + qbytes + kbytes),
                                 bc, own};
     update_cell<STAGE, LEARNED, false>(P, L, io, in, tl.i0 + (int)threadIdx.x, tl.j0 + (int)threadIdx.y,
-                                       tl.k0 + (int)threadIdx.z, tau_out, s_mlp, st, nit, nreg, nfb);
+                                       tl.k0 + (int)threadIdx.z, tau_out, st, nit, nreg, nfb);
     if (nbuf == 1 && t + 1 < t1) {  // single buffer: refill it once every thread is done with it
       if (__syncthreads_or(bad)) { bad = true; break; }
       if (tid == 0) issue(t + 1, 0u);
@@ -610,8 +637,6 @@ __global__ void __maxnreg__(128)
                  const Tile* __restrict__ tiles, int ntiles, const CUtensorMap* __restrict__ tmaps) {
   extern __shared__ __align__(128) float s_raw[];
   __shared__ alignas(8) uint64_t s_bar[2];
-  constexpr bool kInfer = LEARNED && STAGE == 1;  // the network runs in the first stage only
-  __shared__ alignas(16) uint32_t s_mlp[kInfer ? PK_WORDS : 1];
   float* const s_q = s_raw + ((32u - ((smem_u32(s_raw) >> 2) & 31u)) & 31u);  // TMA wants 128-byte buffers
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
@@ -624,7 +649,6 @@ __global__ void __maxnreg__(128)
     mbar_init(&s_bar[1], 1);
     fence_barrier_init();
   }
-  if (kInfer && P.mlp_infer) mlp_load_shared(s_mlp, uio.mlp_packed);
   __syncthreads();
 
   float amax = 0.f;
@@ -701,7 +725,7 @@ __global__ void __maxnreg__(128)
     }
     // ---- the update (as update_kernel), reading k from shared memory
     const UpdInFused<STAGE> in{uio, L.fstride, L.idx(i + 2, j + 2, k + 2), sk, nthr};
-    update_cell<STAGE, LEARNED, false, UpdInFused<STAGE>, true>(P, L, uio, in, i, j, k, tau_out, s_mlp, st, nit,
+    update_cell<STAGE, LEARNED, false, UpdInFused<STAGE>, true>(P, L, uio, in, i, j, k, tau_out, st, nit,
                                                                   nreg, nfb);
     fence_proxy_async_smem();  // this thread's generic accesses of the buffer before the next copy into it
   }

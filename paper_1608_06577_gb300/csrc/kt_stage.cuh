@@ -863,21 +863,15 @@ __device__ __forceinline__ InvIn inv_in(double gnn, double E, double Mx, double 
   return v;
 }
 
-// The network's start for the root-find of the inversion inputs v: features in FP32, the
-// network's output z, and the conformal root corrected by y = r^2 z (r^2 = M^2/E^2, feature 1):
-// e = E (e_conf/E) exp(y/10).  The correction vanishes at rest, where e_conf = E is the root, and
-// the network's BF16 error scales with it.  The network runs once per cell and step: with INFER
-// (the first stage) the warp-wide tensor-core inference gives z, which is returned in z_io (a warp
-// whose cells all have r^2 <= kMlpGateR2 skips it); otherwise (the second stage, whose state
-// differs by O(dtau)) z_io holds that z on entry.  All 32 lanes of the warp call it together.
-template <bool INFER>
-__device__ __forceinline__ double learned_start(const Params& P, const InvIn& v, const uint32_t* s_mlp,
-                                                float& z_io) {
+// The network's start for the root-find of the inversion inputs v: the conformal root corrected
+// by y = r^2 z (r^2 = M^2/E^2, feature 1), e = E (e_conf/E) exp(y/10), with z the network's
+// output for this cell at the start of the step (mlp_start_kernel).  The correction vanishes at
+// rest, where e_conf = E is the root, and the network's BF16 error scales with it; cells with
+// r^2 <= kMlpGateR2 start from e_conf.
+__device__ __forceinline__ double learned_start(const InvIn& v, float z) {
   float x[MLP_IN], ecE;
   mlp_features(fmaxf(v.Ef, 1e-30f), v.M2f, d2f_trunc(v.Pi), x, ecE);
-  if constexpr (INFER)
-    z_io = (P.mlp_infer && __any_sync(0xffffffffu, x[1] > kMlpGateR2)) ? mlp_warp_infer(s_mlp, x) : 0.f;
-  const float y = (x[1] > kMlpGateR2) ? x[1] * z_io : 0.f;
+  const float y = (x[1] > kMlpGateR2) ? x[1] * z : 0.f;
   return f2d_bits(v.Ef * ecE * __expf(0.1f * y));
 }
 
